@@ -1,0 +1,211 @@
+"""FP64 CPU oracle: Python wrapper around ``qcd_oracle.c``.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this module.  It shares no code with the
+GPU library (it never imports ``paper_1712_01505_gb300``) and the library never
+imports it.
+
+Every function takes and returns numpy ``complex128`` arrays in the canonical
+layouts (see the header of ``qcd_oracle.c``):
+
+* gauge field ``U``: ``(4, V, 3, 3)``; site index ``x + Lx*(y + Ly*(z + Lz*t))``
+* 4D spinor: ``(V, 4, 3)``; 5D spinor: ``(Ls, V, 4, 3)``
+
+Operators follow Kanamori & Matsufuru (arXiv:1712.01505): the Wilson matrix of
+Eq. (1) in hopping-parameter form ``M = 1 - kappa H`` (``kappa = 1/(2(m0+4))``),
+the domain-wall matrix of Eq. (2), BiCGStab for Wilson and CG on the normal
+equations for domain-wall (Sec. II C).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qcd_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+c_int_p = ctypes.POINTER(ctypes.c_int)
+c_dbl_p = ctypes.POINTER(ctypes.c_double)
+c_long_p = ctypes.POINTER(ctypes.c_long)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``qcd_oracle.c`` into ``liboracle.so`` with gcc (FP64, OpenMP, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.run(
+            ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+            check=True,
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.ora_wilson_solve.restype = ctypes.c_long
+        _lib.ora_dw_solve.restype = ctypes.c_long
+        _lib.ora_num_threads.restype = ctypes.c_int
+    return _lib
+
+
+def _iarr(v):
+    a = (ctypes.c_int * 4)(*[int(t) for t in v])
+    return a
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def num_threads() -> int:
+    return lib().ora_num_threads()
+
+
+def gamma(k: int) -> np.ndarray:
+    """Dirac matrix gamma_{k+1} for k = 0..3, gamma_5 for k = 4 (chiral basis)."""
+    out = np.zeros((4, 4, 2), dtype=np.float64)
+    lib().ora_gamma(int(k), out.ctypes.data_as(c_dbl_p))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def volume(L) -> int:
+    return int(np.prod(L))
+
+
+def parity(L) -> np.ndarray:
+    """Parity (x+y+z+t) mod 2 of every canonical site."""
+    Lx, Ly, Lz, Lt = L
+    t, z, y, x = np.meshgrid(np.arange(Lt), np.arange(Lz), np.arange(Ly), np.arange(Lx),
+                             indexing="ij")
+    return ((x + y + z + t) & 1).reshape(-1)
+
+
+def hop(L, bc, U, psi, dagger=False, out_parity=-1):
+    """H psi (Eq. (1) hopping term), or H^dag psi; optionally only on one parity."""
+    U, psi = _c(U), _c(psi)
+    out = np.empty_like(psi)
+    lib().ora_hop(_iarr(L), _iarr(bc), _p(U), _p(psi), _p(out), int(dagger), int(out_parity))
+    return out
+
+
+def hop_sites(L, bc, U, psi, sites, dagger=False):
+    """(H psi)(x) at the canonical sites listed; returns (n, 4, 3)."""
+    U, psi = _c(U), _c(psi)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((len(sites), 4, 3), dtype=np.complex128)
+    lib().ora_hop_sites(_iarr(L), _iarr(bc), _p(U), _p(psi), _p(sites), ctypes.c_long(len(sites)),
+                        _p(out), int(dagger))
+    return out
+
+
+def wilson(L, bc, kappa, U, psi, dagger=False):
+    """M psi with M = 1 - kappa H, or M^dag psi."""
+    U, psi = _c(U), _c(psi)
+    out = np.empty_like(psi)
+    lib().ora_wilson(_iarr(L), _iarr(bc), ctypes.c_double(kappa), _p(U), _p(psi), _p(out),
+                     int(dagger))
+    return out
+
+
+def wilson_mhat(L, bc, kappa, U, psi_even, dagger=False):
+    """Schur operator Mhat = 1 - kappa^2 H_eo H_oe on a full-lattice vector living on even sites."""
+    U, psi = _c(U), _c(psi_even)
+    out = np.empty_like(psi)
+    lib().ora_wilson_mhat(_iarr(L), _iarr(bc), ctypes.c_double(kappa), _p(U), _p(psi), _p(out),
+                          int(dagger))
+    return out
+
+
+def wilson_solve(L, bc, kappa, U, b, tol=1e-10, maxiter=100000, dagger=False):
+    """Solve M x = b (or M^dag x = b); returns (x, iterations, full relative residual)."""
+    U, b = _c(U), _c(b)
+    x = np.zeros_like(b)
+    res = ctypes.c_double(0)
+    it = lib().ora_wilson_solve(_iarr(L), _iarr(bc), ctypes.c_double(kappa), _p(U), _p(b), _p(x),
+                                ctypes.c_double(tol), ctypes.c_long(maxiter), int(dagger),
+                                ctypes.byref(res))
+    return x, int(it), res.value
+
+
+def dw(L, bc, Ls, M5, mf, U, psi, dagger=False):
+    """D_DW psi of Eq. (2) (or its adjoint) on a (Ls, V, 4, 3) field."""
+    U, psi = _c(U), _c(psi)
+    out = np.empty_like(psi)
+    lib().ora_dw(_iarr(L), _iarr(bc), int(Ls), ctypes.c_double(M5), ctypes.c_double(mf), _p(U),
+                 _p(psi), _p(out), int(dagger))
+    return out
+
+
+def dw_block(Ls, V, M5, mf, psi, dagger=False):
+    """A psi: the site-local (s, spin) part of Eq. (2)."""
+    psi = _c(psi)
+    out = np.empty_like(psi)
+    lib().ora_dw_block_apply(int(Ls), ctypes.c_long(V), ctypes.c_double(M5), ctypes.c_double(mf),
+                             _p(psi), _p(out), int(dagger))
+    return out
+
+
+def dw_ainv(Ls, V, M5, mf, psi, dagger=False):
+    """A^-1 psi (A^-dag psi) by Gauss-Jordan inversion of the site-local block."""
+    psi = _c(psi)
+    out = np.empty_like(psi)
+    lib().ora_dw_ainv(int(Ls), ctypes.c_long(V), ctypes.c_double(M5), ctypes.c_double(mf),
+                      _p(psi), _p(out), int(dagger))
+    return out
+
+
+def dw_mhat(L, bc, Ls, M5, mf, U, psi_even, dagger=False):
+    """Domain-wall Schur operator Mhat = 1 - 1/4 A^-1 H_eo A^-1 H_oe (or its adjoint)."""
+    U, psi = _c(U), _c(psi_even)
+    out = np.empty_like(psi)
+    lib().ora_dw_mhat(_iarr(L), _iarr(bc), int(Ls), ctypes.c_double(M5), ctypes.c_double(mf),
+                      _p(U), _p(psi), _p(out), int(dagger))
+    return out
+
+
+def dw_solve(L, bc, Ls, M5, mf, U, b, tol=1e-10, maxiter=100000):
+    """Solve D_DW x = b by even-odd CG on Mhat^dag Mhat; returns (x, iterations, residual)."""
+    U, b = _c(U), _c(b)
+    x = np.zeros_like(b)
+    res = ctypes.c_double(0)
+    it = lib().ora_dw_solve(_iarr(L), _iarr(bc), int(Ls), ctypes.c_double(M5),
+                            ctypes.c_double(mf), _p(U), _p(b), _p(x), ctypes.c_double(tol),
+                            ctypes.c_long(maxiter), ctypes.byref(res))
+    return x, int(it), res.value
+
+
+def wilson_force(L, bc, kappa, X, eta):
+    """dS/dU for S = phi^dag (M^dag M)^-1 phi given X = M^-1 eta, eta = M^-dag phi.
+
+    Returns a (4, V, 3, 3, 2) float64 array: d S / d Re U_ab and d S / d Im U_ab.
+    """
+    X, eta = _c(X), _c(eta)
+    V = volume(L)
+    out = np.empty((4, V, 3, 3, 2), dtype=np.float64)
+    lib().ora_wilson_force(_iarr(L), _iarr(bc), ctypes.c_double(kappa), _p(X), _p(eta), _p(out))
+    return out
+
+
+def wilson_action(L, bc, kappa, U, phi, tol=1e-13):
+    """S = phi^dag (M^dag M)^-1 phi = |M^-dag phi|^2 and the solves behind it.
+
+    Returns (S, eta, X).
+    """
+    eta, _, _ = wilson_solve(L, bc, kappa, U, phi, tol=tol, dagger=True)
+    X, _, _ = wilson_solve(L, bc, kappa, U, eta, tol=tol, dagger=False)
+    return float(np.vdot(eta, eta).real), eta, X
