@@ -1,0 +1,234 @@
+/*
+ * libqcd — GB300 (sm_103a) lattice-QCD fermion solver.
+ *
+ * The operations are those of Kanamori & Matsufuru, "Practical Implementation
+ * of Lattice QCD Simulation on Intel Xeon Phi Knights Landing"
+ * (arXiv:1712.01505):
+ *   - the Wilson fermion matrix, Eq. (1), used in hopping-parameter form
+ *       M = 1 - kappa H,  kappa = 1/(2(m0+4))   (so M = 2 kappa D_W),
+ *       H psi(x) = sum_mu (1-gamma_mu) U_mu(x) psi(x+mu)
+ *                       + (1+gamma_mu) U_mu(x-mu)^dag psi(x-mu);
+ *   - the domain-wall fermion matrix, Eq. (2), with the fifth dimension kept
+ *     as an internal degree of freedom (Sec. II B 2), m0 = -M5 in its 4D
+ *     Wilson blocks, P_+- = (1 +- gamma_5)/2 and quark mass m = mf;
+ *   - BiCGStab for Wilson and CG on the normal equations for domain-wall
+ *     (Sec. II C), with a reduced-precision inner solver (Sec. II C, last
+ *     paragraph) corrected by double-precision outer steps.
+ * Both operators are even-odd (Schur) preconditioned on the even sites.
+ *
+ * Conventions
+ *   - Dirac matrices in the chiral basis: gamma_k = [[0,-i sigma_k],[i sigma_k,0]],
+ *     gamma_4 = [[0,1],[1,0]], gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4 = diag(1,1,-1,-1).
+ *   - Canonical site index i = x + Lx*(y + Ly*(z + Lz*t)); parity (x+y+z+t) mod 2.
+ *   - Canonical fields are interleaved complex128 (re, im doubles):
+ *       gauge  U[mu][i][a][b]          shape (4, V, 3, 3),  U_ab of U_mu(x)
+ *       spinor psi[r][i][spin][colour] shape (nrhs, V, 4, 3)
+ *       domain-wall spinor             shape (nrhs, Ls, V, 4, 3), s slowest
+ *       force  dSdU[mu][i][a][b][2]    shape (4, V, 3, 3, 2) float64
+ *   - Boundary factors bc[mu] = +1 (periodic) or -1 (antiperiodic) multiply a
+ *     hop that wraps around direction mu; they are applied in the stencil and
+ *     never folded into the stored links.
+ *
+ * Memory, streams and errors
+ *   - Pointers to canonical fields may be device or host memory; the library
+ *     inspects them with cudaPointerGetAttributes.  Host buffers are staged
+ *     through device memory owned by the gauge handle and the call returns
+ *     only after the result has reached the host.
+ *   - The caller owns every buffer it passes and the library never frees one.
+ *     A qcd_gauge handle owns its reordered link copies and a workspace of
+ *     device vectors (Krylov vectors, staging, reduction scratch), all
+ *     released by qcd_gauge_free.
+ *   - Work is ordered on the caller's stream (`stream` = cudaStream_t, NULL
+ *     for the legacy default stream).  qcd_dslash, qcd_field_pack/unpack and
+ *     qcd_force on device buffers are asynchronous; qcd_solve returns once the
+ *     solve has finished because it fills `info`.
+ *   - Every call returns a qcd_status; arguments are validated on the host
+ *     before anything is launched.  qcd_last_error() gives a message for the
+ *     last failing call of the calling thread.
+ *   - Calls that share one gauge handle must not run concurrently from
+ *     several host threads (they share the handle's workspace).
+ */
+#ifndef QCD_H
+#define QCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QCD_OK = 0,
+  QCD_ERR_ARG = 1,         /* invalid argument (detected before any launch)        */
+  QCD_ERR_CUDA = 2,        /* a CUDA runtime call failed                           */
+  QCD_ERR_OOM = 3,         /* device allocation failed                             */
+  QCD_ERR_NOCONV = 4,      /* maxiter reached; x holds the best iterate            */
+  QCD_ERR_BREAKDOWN = 5,   /* BiCGStab breakdown persisted after restarts          */
+  QCD_ERR_NAN = 6,         /* a reduction produced NaN or Inf                       */
+  QCD_ERR_TIMEOUT = 7,     /* reserved: a bounded device wait gave up               */
+  QCD_ERR_UNSUPPORTED = 8  /* valid but unsupported combination of arguments        */
+} qcd_status;
+
+typedef enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2 } qcd_prec;
+
+typedef enum { QCD_WILSON = 0, QCD_DWF = 1 } qcd_fermion_type;
+
+typedef enum {
+  QCD_OP_D_EO = 0,     /* out_even = H_eo in_odd  (hopping term only, no kappa)    */
+  QCD_OP_D_OE = 1,     /* out_odd  = H_oe in_even                                  */
+  QCD_OP_MHAT = 2,     /* even-odd Schur operator on even sites (see qcd_dslash)   */
+  QCD_OP_MHAT_DAG = 3, /* its adjoint                                              */
+  QCD_OP_FULL = 4,     /* the unpreconditioned matrix M (Wilson) or D_DW (Eq. (2)) */
+  QCD_OP_FULL_DAG = 5  /* its adjoint                                              */
+} qcd_op;
+
+typedef enum {
+  QCD_LAYOUT_CANON = 0,   /* canonical complex128 full-lattice fields            */
+  QCD_LAYOUT_INTERNAL = 1 /* library-private single-parity buffers of `prec`     */
+} qcd_layout;
+
+typedef enum { QCD_BICGSTAB = 0, QCD_CG_NORMAL = 1 } qcd_method;
+
+/* Lattice extents L[mu] (mu = x,y,z,t; Sec. II A: x_mu = 1..L_mu), all even
+ * and >= 2; boundary factors bc[mu] = +1 or -1 (Sec. II B 1: periodic or
+ * antiperiodic); recon = 18 (full links) or 12 (two rows stored, the third
+ * rebuilt as conj(row0 x row1); applies to the FP32 and FP16 copies). */
+typedef struct {
+  int32_t L[4];
+  int32_t bc[4];
+  int32_t recon;
+} qcd_geom;
+
+/* type = QCD_WILSON: kappa = 1/(2(m0+4)) of Eq. (1).
+ * type = QCD_DWF: Ls = N_s >= 2 (fifth-dimension size), M5 (m0 = -M5 in the
+ * D_W blocks of Eq. (2)), mf = m of Eq. (2); kappa is ignored. */
+typedef struct {
+  int32_t type;
+  double kappa;
+  int32_t Ls;
+  double M5;
+  double mf;
+} qcd_fermion;
+
+/* method: QCD_BICGSTAB (Wilson) or QCD_CG_NORMAL (CG on Mhat^dag Mhat; the
+ *   only choice for domain-wall, whose spectrum defeats BiCGStab, Sec. II C).
+ * tol: target |b - A x| / |b| on the full, unpreconditioned system.
+ * maxiter: cap on inner Krylov iterations (summed over restarts).
+ * inner: precision of the inner iterations (QCD_F64: plain double solve;
+ *   QCD_F32 / QCD_F16: mixed precision with double-precision reliable
+ *   updates -- true residual recomputed and solution accumulated in FP64).
+ * delta: a reliable update is made when the iterated residual has dropped by
+ *   this factor since the last one (0 < delta < 1; 0 selects 0.1).
+ * use_graph: capture `graph_chunk` inner iterations in one CUDA graph and
+ *   check convergence once per graph launch (0 = plain launches).
+ * x0_given: x holds an initial guess on entry (warm start).
+ * dagger: solve with the adjoint operator (A^dag x = b); Wilson only. */
+typedef struct {
+  int32_t method;
+  double tol;
+  int32_t maxiter;
+  int32_t inner;
+  double delta;
+  int32_t use_graph;
+  int32_t graph_chunk;
+  int32_t x0_given;
+  int32_t dagger;
+} qcd_solver_params;
+
+/* Per right-hand side result of qcd_solve. */
+typedef struct {
+  int32_t iters;         /* inner Krylov iterations                               */
+  int32_t outer_updates; /* double-precision reliable updates performed           */
+  int32_t converged;     /* 1 if true_resid <= tol                                */
+  int32_t status;        /* qcd_status for this right-hand side                   */
+  double true_resid;     /* |b - A x| / |b| recomputed in FP64 on the full system  */
+  double seconds;        /* wall time of the whole qcd_solve call                  */
+} qcd_solve_info;
+
+typedef struct qcd_gauge qcd_gauge;
+
+/* Load a gauge field (Sec. II A: links U_mu(x) in SU(3)).
+ * U: canonical complex128 (4, V, 3, 3), device or host.  The library keeps
+ * even-odd reordered copies in FP64 (18 reals) and in FP32 and FP16 (geom->recon
+ * reals); the caller's buffer is not referenced after the call returns.
+ * Errors: QCD_ERR_ARG for a NULL pointer, odd or non-positive extents, bc not
+ * +-1, recon not 12/18, or V >= 2^31; QCD_ERR_OOM if the copies do not fit. */
+qcd_status qcd_gauge_load(const qcd_geom* geom, const void* U, void* stream, qcd_gauge** out);
+
+/* Release a handle and everything it owns (NULL is accepted).  Synchronises
+ * the device before freeing. */
+qcd_status qcd_gauge_free(qcd_gauge* g);
+
+/* Bytes of one INTERNAL single-parity buffer holding `nrhs` right-hand sides
+ * of `fermion` (Ls slices for domain-wall) in precision `prec`; 0 on invalid
+ * arguments. */
+size_t qcd_field_bytes(const qcd_geom* geom, const qcd_fermion* fermion, qcd_prec prec,
+                       int32_t nrhs);
+
+/* Convert between canonical complex128 fields and INTERNAL buffers.
+ * pack: the sites of `parity` (0 even, 1 odd) of `canon` (nrhs, [Ls,] V, 4, 3)
+ * are written to `internal` (qcd_field_bytes bytes, device memory) in `prec`
+ * (FP16: binary16 of psi/s with s the largest |component| of the site, round
+ * to nearest even).  unpack: the reverse; sites of the other parity in
+ * `canon` are left untouched.  `canon` may be host or device memory. */
+qcd_status qcd_field_pack(const qcd_gauge* g, const qcd_fermion* fermion, qcd_prec prec,
+                          int32_t parity, const void* canon, void* internal, int32_t nrhs,
+                          void* stream);
+qcd_status qcd_field_unpack(const qcd_gauge* g, const qcd_fermion* fermion, qcd_prec prec,
+                            int32_t parity, const void* internal, void* canon, int32_t nrhs,
+                            void* stream);
+
+/* Apply an operator (Eq. (1) / Eq. (2)) to `nrhs` right-hand sides at once;
+ * the links of a site are loaded once for all of them.
+ *   Wilson:      D_EO = H_eo,  D_OE = H_oe,  MHAT = 1 - kappa^2 H_eo H_oe,
+ *                MHAT_DAG = 1 - kappa^2 (H^dag)_eo (H^dag)_oe, FULL = 1 - kappa H.
+ *   Domain-wall: D_EO / D_OE = the 4D hop H on every s slice;
+ *                MHAT = 1 - 1/4 A^-1 H_eo A^-1 H_oe with A the site-local part
+ *                of Eq. (2) (diagonal 5 - M5 plus the s couplings);
+ *                MHAT_DAG = 1 - 1/4 (H^dag)_eo A^-dag (H^dag)_oe A^-dag;
+ *                FULL = D_DW of Eq. (2).
+ * layout CANON: in/out are full-lattice canonical complex128 fields (device or
+ *   host); for D_EO the odd sites of `in` are read and out is written on the
+ *   even sites and zeroed on the odd ones (D_OE: the reverse; MHAT: even to
+ *   even).  The arithmetic runs in `prec`.
+ * layout INTERNAL: in/out are single-parity device buffers in `prec` (see
+ *   qcd_field_bytes / qcd_field_pack); FULL is not available there.
+ * in and out must not overlap.  Asynchronous on device buffers. */
+qcd_status qcd_dslash(const qcd_gauge* g, const qcd_fermion* fermion, qcd_prec prec, int32_t op,
+                      const void* in, void* out, int32_t nrhs, int32_t layout, void* stream);
+
+/* Solve A x = b for nrhs right-hand sides (A = M for Wilson, D_DW for
+ * domain-wall; A^dag with params->dagger), by even-odd preconditioned
+ * BiCGStab (Wilson) or CG on Mhat^dag Mhat, then reconstruction of the odd
+ * sites.  b, x: canonical complex128, device or host.  info: host array of
+ * nrhs entries.  Returns QCD_OK when every right-hand side reached tol,
+ * QCD_ERR_NOCONV / QCD_ERR_BREAKDOWN / QCD_ERR_NAN otherwise (x then holds the
+ * last double-precision iterate). */
+qcd_status qcd_solve(const qcd_gauge* g, const qcd_fermion* fermion,
+                     const qcd_solver_params* params, const void* b, void* x, int32_t nrhs,
+                     qcd_solve_info* info, void* stream);
+
+/* Fermion force for S = phi^dag (M^dag M)^-1 phi (Wilson, full M = 1 - kappa H):
+ * given eta = M^-dag phi and X = M^-1 eta (canonical (V,4,3) complex128,
+ * device), write dS/dRe U_ab and dS/dIm U_ab for every link into dSdU
+ * ((4, V, 3, 3, 2) float64, device), treating the 18 reals of a link as
+ * independent:  dS = 2 kappa Re(eta^dag dH X).  Asynchronous. */
+qcd_status qcd_force(const qcd_gauge* g, const qcd_fermion* fermion, const void* X,
+                     const void* eta, void* dSdU, void* stream);
+
+/* Message describing the last failing call on this thread ("" if none). */
+const char* qcd_last_error(void);
+
+/* Autotuner control: mode 0 = off (default launch shapes), 1 = on (default).
+ * The tuner times candidate block / tile shapes of the stencil kernels on
+ * first use of each (kernel, lattice, precision, nrhs) key and caches the
+ * fastest; the cache is also read from and written to the file named by the
+ * environment variable QCD_TUNECACHE when set. */
+qcd_status qcd_set_tuning(int32_t mode);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCD_H */

@@ -1,0 +1,158 @@
+// Site-local part of the domain-wall matrix (Eq. (2)) and its inverse.
+//
+// Writing D_DW = A - H/2 with H the 4D Wilson hop acting identically on every
+// slice s, the block A couples (s, spin) at one 4D site:
+//   (A psi)_s = (5 - M5) psi_s - P_- psi_{s+1} - P_+ psi_{s-1}
+//             + m P_+ psi_{Ls-1} [s = 0] + m P_- psi_0 [s = Ls-1]
+// With gamma_5 = diag(1,1,-1,-1) the projectors P_+- select spins {0,1} and
+// {2,3}.  On the P_+ spins A = a - (lower shift with wrap factor -m), on the
+// P_- spins A = a - (upper shift with the same wrap), a = 5 - M5.  The
+// inverse of a I - (twisted lower shift) has the closed form
+//   (A_+^-1)_{s,s'} = a^(-1-k) * (s >= s' ? 1 : -m) / (1 + m a^-Ls),
+//   k = (s - s') mod Ls,
+// and A_-^-1 is its transpose (as is A_+^-dag; A is real).  Both are applied
+// at every site, colour and spin with Ls real coefficients per output.
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace qcd {
+
+namespace {
+
+constexpr int kMaxLs = 64;
+
+struct AinvCoef {
+  int Ls;
+  double apow[kMaxLs];  // a^(-1-k) / (1 + m a^-Ls)
+  double mf;
+};
+
+// block: (32 sites) x (ls slices); grid: (ceil(Vh/32), nrhs)
+template <typename R>
+__global__ void k_ainv(AinvCoef c, AnyView in, AnyView out, long Vh, int dagger, R scale,
+                       AnyView x, int has_x, const int* stop) {
+  if (stop && *stop) return;
+  int r = blockIdx.y;
+  long cb = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int s = threadIdx.y;
+  if (cb >= Vh) return;
+  const int Ls = c.Ls;
+  Cx<R> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
+  for (int sp = 0; sp < Ls; ++sp) {
+    Cx<R> v[12];
+    any_load<R>(in, r, (long)sp * Vh + cb, v);
+    // coefficient for the lower-shift (P_+) inverse at (s, sp) and its transpose
+    int k1 = s - sp;
+    if (k1 < 0) k1 += Ls;
+    R lo = (R)(c.apow[k1] * (s >= sp ? 1.0 : -c.mf));
+    int k2 = sp - s;
+    if (k2 < 0) k2 += Ls;
+    R up = (R)(c.apow[k2] * (sp >= s ? 1.0 : -c.mf));
+    R cp = dagger ? up : lo;  // spins 0,1
+    R cm = dagger ? lo : up;  // spins 2,3
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = {fma(cp, v[k].re, acc[k].re), fma(cp, v[k].im, acc[k].im)};
+#pragma unroll
+    for (int k = 6; k < 12; ++k) acc[k] = {fma(cm, v[k].re, acc[k].re), fma(cm, v[k].im, acc[k].im)};
+  }
+  if (has_x) {
+    Cx<R> w[12];
+    any_load<R>(x, r, (long)s * Vh + cb, w);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {fma(scale, acc[k].re, w[k].re), fma(scale, acc[k].im, w[k].im)};
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {scale * acc[k].re, scale * acc[k].im};
+  }
+  any_store<R>(out, r, (long)s * Vh + cb, acc);
+}
+
+// out = A in + c * y  (A^dag for dagger)
+template <typename R>
+__global__ void k_ablock(int Ls, R a, R mf, AnyView in, AnyView out, R cy, AnyView y, int has_y,
+                         long Vh, int dagger) {
+  int r = blockIdx.y;
+  long cb = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int s = threadIdx.y;
+  if (cb >= Vh) return;
+  Cx<R> v[12], lo[12], up[12];
+  any_load<R>(in, r, (long)s * Vh + cb, v);
+  int sm = s == 0 ? Ls - 1 : s - 1;
+  int spl = s == Ls - 1 ? 0 : s + 1;
+  any_load<R>(in, r, (long)sm * Vh + cb, lo);   // psi_{s-1}
+  any_load<R>(in, r, (long)spl * Vh + cb, up);  // psi_{s+1}
+  // coefficient of psi_{s-1} (lower shift) and psi_{s+1} (upper shift)
+  R flo = (s == 0) ? mf : R(-1);
+  R fup = (s == Ls - 1) ? mf : R(-1);
+  // A: P_+ spins use the lower shift, P_- spins the upper; A^dag swaps them
+  R cp_lo = dagger ? R(0) : flo, cp_up = dagger ? fup : R(0);
+  R cm_lo = dagger ? flo : R(0), cm_up = dagger ? R(0) : fup;
+  Cx<R> o[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    R clo = k < 6 ? cp_lo : cm_lo;
+    R cup = k < 6 ? cp_up : cm_up;
+    o[k].re = a * v[k].re + clo * lo[k].re + cup * up[k].re;
+    o[k].im = a * v[k].im + clo * lo[k].im + cup * up[k].im;
+  }
+  if (has_y) {
+    Cx<R> w[12];
+    any_load<R>(y, r, (long)s * Vh + cb, w);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = {fma(cy, w[k].re, o[k].re), fma(cy, w[k].im, o[k].im)};
+  }
+  any_store<R>(out, r, (long)s * Vh + cb, o);
+}
+
+dim3 block_for(int Ls) {
+  int bx = 32;
+  while (bx * Ls > 1024 && bx > 1) bx /= 2;
+  return dim3(bx, Ls);
+}
+
+}  // namespace
+
+void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double scale,
+             const Field* x, cudaStream_t st, const int* stop) {
+  if (p.Ls < 1 || p.Ls > kMaxLs) raise(QCD_ERR_ARG, "Ls must be in [1, %d]", kMaxLs);
+  if (in.data == out.data || (x && x->data == out.data))
+    raise(QCD_ERR_ARG, "dw_ainv: output aliases an input");
+  AnyView xv = x ? any_view(*x) : any_view(out);
+  AinvCoef c;
+  c.Ls = p.Ls;
+  c.mf = p.mf;
+  double a = 5.0 - p.M5;
+  double den = 1.0 + p.mf * std::pow(a, -p.Ls);
+  for (int k = 0; k < p.Ls; ++k) c.apow[k] = std::pow(a, -1.0 - k) / den;
+  dim3 blk = block_for(p.Ls);
+  dim3 grid((unsigned)((in.Vh + blk.x - 1) / blk.x), in.nrhs);
+  if (in.prec == QCD_F64 || out.prec == QCD_F64)
+    k_ainv<double><<<grid, blk, 0, st>>>(c, any_view(in), any_view(out), in.Vh, dagger, scale, xv,
+                                         x != nullptr, stop);
+  else
+    k_ainv<float><<<grid, blk, 0, st>>>(c, any_view(in), any_view(out), in.Vh, dagger, (float)scale,
+                                        xv, x != nullptr, stop);
+  QCD_LAUNCH_CK();
+}
+
+void dw_block(const DwParams& p, const Field& in, Field& out, int dagger, double c, const Field* y,
+              cudaStream_t st) {
+  if (in.data == out.data) raise(QCD_ERR_ARG, "dw_block: in and out alias");
+  dim3 blk = block_for(p.Ls);
+  dim3 grid((unsigned)((in.Vh + blk.x - 1) / blk.x), in.nrhs);
+  AnyView yv = y ? any_view(*y) : any_view(out);
+  double a = 5.0 - p.M5;
+  if (in.prec == QCD_F64 || out.prec == QCD_F64)
+    k_ablock<double><<<grid, blk, 0, st>>>(p.Ls, a, p.mf, any_view(in), any_view(out), c, yv,
+                                           y != nullptr, in.Vh, dagger);
+  else
+    k_ablock<float><<<grid, blk, 0, st>>>(p.Ls, (float)a, (float)p.mf, any_view(in), any_view(out),
+                                          (float)c, yv, y != nullptr, in.Vh, dagger);
+  QCD_LAUNCH_CK();
+}
+
+}  // namespace qcd

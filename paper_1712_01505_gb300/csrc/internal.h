@@ -1,0 +1,153 @@
+// Host-side internals of libqcd shared between translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "qcd.h"
+
+namespace qcd {
+struct AnyView;
+}
+
+namespace qcd {
+
+// ----------------------------------------------------------------------------- errors
+struct Error {
+  qcd_status status;
+  std::string msg;
+};
+
+[[noreturn]] void raise(qcd_status s, const char* fmt, ...);
+void cuda_check(cudaError_t e, const char* what, const char* file, int line);
+#define QCD_CK(call) ::qcd::cuda_check((call), #call, __FILE__, __LINE__)
+// check the last launch (a launch error leaves no sticky state)
+#define QCD_LAUNCH_CK() ::qcd::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+// ----------------------------------------------------------------------------- lattice
+struct Lattice {
+  int L[4];
+  int bc[4];
+  int recon;
+  long V, Vh;
+};
+
+// ----------------------------------------------------------------------------- fields
+// A single-parity internal vector: nrhs right-hand sides, each `ls` slices of
+// Vh sites, stored component-major (see common.cuh).
+struct Field {
+  int prec = QCD_F64;
+  void* data = nullptr;
+  float* norm = nullptr;  // FP16 only: one scale per site
+  long Vh = 0;
+  int ls = 1;
+  int nrhs = 1;
+  long nsites() const { return Vh * ls; }
+  size_t data_bytes() const;
+  size_t norm_bytes() const { return prec == QCD_F16 ? sizeof(float) * (size_t)nsites() * nrhs : 0; }
+  // view of right-hand sides [r0, r0 + n)
+  Field rhs_range(int r0, int n) const;
+};
+
+size_t spinor_site_bytes(int prec);  // bytes per site of the component arrays
+
+// ----------------------------------------------------------------------------- workspace
+struct Workspace {
+  struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+  };
+  std::map<std::string, Buf> bufs;
+  void* get(const std::string& name, size_t bytes);
+  void release();
+};
+
+}  // namespace qcd
+
+// ----------------------------------------------------------------------------- the handle
+struct qcd_gauge {
+  qcd::Lattice lat;
+  void* U64 = nullptr;  // FP64, 18 reals
+  void* U32 = nullptr;  // FP32, lat.recon reals
+  void* U16 = nullptr;  // FP16, lat.recon reals
+  qcd::Workspace ws;
+  cudaStream_t work = nullptr;  // private stream (capturable) for the solver
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int device = 0;
+};
+
+namespace qcd {
+
+// A field in the handle's workspace.
+Field ws_field(qcd_gauge* g, const std::string& name, int prec, int ls, int nrhs);
+
+// ----------------------------------------------------------------------------- layout (layout.cu)
+void gauge_reorder(qcd_gauge* g, const double* U_canon_dev, cudaStream_t st);
+// canonical complex128 (nrhs, ls, V, 4, 3) <-> internal parity field
+void pack_field(const Lattice& lat, int parity, const double* canon, Field& f, cudaStream_t st);
+void unpack_field(const Lattice& lat, int parity, const Field& f, double* canon, cudaStream_t st);
+void zero_parity_canon(const Lattice& lat, int parity, double* canon, int nvec, cudaStream_t st);
+
+// ----------------------------------------------------------------------------- stencils (wilson.cu)
+// out = a * H_{p,1-p} in           (x == nullptr)
+// out = x + a * H_{p,1-p} in       (x != nullptr)
+// with H -> H^dag for dagger; all slices (ls) and right-hand sides of `in`.
+// `stop` (device int, may be null): the kernel does nothing when *stop != 0
+// (used by the solver's captured iteration chunks).
+void hop(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int dagger, double a,
+         const Field* x, cudaStream_t st, const int* stop = nullptr);
+
+// ----------------------------------------------------------------------------- domain wall (dwf.cu)
+struct DwParams {
+  int Ls;
+  double M5, mf;
+};
+// out = [x +] c * A^-1 in (A^-dag for dagger), per site over (s, spin)
+void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double c, const Field* x,
+             cudaStream_t st, const int* stop = nullptr);
+// out = A in + c * y  (y may be null), A^dag for dagger
+void dw_block(const DwParams& p, const Field& in, Field& out, int dagger, double c, const Field* y,
+              cudaStream_t st);
+
+// ----------------------------------------------------------------------------- BLAS (blas.cu)
+void blas_zero(Field& f, cudaStream_t st);
+void blas_copy(const Field& src, Field& dst, cudaStream_t st);  // any precision -> any
+// y = a*x + b*y (real host scalars), any precisions
+void blas_axpby(double a, const Field& x, double b, Field& y, cudaStream_t st);
+// per right-hand side |x|^2 into host array (synchronises st)
+void blas_norm2(const Field& x, double* out_host, cudaStream_t st, qcd_gauge* g);
+
+// ----------------------------------------------------------------------------- operators (ops.cu)
+struct OpCtx {
+  qcd_gauge* g;
+  qcd_fermion f;
+  int prec;
+};
+// Schur operator on even sites: out = Mhat in (dagger: Mhat^dag); uses workspace temporaries
+void apply_mhat(const OpCtx& c, const Field& in, Field& out, int dagger, cudaStream_t st,
+                const char* tag, const int* stop = nullptr);
+// out_p = in_p - kappa H in_other (Wilson) or A in_p - 1/2 H in_other (DWF), parity p
+void apply_full_parity(const OpCtx& c, const Field& in_same, const Field& in_other, Field& out,
+                       int parity, int dagger, cudaStream_t st, const char* tag);
+AnyView any_view(const Field& f);
+
+// ----------------------------------------------------------------------------- tuner (tune.cu)
+struct LaunchCfg {
+  int block;  // threads per block
+  int tile;   // right-hand sides / slices per thread
+};
+bool tuning_enabled();
+void set_tuning(int mode);
+// candidates are tried with `run` (which must be idempotent) when the key is
+// new and the stream is not capturing; returns the cached or chosen config.
+LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
+               void (*run)(void* ctx, const LaunchCfg& cfg), void* ctx, cudaStream_t st);
+
+// device properties
+int sm_count();
+
+}  // namespace qcd

@@ -1,0 +1,59 @@
+// Composite operators built from the stencil and the site-local kernels:
+// the even-odd Schur operators of the Wilson and domain-wall matrices and the
+// unpreconditioned matrices on a pair of parity fields.
+//
+// Wilson (M = 1 - kappa H, Eq. (1) in hopping form):
+//   Mhat     = 1 - kappa^2 H_eo H_oe
+//   Mhat^dag = 1 - kappa^2 (H^dag)_eo (H^dag)_oe
+// Domain-wall (D = A - H/2, Eq. (2); A site-local, see dwf.cu):
+//   Mhat     = 1 - 1/4 A^-1 H_eo A^-1 H_oe
+//   Mhat^dag = 1 - 1/4 (H^dag)_eo A^-dag (H^dag)_oe A^-dag
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace qcd {
+
+void apply_mhat(const OpCtx& c, const Field& in, Field& out, int dagger, cudaStream_t st,
+                const char* tag, const int* stop) {
+  std::string t = tag;
+  if (c.f.type == QCD_WILSON) {
+    Field tmp = ws_field(c.g, t + ".mhat.t", c.prec, in.ls, in.nrhs);
+    const double k2 = c.f.kappa * c.f.kappa;
+    hop(c.g, in, tmp, 1, dagger, 1.0, nullptr, st, stop);
+    hop(c.g, tmp, out, 0, dagger, -k2, &in, st, stop);
+    return;
+  }
+  DwParams p{c.f.Ls, c.f.M5, c.f.mf};
+  Field t1 = ws_field(c.g, t + ".mhat.t1", c.prec, in.ls, in.nrhs);
+  Field t2 = ws_field(c.g, t + ".mhat.t2", c.prec, in.ls, in.nrhs);
+  if (!dagger) {
+    hop(c.g, in, t1, 1, 0, 1.0, nullptr, st, stop);       // H_oe in
+    dw_ainv(p, t1, t2, 0, 1.0, nullptr, st, stop);        // A^-1 H_oe in
+    hop(c.g, t2, t1, 0, 0, 1.0, nullptr, st, stop);       // H_eo A^-1 H_oe in
+    dw_ainv(p, t1, out, 0, -0.25, &in, st, stop);         // in - 1/4 A^-1 (...)
+  } else {
+    dw_ainv(p, in, t1, 1, 1.0, nullptr, st, stop);        // A^-dag in
+    hop(c.g, t1, t2, 1, 1, 1.0, nullptr, st, stop);       // (H^dag)_oe
+    dw_ainv(p, t2, t1, 1, 1.0, nullptr, st, stop);        // A^-dag
+    hop(c.g, t1, out, 0, 1, -0.25, &in, st, stop);        // in - 1/4 (H^dag)_eo (...)
+  }
+}
+
+// out_p = A_full restricted to output parity p, applied to (in_e, in_o):
+//   Wilson:  out_p = in_p - kappa H_{p,1-p} in_{1-p}
+//   DWF:     out_p = A in_p - 1/2 H_{p,1-p} in_{1-p}
+void apply_full_parity(const OpCtx& c, const Field& in_same, const Field& in_other, Field& out,
+                       int parity, int dagger, cudaStream_t st, const char* tag) {
+  if (c.f.type == QCD_WILSON) {
+    hop(c.g, in_other, out, parity, dagger, -c.f.kappa, &in_same, st);
+    return;
+  }
+  DwParams p{c.f.Ls, c.f.M5, c.f.mf};
+  Field t = ws_field(c.g, std::string(tag) + ".full.t", c.prec, in_same.ls, in_same.nrhs);
+  hop(c.g, in_other, t, parity, dagger, 1.0, nullptr, st);
+  dw_block(p, in_same, out, dagger, -0.5, &t, st);
+}
+
+}  // namespace qcd

@@ -1,0 +1,303 @@
+// Wilson hopping stencil (Eq. (1)) on one parity of the even-odd lattice:
+//
+//   out(x) = [x(x) +] a * sum_mu [ (1 - gamma_mu) U_mu(x) in(x+mu)
+//                                + (1 + gamma_mu) U_mu(x-mu)^dag in(x-mu) ]
+//
+// for x of the output parity (the neighbours are all of the other parity).
+// With `dagger` the projectors are exchanged, which gives H^dag.  The same
+// kernel serves the domain-wall operator (the 4D hop acts identically on every
+// fifth-dimension slice, Sec. II B 2) and several right-hand sides: a thread
+// owns one output site and a tile of TILE slices, loads each link once and
+// applies it to all slices of its tile (the links are "common in the 5th
+// direction").
+//
+// Spin structure: in the chiral basis gamma_mu = [[0, B],[B^dag, 0]] with
+// B_x = -i sigma_1, B_y = -i sigma_2, B_z = -i sigma_3, B_t = 1.  For a spinor
+// (u, l) (upper / lower spin pairs) and sg = -1 for (1 - gamma), +1 for
+// (1 + gamma):  (1 + sg gamma)(u, l) = (h, sg B^dag h) with h = u + sg B l.
+// Only the half spinor h is multiplied by the link: 2 x 66 flops instead of
+// 4 x 66.  Per output site and slice: 8 x (12 projection + 132 link) + 7 x 24
+// accumulation = 1320 flops.
+#include <cstdio>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace qcd {
+
+namespace {
+
+template <typename R>
+__device__ __forceinline__ Cx<R> fmac(R s, Cx<R> a, Cx<R> b) {  // b + s*a
+  return {fma(s, a.re, b.re), fma(s, a.im, b.im)};
+}
+
+// h = u + sg * B l  (2 spins x 3 colours)
+template <int MU, typename R>
+__device__ __forceinline__ void project(const Cx<R> psi[12], R sg, Cx<R> h[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Cx<R> b0, b1;
+    apply_B<MU>(psi[6 + c], psi[9 + c], b0, b1);
+    h[c] = fmac(sg, b0, psi[c]);
+    h[3 + c] = fmac(sg, b1, psi[3 + c]);
+  }
+}
+
+// acc += (g, sg B^dag g)
+template <int MU, typename R>
+__device__ __forceinline__ void reconstruct_add(const Cx<R> g[6], R sg, Cx<R> acc[12]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Cx<R> b0, b1;
+    apply_Bdag<MU>(g[c], g[3 + c], b0, b1);
+    acc[c] = acc[c] + g[c];
+    acc[3 + c] = acc[3 + c] + g[3 + c];
+    acc[6 + c] = fmac(sg, b0, acc[6 + c]);
+    acc[9 + c] = fmac(sg, b1, acc[9 + c]);
+  }
+}
+
+// g = U h (dag = false) or U^dag h (dag = true), for both spins of h
+template <bool DAG, typename R>
+__device__ __forceinline__ void link_mul(const Cx<R> U[9], const Cx<R> h[6], Cx<R> g[6]) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Cx<R> acc = {R(0), R(0)};
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (DAG)
+          acc = cjmadd(U[b * 3 + a], h[sp * 3 + b], acc);
+        else
+          acc = cmadd(U[a * 3 + b], h[sp * 3 + b], acc);
+      }
+      g[sp * 3 + a] = acc;
+    }
+}
+
+template <int P, int RECON>
+struct HopArgs {
+  Geom g;
+  int out_parity;
+  int ls;        // slices per right-hand side
+  int nslices;   // ls * nrhs
+  int ntiles;    // ceil(nslices / TILE)
+  int dagger;
+  int xpay;
+  double a;
+  LinkView<P, RECON> U;
+  SpinorView<P> in, out, x;
+  const int* stop;
+};
+
+template <int P, int RECON, int TILE, int MU>
+__device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCoords& c, int cb,
+                                        int q0, typename MathType<P>::type sg,
+                                        Cx<typename MathType<P>::type> acc[TILE][12]) {
+  using R = typename MathType<P>::type;
+  const Geom& g = A.g;
+  // forward: (1 + sg gamma) U_mu(x) in(x + mu)
+  {
+    int wrap;
+    int j = neighbour_index(g, c, MU, +1, &wrap);
+    long ncb = j >> 1;
+    bool neg = wrap && g.apbc[MU];
+    Cx<R> U[9];
+    A.U.load(A.out_parity, MU, cb, U);
+#pragma unroll
+    for (int t = 0; t < TILE; ++t) {
+      int q = q0 + t;
+      if (TILE > 1 && q >= A.nslices) break;
+      int r = q / A.ls, s = q - r * A.ls;
+      Cx<R> psi[12], h[6], gg[6];
+      A.in.offset_rhs(r).load((long)s * g.Vh + ncb, psi);
+      project<MU>(psi, sg, h);
+      if (neg)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) h[k] = -h[k];
+      link_mul<false>(U, h, gg);
+      reconstruct_add<MU>(gg, sg, acc[t]);
+    }
+  }
+  // backward: (1 - sg gamma) U_mu(x - mu)^dag in(x - mu)
+  {
+    int wrap;
+    int j = neighbour_index(g, c, MU, -1, &wrap);
+    long ncb = j >> 1;
+    bool neg = wrap && g.apbc[MU];
+    Cx<R> U[9];
+    A.U.load(1 - A.out_parity, MU, ncb, U);
+#pragma unroll
+    for (int t = 0; t < TILE; ++t) {
+      int q = q0 + t;
+      if (TILE > 1 && q >= A.nslices) break;
+      int r = q / A.ls, s = q - r * A.ls;
+      Cx<R> psi[12], h[6], gg[6];
+      A.in.offset_rhs(r).load((long)s * g.Vh + ncb, psi);
+      project<MU>(psi, -sg, h);
+      if (neg)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) h[k] = -h[k];
+      link_mul<true>(U, h, gg);
+      reconstruct_add<MU>(gg, -sg, acc[t]);
+    }
+  }
+}
+
+template <int P, int RECON, int TILE>
+__global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
+  using R = typename MathType<P>::type;
+  if (A.stop && *A.stop) return;
+  // block -> (site block, slice tile), tiles of one site block adjacent in
+  // launch order so that they read the same links at about the same time
+  int tile = blockIdx.x % A.ntiles;
+  int sblock = blockIdx.x / A.ntiles;
+  int cb = sblock * blockDim.x + threadIdx.x;
+  if (cb >= A.g.Vh) return;
+  int q0 = tile * TILE;
+  SiteCoords c = cb_to_site(A.g, cb, A.out_parity);
+  Cx<R> acc[TILE][12];
+#pragma unroll
+  for (int t = 0; t < TILE; ++t)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[t][k] = {R(0), R(0)};
+  const R sg = A.dagger ? R(1) : R(-1);
+  hop_dir<P, RECON, TILE, 0>(A, c, cb, q0, sg, acc);
+  hop_dir<P, RECON, TILE, 1>(A, c, cb, q0, sg, acc);
+  hop_dir<P, RECON, TILE, 2>(A, c, cb, q0, sg, acc);
+  hop_dir<P, RECON, TILE, 3>(A, c, cb, q0, sg, acc);
+  const R a = (R)A.a;
+#pragma unroll
+  for (int t = 0; t < TILE; ++t) {
+    int q = q0 + t;
+    if (TILE > 1 && q >= A.nslices) break;
+    int r = q / A.ls, s = q - r * A.ls;
+    long site = (long)s * A.g.Vh + cb;
+    Cx<R> o[12];
+    if (A.xpay) {
+      A.x.offset_rhs(r).load(site, o);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) o[k] = fmac(a, acc[t][k], o[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) o[k] = a * acc[t][k];
+    }
+    A.out.offset_rhs(r).store(site, o);
+  }
+}
+
+Geom dev_geom(const Lattice& lat) {
+  Geom g;
+  for (int m = 0; m < 4; ++m) {
+    g.L[m] = lat.L[m];
+    g.apbc[m] = lat.bc[m] < 0;
+  }
+  g.V = (int)lat.V;
+  g.Vh = (int)lat.Vh;
+  return g;
+}
+
+template <int P>
+SpinorView<P> sview(const Field& f) {
+  SpinorView<P> v;
+  using T = decltype(v.p);
+  v.p = (T)f.data;
+  v.norm = f.norm;
+  v.stride = f.nsites();
+  return v;
+}
+
+template <int P, int RECON>
+struct HopLaunch {
+  HopArgs<P, RECON> args;
+  cudaStream_t st;
+};
+
+template <int P, int RECON, int TILE>
+void launch_tile(HopLaunch<P, RECON>* L, int block) {
+  HopArgs<P, RECON> A = L->args;
+  A.ntiles = (A.nslices + TILE - 1) / TILE;
+  long sblocks = (A.g.Vh + block - 1) / block;
+  k_hop<P, RECON, TILE><<<(unsigned)(sblocks * A.ntiles), block, 0, L->st>>>(A);
+}
+
+template <int P, int RECON>
+void run_cfg(void* ctx, const LaunchCfg& cfg) {
+  auto* L = (HopLaunch<P, RECON>*)ctx;
+  if constexpr (P == P64) {
+    launch_tile<P, RECON, 1>(L, cfg.block);
+  } else {
+    switch (cfg.tile) {
+      case 1: launch_tile<P, RECON, 1>(L, cfg.block); break;
+      case 2: launch_tile<P, RECON, 2>(L, cfg.block); break;
+      default: launch_tile<P, RECON, 4>(L, cfg.block); break;
+    }
+  }
+}
+
+template <int P, int RECON>
+void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& out, int out_parity,
+              int dagger, double a, const Field* x, cudaStream_t st, const int* stop) {
+  HopLaunch<P, RECON> L;
+  HopArgs<P, RECON>& A = L.args;
+  A.g = dev_geom(gh->lat);
+  A.out_parity = out_parity;
+  A.ls = in.ls;
+  A.nslices = in.ls * in.nrhs;
+  A.dagger = dagger;
+  A.xpay = x != nullptr;
+  A.a = a;
+  A.U.p = (decltype(A.U.p))links;
+  A.U.Vh = gh->lat.Vh;
+  A.in = sview<P>(in);
+  A.out = sview<P>(out);
+  A.x = x ? sview<P>(*x) : sview<P>(out);
+  A.stop = stop;
+  L.st = st;
+  std::vector<LaunchCfg> cands;
+  const int blocks[] = {64, 128, 256};
+  const int tiles[] = {1, 2, 4};
+  for (int t : tiles) {
+    if (P == P64 && t > 1) continue;  // register budget: one slice per thread in FP64
+    if (t > 1 && A.nslices < t) continue;
+    for (int b : blocks) cands.push_back({b, t});
+  }
+  char key[160];
+  snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d", P, RECON, gh->lat.L[0],
+           gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay);
+  LaunchCfg cfg = tune(key, cands, &run_cfg<P, RECON>, &L, st);
+  run_cfg<P, RECON>(&L, cfg);
+  QCD_LAUNCH_CK();
+}
+
+}  // namespace
+
+void hop(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int dagger, double a,
+         const Field* x, cudaStream_t st, const int* stop) {
+  if (in.prec != out.prec || (x && x->prec != out.prec))
+    raise(QCD_ERR_ARG, "hop: mixed precisions are not supported");
+  if (in.data == out.data || (x && x->data == out.data))
+    raise(QCD_ERR_ARG, "hop: output aliases an input");
+  if (in.Vh == 0 || in.nrhs * in.ls == 0) return;
+  switch (in.prec) {
+    case QCD_F64:
+      hop_impl<P64, 18>(g, g->U64, in, out, out_parity, dagger, a, x, st, stop);
+      break;
+    case QCD_F32:
+      if (g->lat.recon == 12)
+        hop_impl<P32, 12>(g, g->U32, in, out, out_parity, dagger, a, x, st, stop);
+      else
+        hop_impl<P32, 18>(g, g->U32, in, out, out_parity, dagger, a, x, st, stop);
+      break;
+    default:
+      if (g->lat.recon == 12)
+        hop_impl<P16, 12>(g, g->U16, in, out, out_parity, dagger, a, x, st, stop);
+      else
+        hop_impl<P16, 18>(g, g->U16, in, out, out_parity, dagger, a, x, st, stop);
+  }
+}
+
+}  // namespace qcd

@@ -1,0 +1,71 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports every
+symbol include/qcd.h declares, the binding mirrors the header's structs, and the
+host-side argument validation works without touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1712_01505_gb300 import qcd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qcd.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1712_01505_gb300 import build
+
+    build.build()
+    return qcd.load_library()
+
+
+def header_functions():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:qcd_status|size_t|const char\*)\s+(qcd_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_binding_symbols():
+    assert header_functions() == sorted(qcd.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_header():
+    # field order and C types of the ABI structs (offsets as a C compiler lays them out)
+    assert ctypes.sizeof(qcd.Geom) == 36
+    assert qcd.Fermion.kappa.offset == 8 and qcd.Fermion.Ls.offset == 16 and qcd.Fermion.mf.offset == 32
+    assert qcd.SolverParams.tol.offset == 8 and qcd.SolverParams.delta.offset == 24
+    assert ctypes.sizeof(qcd.SolveInfo) == 32
+
+
+def test_field_bytes_host_validation(lib):
+    g = qcd.Geom((ctypes.c_int32 * 4)(4, 4, 4, 8), (ctypes.c_int32 * 4)(1, 1, 1, -1), 18)
+    f = qcd.wilson(0.12)
+    Vh = 4 * 4 * 4 * 8 // 2
+    assert lib.qcd_field_bytes(ctypes.byref(g), ctypes.byref(f), qcd.F32, 1) == Vh * 96
+    assert lib.qcd_field_bytes(ctypes.byref(g), ctypes.byref(f), qcd.F64, 2) == 2 * Vh * 192
+    assert lib.qcd_field_bytes(ctypes.byref(g), ctypes.byref(f), qcd.F16, 1) == Vh * (48 + 4)
+    d = qcd.dwf(8, 1.8, 0.02)
+    assert lib.qcd_field_bytes(ctypes.byref(g), ctypes.byref(d), qcd.F32, 1) == 8 * Vh * 96
+    bad = qcd.Geom((ctypes.c_int32 * 4)(4, 3, 4, 8), (ctypes.c_int32 * 4)(1, 1, 1, -1), 18)
+    assert lib.qcd_field_bytes(ctypes.byref(bad), ctypes.byref(f), qcd.F32, 1) == 0
+    assert "even" in lib.qcd_last_error().decode()
+    badf = qcd.wilson(-1.0)
+    assert lib.qcd_field_bytes(ctypes.byref(g), ctypes.byref(badf), qcd.F32, 1) == 0
+
+
+def test_gauge_load_rejects_bad_geometry_before_any_launch(lib):
+    h = ctypes.c_void_p()
+    g = qcd.Geom((ctypes.c_int32 * 4)(4, 4, 4, 8), (ctypes.c_int32 * 4)(1, 1, 1, 2), 18)
+    st = lib.qcd_gauge_load(ctypes.byref(g), ctypes.c_void_p(1), None, ctypes.byref(h))
+    assert st == qcd.ERR_ARG and "bc" in lib.qcd_last_error().decode()
+    g = qcd.Geom((ctypes.c_int32 * 4)(4, 4, 4, 8), (ctypes.c_int32 * 4)(1, 1, 1, -1), 10)
+    assert lib.qcd_gauge_load(ctypes.byref(g), ctypes.c_void_p(1), None, ctypes.byref(h)) == qcd.ERR_ARG
+    assert lib.qcd_gauge_load(None, ctypes.c_void_p(1), None, ctypes.byref(h)) == qcd.ERR_ARG
+    assert lib.qcd_gauge_free(None) == qcd.OK
+    assert lib.qcd_set_tuning(3) == qcd.ERR_ARG

@@ -1,0 +1,103 @@
+"""GPU solves (Sec. II C) against the FP64 oracle: every solution must satisfy
+|b - A x| / |b| <= 1e-10 with A applied by the ORACLE's full operator, and agree with
+the oracle's own solution to within the conditioning of the system."""
+import numpy as np
+import pytest
+
+from oracle import oracle as ora
+from paper_1712_01505_gb300 import inputs, qcd
+from tests.gpu_util import device, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+BC = (1, 1, 1, -1)
+
+
+def oracle_resid_wilson(L, kappa, U, b, x, dagger=False):
+    return np.linalg.norm(b - ora.wilson(L, BC, kappa, U, x, dagger=dagger)) / np.linalg.norm(b)
+
+
+def test_config1_wilson_4x4x4x4_fp64_bicgstab():
+    """4^4, eps = 0.3 links (seed 1), kappa = 0.12, Gaussian source (seed 0), FP64 EO BiCGStab to 1e-10."""
+    device()
+    L, kappa = (4, 4, 4, 4), 0.12
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.3, 1)
+    b = inputs.gaussian_source((V, 4, 3), 0)
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    f = qcd.wilson(kappa)
+    x = torch.zeros((V, 4, 3), dtype=torch.complex128, device=device())
+    info, _ = qcd.solve(g, f, to_dev(b), x, method=qcd.BICGSTAB, tol=1e-10, inner="f64")
+    xr = x.cpu().numpy()
+    assert info[0]["converged"] and info[0]["true_resid"] <= 1e-10
+    assert oracle_resid_wilson(L, kappa, U, b, xr) <= 1e-10
+    xo, _, res_o = ora.wilson_solve(L, BC, kappa, U, b, tol=1e-12)
+    assert np.linalg.norm(xr - xo) / np.linalg.norm(xo) < 1e-8
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("graph", [False, True])
+def test_wilson_mixed_precision_reaches_1e10(inner, graph):
+    device()
+    L, kappa = (8, 8, 8, 8), 0.124
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.3, 4)
+    b = inputs.z2_source((V, 4, 3), 0)
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=12)
+    f = qcd.wilson(kappa)
+    x = torch.zeros((V, 4, 3), dtype=torch.complex128, device=device())
+    info, _ = qcd.solve(g, f, to_dev(b), x, method=qcd.BICGSTAB, tol=1e-10, inner=inner,
+                        use_graph=graph, graph_chunk=16)
+    assert info[0]["converged"], info
+    assert oracle_resid_wilson(L, kappa, U, b, x.cpu().numpy()) <= 1e-10
+    if inner != "f64":
+        assert info[0]["outer_updates"] >= 2
+
+
+def test_wilson_dagger_solve_and_warm_start():
+    device()
+    L, kappa = (4, 4, 6, 8), 0.12
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.3, 5)
+    b = inputs.gaussian_source((V, 4, 3), 6)
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    f = qcd.wilson(kappa)
+    x = torch.zeros((V, 4, 3), dtype=torch.complex128, device=device())
+    info, _ = qcd.solve(g, f, to_dev(b), x, tol=1e-11, inner="f32", dagger=True)
+    assert oracle_resid_wilson(L, kappa, U, b, x.cpu().numpy(), dagger=True) <= 1e-11
+    # warm start from the converged solution: no inner iterations are needed
+    info2, _ = qcd.solve(g, f, to_dev(b), x, tol=1e-10, inner="f32", dagger=True, x0_given=True)
+    assert info2[0]["iters"] == 0 and info2[0]["converged"]
+
+
+def test_wilson_multi_rhs_point_sources():
+    """The 12 spin-colour point sources at one site, solved together (per-rhs scalars)."""
+    device()
+    L, kappa = (4, 4, 4, 8), 0.124
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.2, 4)
+    x0, b = inputs.point_sources(L, 0)
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=12)
+    f = qcd.wilson(kappa)
+    x = torch.zeros((12, V, 4, 3), dtype=torch.complex128, device=device())
+    info, _ = qcd.solve(g, f, to_dev(b), x, nrhs=12, tol=1e-10, inner="f32", use_graph=True, graph_chunk=8)
+    xr = x.cpu().numpy()
+    for k in range(12):
+        assert info[k]["converged"]
+        assert oracle_resid_wilson(L, kappa, U, b[k], xr[k]) <= 1e-10
+
+
+def test_solver_reports_noconv_with_best_iterate():
+    device()
+    L, kappa = (4, 4, 4, 8), 0.124
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.3, 8)
+    b = inputs.gaussian_source((V, 4, 3), 9)
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    f = qcd.wilson(kappa)
+    x = torch.zeros((V, 4, 3), dtype=torch.complex128, device=device())
+    info, st = qcd.solve(g, f, to_dev(b), x, tol=1e-12, maxiter=3, inner="f32", check=False)
+    assert st == qcd.ERR_NOCONV
+    assert not info[0]["converged"] and info[0]["iters"] <= 3
+    r = oracle_resid_wilson(L, kappa, U, b, x.cpu().numpy())
+    assert r < 1.0 and abs(r - info[0]["true_resid"]) < 1e-6 * max(r, 1e-30)

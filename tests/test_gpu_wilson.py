@@ -1,0 +1,223 @@
+"""GPU parity of the Wilson operators (Eq. (1)) and layouts against the FP64 oracle.
+
+All calls go through the C ABI (paper_1712_01505_gb300.qcd -> libqcd.so).
+Tolerances: FP64 element-wise 1e-13 of the largest output; FP32 1e-6 norm-wise
+(operator apply, single precision); FP16 storage 2e-3 norm-wise.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as ora
+from paper_1712_01505_gb300 import inputs, qcd
+from tests.gpu_util import device, max_err, rel_err, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+BC = (1, 1, 1, -1)
+TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 2e-3}
+# 4^4: one tile; 6x4x6x10: Vh = 720, several blocks and a ragged tail; 2x2x2x2: the degenerate
+# case where x+mu and x-mu coincide in every direction
+LATTICES = [(4, 4, 4, 4), (6, 4, 6, 10), (2, 2, 2, 2)]
+
+
+def _case(L, seed=3, eps=0.4, nrhs=1):
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, eps, seed)
+    psi = inputs.gaussian_source((nrhs, V, 4, 3) if nrhs > 1 else (V, 4, 3), seed + 100)
+    return V, U, psi
+
+
+def _check(out, ref, prec):
+    if prec == "f64":
+        assert max_err(out, ref) < TOL["f64"]
+    else:
+        assert rel_err(out, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("L", LATTICES)
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f32", 18), ("f32", 12), ("f16", 18), ("f16", 12)])
+@pytest.mark.parametrize("op", ["D_EO", "D_OE"])
+def test_hop_parity(L, prec, recon, op):
+    device()
+    V, U, psi = _case(L)
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=recon)
+    f = qcd.wilson(0.12)
+    out = torch.empty((V, 4, 3), dtype=torch.complex128, device=device())
+    qcd.dslash(g, f, op, to_dev(psi), out, prec=prec)
+    torch.cuda.synchronize()
+    po = 0 if op == "D_EO" else 1
+    par = ora.parity(L)
+    inp = psi.copy()
+    inp[par == po] = 0
+    ref = ora.hop(L, BC, U, inp, out_parity=po)
+    _check(out, ref, prec)
+    assert np.all(out.cpu().numpy()[par != po] == 0)
+
+
+@pytest.mark.parametrize("L", LATTICES[:2])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("dag", [False, True])
+def test_mhat_and_full_parity(L, prec, dag):
+    device()
+    V, U, psi = _case(L, seed=5)
+    kappa = 0.124
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=18)
+    f = qcd.wilson(kappa)
+    par = ora.parity(L)
+    pe = psi.copy()
+    pe[par == 1] = 0
+    out = torch.empty((V, 4, 3), dtype=torch.complex128, device=device())
+    qcd.dslash(g, f, "MHAT_DAG" if dag else "MHAT", to_dev(psi), out, prec=prec)
+    torch.cuda.synchronize()
+    _check(out, ora.wilson_mhat(L, BC, kappa, U, pe, dagger=dag), prec)
+    qcd.dslash(g, f, "FULL_DAG" if dag else "FULL", to_dev(psi), out, prec=prec)
+    torch.cuda.synchronize()
+    _check(out, ora.wilson(L, BC, kappa, U, psi, dagger=dag), prec)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_multi_rhs_shares_links(prec):
+    """nrhs right-hand sides in one launch equal the single-rhs oracle results."""
+    device()
+    L, nrhs = (4, 4, 6, 6), 5
+    V, U, psi = _case(L, seed=7, nrhs=nrhs)
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=12)
+    f = qcd.wilson(0.12)
+    out = torch.empty((nrhs, V, 4, 3), dtype=torch.complex128, device=device())
+    qcd.dslash(g, f, "D_EO", to_dev(psi), out, prec=prec, nrhs=nrhs)
+    torch.cuda.synchronize()
+    par = ora.parity(L)
+    for r in range(nrhs):
+        inp = psi[r].copy()
+        inp[par == 0] = 0
+        _check(out[r], ora.hop(L, BC, U, inp, out_parity=0), prec)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_pack_unpack_roundtrip(prec):
+    device()
+    L = (6, 4, 6, 10)
+    V, U, psi = _case(L, seed=9)
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    f = qcd.wilson(0.1)
+    nbytes = qcd.field_bytes(g, f, prec)
+    buf = torch.empty(nbytes, dtype=torch.uint8, device=device())
+    back = torch.zeros((V, 4, 3), dtype=torch.complex128, device=device())
+    for parity in (0, 1):
+        qcd.field_pack(g, f, prec, parity, to_dev(psi), buf)
+        qcd.field_unpack(g, f, prec, parity, buf, back)
+    torch.cuda.synchronize()
+    if prec == "f64":
+        assert np.array_equal(back.cpu().numpy(), psi)  # bit-exact
+    elif prec == "f32":
+        assert np.array_equal(back.cpu().numpy(), psi.astype(np.complex64).astype(np.complex128))
+    else:
+        assert rel_err(back, psi) < 1e-3
+
+
+def test_internal_layout_and_host_buffers():
+    """INTERNAL-layout D_EO equals the canonical path; host (numpy) buffers are staged."""
+    device()
+    L = (4, 4, 4, 8)
+    V, U, psi = _case(L, seed=11)
+    g = qcd.Gauge.load(U, L, BC, recon=12)  # host gauge buffer
+    f = qcd.wilson(0.12)
+    nb = qcd.field_bytes(g, f, "f32")
+    bin_ = torch.empty(nb, dtype=torch.uint8, device=device())
+    bout = torch.empty(nb, dtype=torch.uint8, device=device())
+    qcd.field_pack(g, f, "f32", 1, psi, bin_)  # host canonical source
+    qcd.dslash(g, f, "D_EO", bin_, bout, prec="f32", layout=qcd.INTERNAL)
+    res = np.zeros((V, 4, 3), dtype=np.complex128)
+    qcd.field_unpack(g, f, "f32", 0, bout, res)
+    par = ora.parity(L)
+    inp = psi.copy()
+    inp[par == 0] = 0
+    ref = ora.hop(L, BC, U, inp, out_parity=0)
+    assert rel_err(res, ref) < 1e-6
+    out_host = np.zeros_like(psi)
+    qcd.dslash(g, f, "D_EO", psi, out_host, prec="f64")
+    assert max_err(out_host, ref) < 1e-13
+
+
+def test_free_field_plane_wave_eigenvalue():
+    """U = 1: a plane wave u e^{ipx} is an eigenvector of M with the closed-form eigenvalue."""
+    device()
+    L = (4, 4, 4, 8)
+    V = int(np.prod(L))
+    kappa = 0.11
+    U = inputs.unit_gauge(L)
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    f = qcd.wilson(kappa)
+    n = np.array([1, 0, 2, 3])
+    p = (2 * np.pi * n + np.array([0, 0, 0, np.pi])) / np.array(L)
+    t, z, y, x = np.meshgrid(*[np.arange(l) for l in L[::-1]], indexing="ij")
+    phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t)).reshape(-1)
+    # eigenvector of sum_mu gamma_mu sin p_mu (the gammas fix the spin part, not the eigenvalue)
+    S = sum(ora.gamma(m) * np.sin(p[m]) for m in range(4))
+    w, vec = np.linalg.eigh(S)
+    for k in (0, 3):
+        psi = phase[:, None, None] * vec[:, k][None, :, None] * np.array([1.0, 0, 0])[None, None, :]
+        out = torch.empty((V, 4, 3), dtype=torch.complex128, device=device())
+        qcd.dslash(g, f, "FULL", to_dev(psi), out, prec="f64")
+        torch.cuda.synchronize()
+        lam = 1 - 2 * kappa * np.cos(p).sum() + 2j * kappa * w[k]
+        assert max_err(out, lam * psi) < 1e-13
+        qcd.dslash(g, f, "FULL", to_dev(psi), out, prec="f32")
+        torch.cuda.synchronize()
+        assert rel_err(out, lam * psi) < 1e-6
+
+
+def test_gauge_covariance_on_gpu():
+    device()
+    L = (4, 2, 4, 6)
+    V, U, psi = _case(L, seed=13)
+    Om = inputs.random_gauge_transform(V, 14)
+    Lx, Ly, Lz, Lt = L
+
+    def shift(a, mu):
+        return np.roll(a.reshape((Lt, Lz, Ly, Lx) + a.shape[1:]), -1, axis=3 - mu).reshape(a.shape)
+
+    Up = np.stack([Om @ U[m] @ np.conj(np.swapaxes(shift(Om, m), -1, -2)) for m in range(4)])
+    f = qcd.wilson(0.13)
+    out1 = torch.empty((V, 4, 3), dtype=torch.complex128, device=device())
+    out2 = torch.empty_like(out1)
+    g1 = qcd.Gauge.load(to_dev(Up), L, BC)
+    g2 = qcd.Gauge.load(to_dev(U), L, BC)
+    qcd.dslash(g1, f, "FULL", to_dev(np.einsum("xab,xsb->xsa", Om, psi)), out1, prec="f64")
+    qcd.dslash(g2, f, "FULL", to_dev(psi), out2, prec="f64")
+    torch.cuda.synchronize()
+    rot = np.einsum("xab,xsb->xsa", Om, out2.cpu().numpy())
+    assert max_err(out1, rot) < 1e-13
+
+
+def test_sampled_sites_at_32x32x32x64_fp32():
+    """Full-size config (32^3 x 64, eps = 0.2, kappa = 0.125): the FP32 INTERNAL-layout D_EO in the
+    benchmark's launch configuration, checked on sampled output sites the oracle computes one by one."""
+    device()
+    L = (32, 32, 32, 64)
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.2, 2)
+    psi = inputs.z2_source((V, 4, 3), 0)
+    par = ora.parity(L)
+    rng = np.random.default_rng(5)
+    even = np.flatnonzero(par == 0)
+    sites = np.concatenate([even[:64], even[-64:], rng.choice(even, 512, replace=False)])
+    inp = psi.copy()
+    inp[par == 0] = 0
+    ref = ora.hop_sites(L, BC, U, inp, sites)
+    for recon in (18, 12):
+        g = qcd.Gauge.load(to_dev(U), L, BC, recon=recon)
+        f = qcd.wilson(0.125)
+        nb = qcd.field_bytes(g, f, "f32")
+        bi = torch.empty(nb, dtype=torch.uint8, device=device())
+        bo = torch.empty(nb, dtype=torch.uint8, device=device())
+        qcd.field_pack(g, f, "f32", 1, to_dev(psi), bi)
+        qcd.dslash(g, f, "D_EO", bi, bo, prec="f32", layout=qcd.INTERNAL)
+        out = torch.zeros((V, 4, 3), dtype=torch.complex128, device=device())
+        qcd.field_unpack(g, f, "f32", 0, bo, out)
+        torch.cuda.synchronize()
+        got = out[torch.from_numpy(sites).to(device())].cpu().numpy()
+        assert rel_err(got, ref) < 1e-6
+        g.free()
+        del bi, bo, out
+        torch.cuda.empty_cache()
