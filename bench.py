@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark of the lattice-QCD fermion solve hot path on one GB300 (or N replicas).
+
+Workload (the paper's 32^3 x 64 Wilson lattice, Sec. V): Wilson fermion on
+32^3 x 64, smoothed-random SU(3) links (eps = 0.2, seed 2), kappa = 0.125,
+periodic space / antiperiodic time, complex Z2 noise source (seed 0); the
+FP32/FP16 link copies use 12-real reconstruction.
+
+One step = one pass of the hot path on that input:
+  1. the standalone even-odd hopping stencil D_eo in FP32 (NDSLASH launches)
+     and in FP64 (one launch), on internal-layout device buffers;
+  2. the mixed-precision even-odd BiCGStab solve (FP32 inner iterations,
+     FP64 reliable updates) to |b - M x| / |b| <= 1e-10 on the full system,
+     from canonical device buffers (source preparation, solve, reconstruction
+     and the final FP64 true residual included).
+`value` is the whole-step dslash rate: 1320 flop per output site for every
+half-dslash the step executes (standalone ones and those inside the solve),
+divided by the step's device time.  The plain FP64 GPU solve of the same
+system is timed once after the timed steps and reported beside the mixed one.
+
+--impl reference times the FP64 CPU oracle on the same workload (a bounded
+sample: the hopping term on the full lattice) on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dslash GFLOP/s & %HBM roofline; mixed vs FP64 solve time to rel. residual 1e-10"
+L = (32, 32, 32, 64)
+BC = (1, 1, 1, -1)
+EPS, GAUGE_SEED, KAPPA, SRC_SEED = 0.2, 2, 0.125, 0
+RECON = 12
+TOL = 1e-10
+NDSLASH = 10
+FLOP_SITE = 1320                       # per output site of one half-dslash (hopping term)
+BYTES_SITE_FP32 = {12: 8 * 48 + 96 + 96, 18: 8 * 72 + 96 + 96}   # compulsory: links + in + out
+BYTES_SITE_FP64 = 8 * 144 + 192 + 192
+WORKLOAD = "wilson_32x32x32x64_kappa0.125_eps0.2_z2"
+PROFILE = os.path.join(ROOT, "profiles", "wilson_dslash_fp32_32x32x32x64.md")
+KERNEL_SOURCES = ["paper_1712_01505_gb300/csrc/wilson.cu", "paper_1712_01505_gb300/csrc/common.cuh"]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 FMA throughput of a GB300 measured with a dependent-chain FMA loop over
+# all SMs (2 FP64 FMA / clock / SM at 1.99 GHz x 152 SMs): 1.20 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.20
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """dram bytes per launch of the FP32 D_eo from the committed ncu summary, if the kernel is unchanged."""
+    if not os.path.exists(PROFILE):
+        return None
+    txt = open(PROFILE).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    hsh = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    if not m or not hsh or hsh.group(1) != kernel_hash():
+        return None
+    return float(m.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(U, psi, budget_s=12.0):
+    """The FP64 oracle's hopping term D_eo on the full lattice, timed on the host cores."""
+    from oracle import oracle as ora
+
+    par = ora.parity(L)
+    inp = psi.copy()
+    inp[par == 0] = 0
+    ora.hop(L, BC, U, inp, out_parity=0)  # warm-up (page-in, thread pool)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        ora.hop(L, BC, U, inp, out_parity=0)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 50:
+            break
+    Vh = int(np.prod(L)) // 2
+    gflops = FLOP_SITE * Vh * reps / el / 1e9
+    return {"value": round(gflops, 4), "unit": "GFLOP/s", "cores": ora.num_threads(), "kind": "oracle",
+            "sample": f"{reps} oracle FP64 D_eo applications on the full 32^3x64 lattice "
+                      f"({Vh} output sites each, {el:.1f} s)"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1712_01505_gb300 import inputs
+    from oracle import oracle as ora
+
+    U = inputs.gauge_field(L, EPS, GAUGE_SEED)
+    psi = inputs.z2_source((int(np.prod(L)), 4, 3), SRC_SEED)
+    par = ora.parity(L)
+    inp = psi.copy()
+    inp[par == 0] = 0
+    Vh = int(np.prod(L)) // 2
+    for _ in range(args.warmup):
+        ora.hop(L, BC, U, inp, out_parity=0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ora.hop(L, BC, U, inp, out_parity=0)
+    el = time.perf_counter() - t0
+    val = FLOP_SITE * Vh * args.steps / el / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "lattice": list(L), "kappa": KAPPA,
+                                              "eps": EPS, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": round(val, 4), "unit": "GFLOP/s", "cores": ora.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"each step: one FP64 oracle D_eo on the full lattice ({Vh} sites)"},
+            "e2e": {"value": round(val, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-solve", action="store_true")
+    ap.add_argument("--profile", default="none", choices=["none", "dslash", "step"],
+                    help="for ncu: 'dslash' runs only the standalone FP32 D_eo launches, 'step' one step "
+                         "between cudaProfilerStart/Stop (use ncu --profile-from-start off); no JSON line")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1712_01505_gb300 import inputs, qcd
+
+    V = int(np.prod(L))
+    Vh = V // 2
+    U = inputs.gauge_field(L, EPS, GAUGE_SEED)
+    psi = inputs.z2_source((V, 4, 3), SRC_SEED)
+    g = qcd.Gauge.load(torch.from_numpy(U).to(dev), L, BC, recon=RECON)
+    f = qcd.wilson(KAPPA)
+    stream = torch.cuda.current_stream(dev)
+    b_dev = torch.from_numpy(psi).to(dev)
+    x_dev = torch.zeros_like(b_dev)
+    # internal-layout buffers for the standalone stencil
+    nb32 = qcd.field_bytes(g, f, "f32")
+    nb64 = qcd.field_bytes(g, f, "f64")
+    in32 = torch.empty(nb32, dtype=torch.uint8, device=dev)
+    out32 = torch.empty(nb32, dtype=torch.uint8, device=dev)
+    in64 = torch.empty(nb64, dtype=torch.uint8, device=dev)
+    out64 = torch.empty(nb64, dtype=torch.uint8, device=dev)
+    qcd.field_pack(g, f, "f32", 1, b_dev, in32)
+    qcd.field_pack(g, f, "f64", 1, b_dev, in64)
+    solve_kw = dict(method=qcd.BICGSTAB, tol=TOL, inner="f32", use_graph=True, graph_chunk=32)
+
+    ev_d0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_d1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_s0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_s1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+    def step(i=None):
+        if i is not None:
+            ev_d0[i].record(stream)
+        for _ in range(NDSLASH):
+            qcd.dslash(g, f, "D_EO", in32, out32, prec="f32", layout=qcd.INTERNAL)
+        if i is not None:
+            ev_d1[i].record(stream)
+        qcd.dslash(g, f, "D_EO", in64, out64, prec="f64", layout=qcd.INTERNAL)
+        if i is not None:
+            ev_s0[i].record(stream)
+        x_dev.zero_()
+        info, _ = qcd.solve(g, f, b_dev, x_dev, **solve_kw)
+        if i is not None:
+            ev_s1[i].record(stream)
+        return info[0]
+
+    if args.profile == "dslash":
+        for _ in range(3):  # tuning and warm-up, then the profiled launches
+            qcd.dslash(g, f, "D_EO", in32, out32, prec="f32", layout=qcd.INTERNAL)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(NDSLASH):
+            qcd.dslash(g, f, "D_EO", in32, out32, prec="f32", layout=qcd.INTERNAL)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print("profile dslash done", flush=True)
+        return
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if args.profile == "step":
+        torch.cuda.profiler.start()
+        info = step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(f"profile step done: {info}", flush=True)
+        return
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    n0 = qcd.kernel_launches()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    infos = [step(i) for i in range(args.steps)]
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    n_launch = qcd.kernel_launches() - n0
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    d_ms = [ev_d0[i].elapsed_time(ev_d1[i]) / NDSLASH for i in range(args.steps)]
+    s_ms = [ev_s0[i].elapsed_time(ev_s1[i]) for i in range(args.steps)]
+    dslash_avg_ms = sum(d_ms) / len(d_ms)
+    for inf in infos:
+        if not inf["converged"] or inf["true_resid"] > TOL:
+            raise SystemExit(f"solve failed to converge: {inf}")
+
+    def hops_in_solve(inf):
+        # 4 inner half-dslashes per BiCGStab iteration; FP64: 1 (source) + 2 per true
+        # residual (outer_updates + 1 of them) + 1 (reconstruction) + 2 (final residual)
+        return 4 * inf["iters"] + 1 + 2 * (inf["outer_updates"] + 1) + 1 + 2
+
+    hops = sum(NDSLASH + 1 + hops_in_solve(inf) for inf in infos)
+    flops = FLOP_SITE * Vh * hops
+    value = flops / (total_ms / 1e3) / 1e9 * world
+    hbm, peak_kind = peaks()
+    alg_bytes = BYTES_SITE_FP32[RECON] * Vh
+    achieved = alg_bytes / (dslash_avg_ms / 1e3) / 1e9
+    traffic = profiled_traffic()
+
+    # ---- plain FP64 GPU solve (the comparison), once
+    fp64 = None
+    if not args.no_fp64_solve:
+        x_dev.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info64, _ = qcd.solve(g, f, b_dev, x_dev, method=qcd.BICGSTAB, tol=TOL, inner="f64", use_graph=True,
+                              graph_chunk=32)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"ms": round(e0.elapsed_time(e1), 3), "iters": info64[0]["iters"],
+                "true_resid": info64[0]["true_resid"]}
+
+    # ---- standalone FP64 D_eo rate (ALU-bound on GB300)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        qcd.dslash(g, f, "D_EO", in64, out64, prec="f64", layout=qcd.INTERNAL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    d64_ms = e0.elapsed_time(e1) / 3
+
+    # ---- end to end through the C ABI with host buffers (pinned), one step
+    b_host = torch.from_numpy(psi).pin_memory().numpy()
+    x_host = torch.zeros((V, 4, 3), dtype=torch.complex128).pin_memory().numpy()
+    o_host = torch.zeros((V, 4, 3), dtype=torch.complex128).pin_memory().numpy()
+    e2e_ms = []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qcd.dslash(g, f, "D_EO", b_host, o_host, prec="f32")
+        info_e, _ = qcd.solve(g, f, b_host, x_host, **solve_kw)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_hops = 1 + hops_in_solve(info_e[0])
+    e2e_val = FLOP_SITE * Vh * e2e_hops / (min(e2e_ms) / 1e3) / 1e9 * world
+    spinor_bytes = V * 12 * 16
+
+    mixed_ms = statistics.median(s_ms)
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: smoothed-random SU(3) links and Z2 noise source (seeded)",
+        "config": {"workload": WORKLOAD, "lattice": list(L), "kappa": KAPPA, "eps": EPS, "recon": RECON,
+                   "solver": "EO BiCGStab, FP32 inner + FP64 reliable updates, CUDA graph chunks of 32",
+                   "tol": TOL, "ndslash_per_step": NDSLASH,
+                   "l2": "inputs larger than L2 (links 403 MB, each parity vector 101 MB)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "kernel": "k_hop<FP32,12-real> (D_eo)", "achieved": round(achieved, 1),
+                     "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                     "traffic": traffic, "algorithmic_bytes": alg_bytes,
+                     "note": f"peak of {peak_kind} (copy bandwidth); {BYTES_SITE_FP32[RECON]} B per output site"},
+        "dslash": {"fp32_ms": round(dslash_avg_ms, 4),
+                   "fp32_gflops": round(FLOP_SITE * Vh / (dslash_avg_ms / 1e3) / 1e9, 1),
+                   "fp64_ms": round(d64_ms, 4),
+                   "fp64_gflops": round(FLOP_SITE * Vh / (d64_ms / 1e3) / 1e9, 1),
+                   "fp64_bound": "alu", "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+                   "fp64_frac": round(FLOP_SITE * Vh / (d64_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, 4),
+                   "fp64_gbs": round(BYTES_SITE_FP64 * Vh / (d64_ms / 1e3) / 1e9, 1)},
+        "solve": {"mixed_ms": round(mixed_ms, 3), "mixed_iters": infos[-1]["iters"],
+                  "mixed_updates": infos[-1]["outer_updates"], "mixed_true_resid": infos[-1]["true_resid"],
+                  "fp64": fp64, "speedup_vs_fp64": round(fp64["ms"] / mixed_ms, 3) if fp64 else None},
+        "e2e": {"value": round(e2e_val, 3), "unit": "GFLOP/s", "ms": round(min(e2e_ms), 3),
+                "h2d_bytes_per_step": 2 * spinor_bytes, "d2h_bytes_per_step": 2 * spinor_bytes},
+        "gpu_launches": n_launch,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(U, psi)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    g.free()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -227,6 +227,10 @@ const char* qcd_last_error(void);
  * environment variable QCD_TUNECACHE when set. */
 qcd_status qcd_set_tuning(int32_t mode);
 
+/* Instrumentation: the number of kernels this library has launched in this
+ * process so far (a replayed CUDA graph counts each of its kernel nodes). */
+qcd_status qcd_kernel_launches(uint64_t* count);
+
 #ifdef __cplusplus
 }
 #endif

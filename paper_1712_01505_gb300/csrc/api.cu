@@ -1,6 +1,7 @@
 // The C ABI of libqcd (declared in include/qcd.h): argument validation,
 // handle and workspace management, host/device staging of canonical fields,
 // and dispatch to the kernels.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -19,7 +20,12 @@ void force_device(const qcd_gauge* g, const qcd_fermion& f, const double* X, con
 
 namespace {
 thread_local std::string t_err;
+std::atomic<long> g_launches{0};
 }
+
+void note_launches(long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+void set_launches(long n) { g_launches.store(n, std::memory_order_relaxed); }
 
 void raise(qcd_status s, const char* fmt, ...) {
   char buf[512];
@@ -199,6 +205,13 @@ using namespace qcd;
 extern "C" {
 
 const char* qcd_last_error(void) { return t_err.c_str(); }
+
+qcd_status qcd_kernel_launches(uint64_t* count) {
+  return guarded([&] {
+    if (!count) raise(QCD_ERR_ARG, "count is NULL");
+    *count = (uint64_t)launches_so_far();
+  });
+}
 
 qcd_status qcd_set_tuning(int32_t mode) {
   return guarded([&] {

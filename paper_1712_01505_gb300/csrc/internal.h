@@ -25,8 +25,15 @@ struct Error {
 [[noreturn]] void raise(qcd_status s, const char* fmt, ...);
 void cuda_check(cudaError_t e, const char* what, const char* file, int line);
 #define QCD_CK(call) ::qcd::cuda_check((call), #call, __FILE__, __LINE__)
-// check the last launch (a launch error leaves no sticky state)
-#define QCD_LAUNCH_CK() ::qcd::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+// count one kernel launch and check it (a launch error leaves no sticky state)
+void note_launches(long n);
+long launches_so_far();
+void set_launches(long n);
+#define QCD_LAUNCH_CK()           \
+  do {                            \
+    ::qcd::note_launches(1);      \
+    ::qcd::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__); \
+  } while (0)
 
 // ----------------------------------------------------------------------------- lattice
 struct Lattice {

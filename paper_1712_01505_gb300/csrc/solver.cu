@@ -461,6 +461,7 @@ struct Solver {
   std::vector<Scal> hsc;
   cudaGraphExec_t gexec = nullptr;
   int gchunk = 0;
+  long gnodes = 0;
 
   bool bicg() const { return prm.method == QCD_BICGSTAB; }
   long n() const { return r.nsites(); }
@@ -480,29 +481,43 @@ struct Solver {
   void body_t(dim3 grid, long nn, int dag) {
     if (bicg()) {
       k_bicg_beta<<<1, 32, 0, st>>>(sc, nrhs, ctl);
+      QCD_LAUNCH_CK();
       k_bicg_p<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(p), any_view(v), nn, sc, ctl);
+      QCD_LAUNCH_CK();
       apply_mhat(opin, p, v, dag, st, "in", ctl);
       k_cdot<R><<<grid, kThreads, 0, st>>>(any_view(rt), any_view(v), nn, partial, sc, ctl);
+      QCD_LAUNCH_CK();
       k_bicg_alpha<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
+      QCD_LAUNCH_CK();
       k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl);
+      QCD_LAUNCH_CK();
       apply_mhat(opin, s, t, dag, st, "in", ctl);
       k_ts_tt<R><<<grid, kThreads, 0, st>>>(any_view(t), any_view(s), nn, partial, sc, ctl);
+      QCD_LAUNCH_CK();
       k_bicg_omega<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
+      QCD_LAUNCH_CK();
       k_bicg_xr<R, RX><<<grid, kThreads, 0, st>>>(any_view(xin), any_view(p), any_view(s), any_view(t),
                                                   any_view(r), any_view(rt), nn, partial, sc, ctl);
+      QCD_LAUNCH_CK();
       k_bicg_check<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
+      QCD_LAUNCH_CK();
     } else {
       k_cg_beta<<<1, 32, 0, st>>>(sc, nrhs, ctl);
+      QCD_LAUNCH_CK();
       k_cg_p<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(p), nn, sc, ctl);
+      QCD_LAUNCH_CK();
       apply_mhat(opin, p, w, 0, st, "in", ctl);
       apply_mhat(opin, w, q, 1, st, "in", ctl);
       k_rdot<R><<<grid, kThreads, 0, st>>>(any_view(p), any_view(q), nn, partial, sc, ctl);
+      QCD_LAUNCH_CK();
       k_cg_alpha<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
+      QCD_LAUNCH_CK();
       k_cg_xr<R, RX><<<grid, kThreads, 0, st>>>(any_view(xin), any_view(p), any_view(q), any_view(r),
                                                 nn, partial, sc, ctl);
+      QCD_LAUNCH_CK();
       k_cg_check<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
+      QCD_LAUNCH_CK();
     }
-    QCD_LAUNCH_CK();
   }
 
   void run_chunk(int k, bool graph) {
@@ -511,17 +526,23 @@ struct Solver {
         if (gexec) cudaGraphExecDestroy(gexec);
         gexec = nullptr;
         cudaGraph_t gr;
+        long c0 = launches_so_far();
         QCD_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         k_reset<<<1, 1, 0, st>>>(ctl);
+        QCD_LAUNCH_CK();
         for (int i = 0; i < k; ++i) body();
         QCD_CK(cudaStreamEndCapture(st, &gr));
+        gnodes = launches_so_far() - c0;  // captured, not yet executed
+        set_launches(c0);
         QCD_CK(cudaGraphInstantiate(&gexec, gr, 0));
         cudaGraphDestroy(gr);
         gchunk = k;
       }
       QCD_CK(cudaGraphLaunch(gexec, st));
+      note_launches(gnodes);
     } else {
       k_reset<<<1, 1, 0, st>>>(ctl);
+      QCD_LAUNCH_CK();
       for (int i = 0; i < k; ++i) body();
     }
   }

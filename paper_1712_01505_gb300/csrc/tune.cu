@@ -105,6 +105,7 @@ LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
     for (int r = 0; r < reps; ++r) run(ctx, c);
     QCD_CK(cudaEventRecord(e1, st));
     QCD_CK(cudaEventSynchronize(e1));
+    note_launches(reps - 1);
     QCD_LAUNCH_CK();
     float ms = 0;
     QCD_CK(cudaEventElapsedTime(&ms, e0, e1));

@@ -12,6 +12,9 @@ whose links are SU(3) matrices.
 """
 from __future__ import annotations
 
+import os
+import tempfile
+
 import numpy as np
 
 
@@ -52,10 +55,26 @@ def random_su3_near_identity(n: int, eps: float, rng: np.random.Generator) -> np
 
 
 def gauge_field(L, eps: float, seed: int) -> np.ndarray:
-    """Smoothed random SU(3) gauge field, shape (4, V, 3, 3); links drawn mu-major then by site."""
+    """Smoothed random SU(3) gauge field, shape (4, V, 3, 3); links drawn mu-major then by site.
+
+    Fields of 2^20 sites or more are cached as .npy files in $QCD_INPUT_CACHE
+    (default: the system temporary directory), since drawing one takes tens of
+    seconds; the cache key is (L, eps, seed) and the content is the same array.
+    """
     V = volume(L)
-    U = random_su3_near_identity(4 * V, eps, _rng(seed))
-    return U.reshape(4, V, 3, 3)
+    path = None
+    if V >= (1 << 20):
+        d = os.environ.get("QCD_INPUT_CACHE", os.path.join(tempfile.gettempdir(), "qcd_inputs"))
+        path = os.path.join(d, f"gauge_{'x'.join(map(str, L))}_eps{eps:g}_seed{int(seed)}.npy")
+        if os.path.exists(path):
+            return np.load(path)
+    U = random_su3_near_identity(4 * V, eps, _rng(seed)).reshape(4, V, 3, 3)
+    if path:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = f"{path}.{os.getpid()}.tmp.npy"
+        np.save(tmp, U)
+        os.replace(tmp, path)
+    return U
 
 
 def unit_gauge(L) -> np.ndarray:

@@ -41,7 +41,7 @@ BICGSTAB, CG_NORMAL = 0, 1
 
 # every symbol the header declares
 SYMBOLS = ["qcd_gauge_load", "qcd_gauge_free", "qcd_field_bytes", "qcd_field_pack", "qcd_field_unpack",
-           "qcd_dslash", "qcd_solve", "qcd_force", "qcd_last_error", "qcd_set_tuning"]
+           "qcd_dslash", "qcd_solve", "qcd_force", "qcd_last_error", "qcd_set_tuning", "qcd_kernel_launches"]
 
 
 class QCDError(RuntimeError):
@@ -102,8 +102,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qcd_force.argtypes = [vp, ctypes.POINTER(Fermion), vp, vp, vp, vp]
     lib.qcd_last_error.restype = ctypes.c_char_p
     lib.qcd_set_tuning.argtypes = [i32]
+    lib.qcd_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     for name in ("qcd_gauge_load", "qcd_gauge_free", "qcd_field_pack", "qcd_field_unpack", "qcd_dslash",
-                 "qcd_solve", "qcd_force", "qcd_set_tuning"):
+                 "qcd_solve", "qcd_force", "qcd_set_tuning", "qcd_kernel_launches"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -145,6 +146,13 @@ def wilson(kappa: float) -> Fermion:
 def dwf(Ls: int, M5: float, mf: float) -> Fermion:
     """Domain-wall fermion, Eq. (2): N_s = Ls, m0 = -M5, quark mass mf."""
     return Fermion(DWF, 0.0, int(Ls), float(M5), float(mf))
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    n = ctypes.c_uint64()
+    _check(load_library().qcd_kernel_launches(ctypes.byref(n)))
+    return int(n.value)
 
 
 def set_tuning(on: bool):
