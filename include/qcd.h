@@ -227,6 +227,32 @@ const char* qcd_last_error(void);
  * environment variable QCD_TUNECACHE when set. */
 qcd_status qcd_set_tuning(int32_t mode);
 
+/* Allocation-free Wilson Schur operator (the paper has no counterpart; this
+ * entry point exists for callers that cannot let the library allocate device
+ * memory -- e.g. a framework whose allocator already owns the GPU's memory,
+ * a pipeline that cannot afford the device-wide synchronisation of
+ * cudaMalloc/cudaFree, or code held to a fixed footprint after start-up).
+ * Computes the same as qcd_dslash(g, fermion, prec, dagger ? QCD_OP_MHAT_DAG
+ * : QCD_OP_MHAT, in, out, nrhs, QCD_LAYOUT_INTERNAL, stream): out = in -
+ * kappa^2 H_eo H_oe in (H -> H^dag for dagger != 0) on INTERNAL single-parity
+ * device buffers, without calling cudaMalloc, cudaFree or any allocating
+ * routine.  The odd-parity intermediate lives in a fixed device array of
+ * QCD_NOALLOC_SCRATCH_BYTES bytes inside the library (present on every GPU
+ * that loads the library until the process exits).
+ *   - Wilson fermions only (QCD_ERR_UNSUPPORTED otherwise).
+ *   - QCD_ERR_ARG if the intermediate (Vh * nrhs sites in `prec`) exceeds
+ *     QCD_NOALLOC_SCRATCH_BYTES, before anything is launched.
+ *   - The first call on a device looks up the array's device address on that
+ *     device; make that first call before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind: calls
+ *     whose GPU work overlaps (different streams or host threads) race on it
+ *     and must be ordered by the caller.
+ *   - The stencil runs with the tuner's cached launch shape if there is one,
+ *     else the default shape (no timing runs). */
+#define QCD_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+qcd_status qcd_mhat_noalloc(const qcd_gauge* g, const qcd_fermion* fermion, qcd_prec prec,
+                            int32_t dagger, const void* in, void* out, int32_t nrhs, void* stream);
+
 /* Instrumentation: the number of kernels this library has launched in this
  * process so far (a replayed CUDA graph counts each of its kernel nodes). */
 qcd_status qcd_kernel_launches(uint64_t* count);

@@ -17,6 +17,8 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
                   double* x, int nrhs, qcd_solve_info* info, cudaStream_t st);
 void force_device(const qcd_gauge* g, const qcd_fermion& f, const double* X, const double* eta,
                   double* dSdU, cudaStream_t st);
+void mhat_noalloc(const qcd_gauge* g, const qcd_fermion& f, int prec, int dagger, const void* in,
+                  void* out, int nrhs, cudaStream_t st);
 
 namespace {
 thread_local std::string t_err;
@@ -432,6 +434,22 @@ qcd_status qcd_solve(const qcd_gauge* gc, const qcd_fermion* fermion, const qcd_
     for (int r = 0; r < nrhs; ++r)
       if (info[r].status != QCD_OK) worst = (qcd_status)info[r].status;
     if (worst != QCD_OK) raise(worst, "solve did not reach tol for every right-hand side (see info)");
+  });
+}
+
+qcd_status qcd_mhat_noalloc(const qcd_gauge* gc, const qcd_fermion* fermion, qcd_prec prec,
+                            int32_t dagger, const void* in, void* out, int32_t nrhs, void* stream) {
+  return guarded([&] {
+    check_gauge(gc);
+    check_fermion(fermion);
+    if (fermion->type != QCD_WILSON) raise(QCD_ERR_UNSUPPORTED, "qcd_mhat_noalloc is for Wilson fermions");
+    check_prec(prec);
+    if (dagger != 0 && dagger != 1) raise(QCD_ERR_ARG, "dagger must be 0 or 1");
+    if (!in || !out) raise(QCD_ERR_ARG, "in and out must not be NULL");
+    if (in == out) raise(QCD_ERR_ARG, "in and out must not overlap");
+    if (nrhs < 1 || nrhs > 64) raise(QCD_ERR_ARG, "nrhs = %d must be in [1, 64]", nrhs);
+    if (!is_device_ptr(in) || !is_device_ptr(out)) raise(QCD_ERR_ARG, "in and out must be device memory");
+    mhat_noalloc(gc, *fermion, prec, dagger, in, out, nrhs, (cudaStream_t)stream);
   });
 }
 

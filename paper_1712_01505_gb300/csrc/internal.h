@@ -106,7 +106,7 @@ void zero_parity_canon(const Lattice& lat, int parity, double* canon, int nvec, 
 // `stop` (device int, may be null): the kernel does nothing when *stop != 0
 // (used by the solver's captured iteration chunks).
 void hop(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int dagger, double a,
-         const Field* x, cudaStream_t st, const int* stop = nullptr);
+         const Field* x, cudaStream_t st, const int* stop = nullptr, bool allow_tuning = true);
 
 // ----------------------------------------------------------------------------- domain wall (dwf.cu)
 struct DwParams {
@@ -152,7 +152,8 @@ void set_tuning(int mode);
 // candidates are tried with `run` (which must be idempotent) when the key is
 // new and the stream is not capturing; returns the cached or chosen config.
 LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
-               void (*run)(void* ctx, const LaunchCfg& cfg), void* ctx, cudaStream_t st);
+               void (*run)(void* ctx, const LaunchCfg& cfg), void* ctx, cudaStream_t st,
+               bool allow_timing = true);
 
 // device properties
 int sm_count();

@@ -76,7 +76,8 @@ int sm_count() {
 }
 
 LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
-               void (*run)(void* ctx, const LaunchCfg& cfg), void* ctx, cudaStream_t st) {
+               void (*run)(void* ctx, const LaunchCfg& cfg), void* ctx, cudaStream_t st,
+               bool allow_timing) {
   if (cands.empty()) raise(QCD_ERR_ARG, "tune: no candidates for %s", key.c_str());
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -86,7 +87,7 @@ LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
       for (const auto& c : cands)
         if (c.block == it->second.block && c.tile == it->second.tile) return it->second;
     }
-    if (g_mode == 0) return cands[0];
+    if (g_mode == 0 || !allow_timing) return cands[0];
   }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   QCD_CK(cudaStreamIsCapturing(st, &cs));

@@ -240,7 +240,8 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
 
 template <int P, int RECON>
 void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& out, int out_parity,
-              int dagger, double a, const Field* x, cudaStream_t st, const int* stop) {
+              int dagger, double a, const Field* x, cudaStream_t st, const int* stop,
+              bool allow_tuning) {
   HopLaunch<P, RECON> L;
   HopArgs<P, RECON>& A = L.args;
   A.g = dev_geom(gh->lat);
@@ -268,7 +269,7 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   char key[160];
   snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay);
-  LaunchCfg cfg = tune(key, cands, &run_cfg<P, RECON>, &L, st);
+  LaunchCfg cfg = tune(key, cands, &run_cfg<P, RECON>, &L, st, allow_tuning);
   run_cfg<P, RECON>(&L, cfg);
   QCD_LAUNCH_CK();
 }
@@ -276,7 +277,7 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
 }  // namespace
 
 void hop(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int dagger, double a,
-         const Field* x, cudaStream_t st, const int* stop) {
+         const Field* x, cudaStream_t st, const int* stop, bool allow_tuning) {
   if (in.prec != out.prec || (x && x->prec != out.prec))
     raise(QCD_ERR_ARG, "hop: mixed precisions are not supported");
   if (in.data == out.data || (x && x->data == out.data))
@@ -284,19 +285,19 @@ void hop(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int da
   if (in.Vh == 0 || in.nrhs * in.ls == 0) return;
   switch (in.prec) {
     case QCD_F64:
-      hop_impl<P64, 18>(g, g->U64, in, out, out_parity, dagger, a, x, st, stop);
+      hop_impl<P64, 18>(g, g->U64, in, out, out_parity, dagger, a, x, st, stop, allow_tuning);
       break;
     case QCD_F32:
       if (g->lat.recon == 12)
-        hop_impl<P32, 12>(g, g->U32, in, out, out_parity, dagger, a, x, st, stop);
+        hop_impl<P32, 12>(g, g->U32, in, out, out_parity, dagger, a, x, st, stop, allow_tuning);
       else
-        hop_impl<P32, 18>(g, g->U32, in, out, out_parity, dagger, a, x, st, stop);
+        hop_impl<P32, 18>(g, g->U32, in, out, out_parity, dagger, a, x, st, stop, allow_tuning);
       break;
     default:
       if (g->lat.recon == 12)
-        hop_impl<P16, 12>(g, g->U16, in, out, out_parity, dagger, a, x, st, stop);
+        hop_impl<P16, 12>(g, g->U16, in, out, out_parity, dagger, a, x, st, stop, allow_tuning);
       else
-        hop_impl<P16, 18>(g, g->U16, in, out, out_parity, dagger, a, x, st, stop);
+        hop_impl<P16, 18>(g, g->U16, in, out, out_parity, dagger, a, x, st, stop, allow_tuning);
   }
 }
 

@@ -41,7 +41,8 @@ BICGSTAB, CG_NORMAL = 0, 1
 
 # every symbol the header declares
 SYMBOLS = ["qcd_gauge_load", "qcd_gauge_free", "qcd_field_bytes", "qcd_field_pack", "qcd_field_unpack",
-           "qcd_dslash", "qcd_solve", "qcd_force", "qcd_last_error", "qcd_set_tuning", "qcd_kernel_launches"]
+           "qcd_dslash", "qcd_solve", "qcd_force", "qcd_last_error", "qcd_set_tuning", "qcd_kernel_launches",
+           "qcd_mhat_noalloc"]
 
 
 class QCDError(RuntimeError):
@@ -103,8 +104,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qcd_last_error.restype = ctypes.c_char_p
     lib.qcd_set_tuning.argtypes = [i32]
     lib.qcd_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+    lib.qcd_mhat_noalloc.argtypes = [vp, ctypes.POINTER(Fermion), i32, i32, vp, vp, i32, vp]
     for name in ("qcd_gauge_load", "qcd_gauge_free", "qcd_field_pack", "qcd_field_unpack", "qcd_dslash",
-                 "qcd_solve", "qcd_force", "qcd_set_tuning", "qcd_kernel_launches"):
+                 "qcd_solve", "qcd_force", "qcd_set_tuning", "qcd_kernel_launches", "qcd_mhat_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -215,6 +217,16 @@ def dslash(gauge, fermion, op, inp, out, prec="f64", nrhs=1, layout=CANON, strea
     op = OPS[op] if isinstance(op, str) else int(op)
     _check(load_library().qcd_dslash(gauge.handle, ctypes.byref(fermion), PREC[prec], op, _ptr(inp),
                                      _ptr(out), nrhs, layout, _stream(stream)))
+    return out
+
+
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def mhat_noalloc(gauge, fermion, inp, out, prec="f32", dagger=False, nrhs=1, stream=None):
+    """qcd_mhat_noalloc: Wilson Mhat (Mhat^dag) on INTERNAL buffers without device allocation."""
+    _check(load_library().qcd_mhat_noalloc(gauge.handle, ctypes.byref(fermion), PREC[prec], int(dagger),
+                                           _ptr(inp), _ptr(out), nrhs, _stream(stream)))
     return out
 
 
