@@ -1,0 +1,169 @@
+"""Measurements of the other workloads of the solve path (invoked as `bench.py --workload ...`).
+
+* dwf:     domain-wall 16^3 x 32 x Ls=16, M5 = 1.8, mf = 0.02, eps = 0.2 (seed 3), Gaussian
+           source (seed 0): the fifth-dimension hop in FP32 and FP16, and CG on Mhat^dag Mhat
+           with FP16 inner iterations + FP64 outer steps against the plain FP64 CG, to 1e-10.
+* batched: Wilson 24^3 x 48, kappa = 0.124, eps = 0.2 (seed 4), the 12 spin-colour point
+           sources at one random site (seed 0): one 12-rhs solve (shared link loads, graph
+           chunks, tuned tiles) against 12 single-rhs solves, FP32 inner + FP64, to 1e-10.
+* force:   Wilson 16^4, kappa = 0.12, eps = 0.3 (seed 5), Gaussian phi (seed 0): the backward
+           pass of S = phi^dag (M^dag M)^-1 phi (adjoint solve + outer-product kernel).
+Each prints one JSON line.
+"""
+from __future__ import annotations
+
+import json
+import time
+
+import numpy as np
+import torch
+
+from paper_1712_01505_gb300 import inputs, qcd
+
+BC = (1, 1, 1, -1)
+
+
+def _events():
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _time_launches(fn, n=20, warm=3):
+    for _ in range(warm):
+        fn()
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(n):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def _peak():
+    import os
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    return float(json.load(open(p))["hbm_gbs"]) if os.path.exists(p) else 6800.0
+
+
+def run_dwf(args):
+    L, Ls, M5, mf = (16, 16, 16, 32), 16, 1.8, 0.02
+    V = int(np.prod(L))
+    Vh = V // 2
+    U = inputs.gauge_field(L, 0.2, 3)
+    b = inputs.gaussian_source((Ls, V, 4, 3), 0)
+    dev = torch.device("cuda", 0)
+    g = qcd.Gauge.load(torch.from_numpy(U).to(dev), L, BC, recon=12)
+    f = qcd.dwf(Ls, M5, mf)
+    bd = torch.from_numpy(b).to(dev)
+    hop = {}
+    for prec, site_b, link_b in (("f32", 96, 48), ("f16", 52, 24)):
+        nb = qcd.field_bytes(g, f, prec)
+        a_ = torch.empty(nb, dtype=torch.uint8, device=dev)
+        o_ = torch.empty(nb, dtype=torch.uint8, device=dev)
+        qcd.field_pack(g, f, prec, 1, bd, a_)
+        ms = _time_launches(lambda: qcd.dslash(g, f, "D_EO", a_, o_, prec=prec, layout=qcd.INTERNAL))
+        ms_m = _time_launches(lambda: qcd.dslash(g, f, "MHAT", a_, o_, prec=prec, layout=qcd.INTERNAL), n=10)
+        alg = Vh * (8 * link_b + Ls * 2 * site_b)
+        hop[prec] = {"hop_ms": round(ms, 4), "hop_gflops": round(1320 * Vh * Ls / ms / 1e6, 1),
+                     "hop_gbs": round(alg / ms / 1e6, 1), "hop_frac": round(alg / ms / 1e6 / _peak(), 4),
+                     "mhat_ms": round(ms_m, 4)}
+    res = {}
+    for inner in ("f16", "f32", "f64"):
+        x = torch.zeros_like(bd)
+        qcd.solve(g, f, bd, x, method=qcd.CG_NORMAL, tol=1e-10, inner=inner, use_graph=True, graph_chunk=32,
+                  delta=args.delta)  # warm-up (tuning, workspace)
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info, _ = qcd.solve(g, f, bd, x, method=qcd.CG_NORMAL, tol=1e-10, inner=inner, use_graph=True,
+                            graph_chunk=32, delta=args.delta)
+        torch.cuda.synchronize()
+        res[inner] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "iters": info[0]["iters"],
+                      "updates": info[0]["outer_updates"], "true_resid": info[0]["true_resid"]}
+    out = {"workload": "dwf_16x16x16x32_Ls16_M5_1.8_mf0.02", "hop": hop, "cg": res,
+           "speedup_f16_vs_f64": round(res["f64"]["ms"] / res["f16"]["ms"], 3),
+           "speedup_f32_vs_f64": round(res["f64"]["ms"] / res["f32"]["ms"], 3)}
+    print(json.dumps(out), flush=True)
+
+
+def run_batched(args):
+    L, kappa = (24, 24, 24, 48), 0.124
+    V = int(np.prod(L))
+    Vh = V // 2
+    U = inputs.gauge_field(L, 0.2, 4)
+    x0, b = inputs.point_sources(L, 0)
+    dev = torch.device("cuda", 0)
+    g = qcd.Gauge.load(torch.from_numpy(U).to(dev), L, BC, recon=12)
+    f = qcd.wilson(kappa)
+    bd = torch.from_numpy(b).to(dev)
+    # 12-rhs stencil vs 12 single-rhs stencils (FP32, internal layout)
+    nb12 = qcd.field_bytes(g, f, "f32", 12)
+    a12 = torch.empty(nb12, dtype=torch.uint8, device=dev)
+    o12 = torch.empty(nb12, dtype=torch.uint8, device=dev)
+    qcd.field_pack(g, f, "f32", 1, bd, a12, nrhs=12)
+    ms12 = _time_launches(lambda: qcd.dslash(g, f, "D_EO", a12, o12, prec="f32", nrhs=12, layout=qcd.INTERNAL))
+    nb1 = qcd.field_bytes(g, f, "f32", 1)
+    ms1 = _time_launches(lambda: qcd.dslash(g, f, "D_EO", a12[:nb1], o12[:nb1], prec="f32",
+                                            layout=qcd.INTERNAL))
+    alg12 = Vh * (8 * 48 + 12 * 192)
+    kw = dict(method=qcd.BICGSTAB, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32, delta=args.delta)
+    x = torch.zeros_like(bd)
+    qcd.solve(g, f, bd, x, nrhs=12, **kw)  # warm-up
+    x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info, _ = qcd.solve(g, f, bd, x, nrhs=12, **kw)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    iters_seq = []
+    for k in range(12):
+        xk = torch.zeros_like(bd[k])
+        ik, _ = qcd.solve(g, f, bd[k].contiguous(), xk, **kw)
+        iters_seq.append(ik[0]["iters"])
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    out = {"workload": "wilson_24x24x24x48_kappa0.124_12pointsources", "x0": x0,
+           "dslash12_ms": round(ms12, 4), "dslash12_gflops": round(1320 * Vh * 12 / ms12 / 1e6, 1),
+           "dslash12_gbs": round(alg12 / ms12 / 1e6, 1), "dslash12_frac": round(alg12 / ms12 / 1e6 / _peak(), 4),
+           "dslash1_x12_ms": round(12 * ms1, 4),
+           "solve12_s": round(t_batch, 4), "solve_12x1_s": round(t_seq, 4),
+           "speedup_batched": round(t_seq / t_batch, 3),
+           "iters": [i["iters"] for i in info], "iters_seq": iters_seq,
+           "max_true_resid": max(i["true_resid"] for i in info)}
+    print(json.dumps(out), flush=True)
+
+
+def run_force(args):
+    from paper_1712_01505_gb300.autograd import wilson_action
+
+    L, kappa = (16, 16, 16, 16), 0.12
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.3, 5)
+    phi = inputs.gaussian_source((V, 4, 3), 0)
+    dev = torch.device("cuda", 0)
+    Ut = torch.from_numpy(U).to(dev)
+    pt = torch.from_numpy(phi).to(dev)
+    times = []
+    for rep in range(4):
+        u = Ut.clone().requires_grad_(True)
+        S = wilson_action(u, pt, kappa, L, BC, tol=1e-10, inner="f32")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.backward()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    g = qcd.Gauge.load(Ut, L, BC)
+    f = qcd.wilson(kappa)
+    X = torch.from_numpy(inputs.gaussian_source((V, 4, 3), 1)).to(dev)
+    out_t = torch.empty((4, V, 3, 3, 2), dtype=torch.float64, device=dev)
+    ms = _time_launches(lambda: qcd.force(g, f, X, pt, out_t))
+    out = {"workload": "force_wilson_16x16x16x16_kappa0.12", "backward_ms": round(min(times[1:]) * 1e3, 3),
+           "force_kernel_ms": round(ms, 4),
+           "force_kernel_gbs": round(V * (2 * 192 + 4 * 144) / ms / 1e6, 1)}
+    print(json.dumps(out), flush=True)
+
+
+def run_workload(args):
+    torch.cuda.set_device(0)
+    {"dwf": run_dwf, "batched": run_batched, "force": run_force}[args.workload](args)

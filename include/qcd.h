@@ -217,6 +217,14 @@ qcd_status qcd_solve(const qcd_gauge* g, const qcd_fermion* fermion,
 qcd_status qcd_force(const qcd_gauge* g, const qcd_fermion* fermion, const void* X,
                      const void* eta, void* dSdU, void* stream);
 
+/* Squared norm |psi|^2 (sum over sites, spins, colours of |component|^2) of
+ * each of the nrhs right-hand sides of a canonical complex128 field
+ * (nrhs, [Ls,] V, 4, 3), summed in FP64; e.g. the action S = |eta|^2 with
+ * eta = M^-dag phi (Sec. II A: S_F = psi^dag D^-1 psi).  psi: device or host;
+ * out: host array of nrhs doubles.  Synchronises the stream. */
+qcd_status qcd_norm2(const qcd_gauge* g, const qcd_fermion* fermion, const void* psi, int32_t nrhs,
+                     double* out, void* stream);
+
 /* Message describing the last failing call on this thread ("" if none). */
 const char* qcd_last_error(void);
 

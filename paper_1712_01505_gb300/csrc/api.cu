@@ -437,6 +437,22 @@ qcd_status qcd_solve(const qcd_gauge* gc, const qcd_fermion* fermion, const qcd_
   });
 }
 
+qcd_status qcd_norm2(const qcd_gauge* gc, const qcd_fermion* fermion, const void* psi, int32_t nrhs,
+                     double* out, void* stream) {
+  return guarded([&] {
+    check_gauge(gc);
+    qcd_gauge* g = const_cast<qcd_gauge*>(gc);
+    int ls = check_fermion(fermion);
+    if (!psi || !out) raise(QCD_ERR_ARG, "NULL argument");
+    if (nrhs < 1 || nrhs > 64) raise(QCD_ERR_ARG, "nrhs = %d must be in [1, 64]", nrhs);
+    cudaStream_t st = (cudaStream_t)stream;
+    long per = (long)ls * g->lat.V * 12;
+    size_t cb = (size_t)nrhs * per * 16;
+    Staged s = stage_in(g, "io.in", psi, cb, st, true);
+    canon_norm2(s.dev, per, nrhs, out, st, g);
+  });
+}
+
 qcd_status qcd_mhat_noalloc(const qcd_gauge* gc, const qcd_fermion* fermion, qcd_prec prec,
                             int32_t dagger, const void* in, void* out, int32_t nrhs, void* stream) {
   return guarded([&] {

@@ -75,7 +75,36 @@ __global__ void k_norm2(AnyView x, long n, double* partial) {
   if (threadIdx.x == 0) partial[(long)r * gridDim.x + blockIdx.x] = acc[0];
 }
 
+// per-block partial sums of |z|^2 over a canonical complex128 array (one rhs per grid row)
+__global__ void k_canon_norm2(const double2* __restrict__ z, long n_per_rhs, double* partial) {
+  int r = blockIdx.y;
+  const double2* zr = z + (long)r * n_per_rhs;
+  double acc[1] = {0.0};
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n_per_rhs; i += (long)gridDim.x * blockDim.x) {
+    double2 v = zr[i];
+    acc[0] = fma(v.x, v.x, fma(v.y, v.y, acc[0]));
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) partial[(long)r * gridDim.x + blockIdx.x] = acc[0];
+}
+
 }  // namespace
+
+void canon_norm2(const double* z, long n_per_rhs, int nrhs, double* out_host, cudaStream_t st,
+                 qcd_gauge* g) {
+  unsigned nb = grid_for(n_per_rhs);
+  double* partial = (double*)g->ws.get("blas.cnorm2.partial", sizeof(double) * nb * nrhs);
+  k_canon_norm2<<<dim3(nb, nrhs), kThreads, 0, st>>>((const double2*)z, n_per_rhs, partial);
+  QCD_LAUNCH_CK();
+  std::vector<double> h((size_t)nb * nrhs);
+  QCD_CK(cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+  QCD_CK(cudaStreamSynchronize(st));
+  for (int r = 0; r < nrhs; ++r) {
+    double s = 0;
+    for (unsigned b = 0; b < nb; ++b) s += h[(size_t)r * nb + b];
+    out_host[r] = s;
+  }
+}
 
 void blas_zero(Field& f, cudaStream_t st) {
   if (f.data) QCD_CK(cudaMemsetAsync(f.data, 0, f.data_bytes(), st));

@@ -127,6 +127,9 @@ void blas_copy(const Field& src, Field& dst, cudaStream_t st);  // any precision
 void blas_axpby(double a, const Field& x, double b, Field& y, cudaStream_t st);
 // per right-hand side |x|^2 into host array (synchronises st)
 void blas_norm2(const Field& x, double* out_host, cudaStream_t st, qcd_gauge* g);
+// per right-hand side sum |z|^2 of a canonical complex128 device array (synchronises st)
+void canon_norm2(const double* z, long n_per_rhs, int nrhs, double* out_host, cudaStream_t st,
+                 qcd_gauge* g);
 
 // ----------------------------------------------------------------------------- operators (ops.cu)
 struct OpCtx {

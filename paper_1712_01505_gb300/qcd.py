@@ -42,7 +42,7 @@ BICGSTAB, CG_NORMAL = 0, 1
 # every symbol the header declares
 SYMBOLS = ["qcd_gauge_load", "qcd_gauge_free", "qcd_field_bytes", "qcd_field_pack", "qcd_field_unpack",
            "qcd_dslash", "qcd_solve", "qcd_force", "qcd_last_error", "qcd_set_tuning", "qcd_kernel_launches",
-           "qcd_mhat_noalloc"]
+           "qcd_mhat_noalloc", "qcd_norm2"]
 
 
 class QCDError(RuntimeError):
@@ -105,8 +105,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qcd_set_tuning.argtypes = [i32]
     lib.qcd_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     lib.qcd_mhat_noalloc.argtypes = [vp, ctypes.POINTER(Fermion), i32, i32, vp, vp, i32, vp]
+    lib.qcd_norm2.argtypes = [vp, ctypes.POINTER(Fermion), vp, i32, ctypes.POINTER(ctypes.c_double), vp]
     for name in ("qcd_gauge_load", "qcd_gauge_free", "qcd_field_pack", "qcd_field_unpack", "qcd_dslash",
-                 "qcd_solve", "qcd_force", "qcd_set_tuning", "qcd_kernel_launches", "qcd_mhat_noalloc"):
+                 "qcd_solve", "qcd_force", "qcd_set_tuning", "qcd_kernel_launches", "qcd_mhat_noalloc",
+                 "qcd_norm2"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -245,6 +247,14 @@ def solve(gauge, fermion, b, x, nrhs=1, stream=None, check=True, **kw):
     if check:
         _check(st)
     return [i.as_dict() for i in info], st
+
+
+def norm2(gauge, fermion, psi, nrhs=1, stream=None):
+    """qcd_norm2: |psi|^2 per right-hand side (FP64 sums), as a list of floats."""
+    out = (ctypes.c_double * nrhs)()
+    _check(load_library().qcd_norm2(gauge.handle, ctypes.byref(fermion), _ptr(psi), nrhs, out,
+                                    _stream(stream)))
+    return list(out)
 
 
 def force(gauge, fermion, X, eta, out, stream=None):
