@@ -29,15 +29,15 @@ struct AinvCoef {
   double mf;
 };
 
-// block: (32 sites) x (ls slices); grid: (ceil(Vh/32), nrhs)
+// block: (32 sites) x (8 slices); grid: (ceil(Vh/32), nrhs, ceil(Ls/8))
 template <typename R>
-__global__ void k_ainv(AinvCoef c, AnyView in, AnyView out, long Vh, int dagger, R scale,
+__global__ void __launch_bounds__(256) k_ainv(AinvCoef c, AnyView in, AnyView out, long Vh, int dagger, R scale,
                        AnyView x, int has_x, const int* stop) {
   if (stop && *stop) return;
   int r = blockIdx.y;
   long cb = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int s = threadIdx.y;
-  if (cb >= Vh) return;
+  int s = blockIdx.z * blockDim.y + threadIdx.y;
+  if (cb >= Vh || s >= c.Ls) return;
   const int Ls = c.Ls;
   Cx<R> acc[12];
 #pragma unroll
@@ -73,12 +73,12 @@ __global__ void k_ainv(AinvCoef c, AnyView in, AnyView out, long Vh, int dagger,
 
 // out = A in + c * y  (A^dag for dagger)
 template <typename R>
-__global__ void k_ablock(int Ls, R a, R mf, AnyView in, AnyView out, R cy, AnyView y, int has_y,
+__global__ void __launch_bounds__(256) k_ablock(int Ls, R a, R mf, AnyView in, AnyView out, R cy, AnyView y, int has_y,
                          long Vh, int dagger) {
   int r = blockIdx.y;
   long cb = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int s = threadIdx.y;
-  if (cb >= Vh) return;
+  int s = blockIdx.z * blockDim.y + threadIdx.y;
+  if (cb >= Vh || s >= Ls) return;
   Cx<R> v[12], lo[12], up[12];
   any_load<R>(in, r, (long)s * Vh + cb, v);
   int sm = s == 0 ? Ls - 1 : s - 1;
@@ -108,10 +108,10 @@ __global__ void k_ablock(int Ls, R a, R mf, AnyView in, AnyView out, R cy, AnyVi
   any_store<R>(out, r, (long)s * Vh + cb, o);
 }
 
-dim3 block_for(int Ls) {
-  int bx = 32;
-  while (bx * Ls > 1024 && bx > 1) bx /= 2;
-  return dim3(bx, Ls);
+// block: 32 consecutive sites (one warp, coalesced) x 8 slices; grid z covers the slices
+dim3 block_for(int) { return dim3(32, 8); }
+dim3 grid_for(const Field& f, dim3 blk, int Ls) {
+  return dim3((unsigned)((f.Vh + blk.x - 1) / blk.x), f.nrhs, (unsigned)((Ls + blk.y - 1) / blk.y));
 }
 
 }  // namespace
@@ -129,7 +129,7 @@ void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double 
   double den = 1.0 + p.mf * std::pow(a, -p.Ls);
   for (int k = 0; k < p.Ls; ++k) c.apow[k] = std::pow(a, -1.0 - k) / den;
   dim3 blk = block_for(p.Ls);
-  dim3 grid((unsigned)((in.Vh + blk.x - 1) / blk.x), in.nrhs);
+  dim3 grid = grid_for(in, blk, p.Ls);
   if (in.prec == QCD_F64 || out.prec == QCD_F64)
     k_ainv<double><<<grid, blk, 0, st>>>(c, any_view(in), any_view(out), in.Vh, dagger, scale, xv,
                                          x != nullptr, stop);
@@ -143,7 +143,7 @@ void dw_block(const DwParams& p, const Field& in, Field& out, int dagger, double
               cudaStream_t st) {
   if (in.data == out.data) raise(QCD_ERR_ARG, "dw_block: in and out alias");
   dim3 blk = block_for(p.Ls);
-  dim3 grid((unsigned)((in.Vh + blk.x - 1) / blk.x), in.nrhs);
+  dim3 grid = grid_for(in, blk, p.Ls);
   AnyView yv = y ? any_view(*y) : any_view(out);
   double a = 5.0 - p.M5;
   if (in.prec == QCD_F64 || out.prec == QCD_F64)

@@ -303,7 +303,6 @@ __global__ void k_bicg_check(Scal* sc, const double* partial, int nblk, int* ctl
   } else if (s.delta2 > 0.0 && d[2] <= s.delta2 * s.r2_ref) {
     s.flag = FLAG_UPDATE;
   }
-  if (s.flag != FLAG_NONE) *ctl = 1;
 }
 
 // ----------------------------------------------------------------------------- CG kernels
@@ -410,7 +409,6 @@ __global__ void k_cg_check(Scal* sc, const double* partial, int nblk, int* ctl) 
     s.flag = FLAG_CHECK;
   else if (s.delta2 > 0.0 && d[0] <= s.delta2 * s.r2_ref)
     s.flag = FLAG_UPDATE;
-  if (s.flag != FLAG_NONE) *ctl = 1;
 }
 
 // partial sums of Re(a, b)
@@ -433,6 +431,28 @@ __global__ void k_rdot(AnyView a_, AnyView b_, long n, double* partial, const Sc
 }
 
 __global__ void k_reset(int* ctl) { *ctl = 0; }
+
+// End-of-iteration stop decision over all right-hand sides (<<<1, 32>>>).  A
+// right-hand side that has flagged (outer step due, target reached) keeps
+// iterating until every active one has flagged, so that the batch shares one
+// FP64 outer step, unless one of them is overdue: its residual has dropped a
+// further factor 10 past its trigger (or breakdown / NaN, which stop at once
+// where they are detected).
+__global__ void k_decide(const Scal* sc, int nrhs, int* ctl) {
+  if (STOPPED(ctl) || threadIdx.x) return;
+  int nact = 0, nflag = 0, urgent = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    const Scal& s = sc[r];
+    if (!s.active) continue;
+    ++nact;
+    if (s.flag == FLAG_NONE) continue;
+    ++nflag;
+    if (s.flag == FLAG_NAN || s.flag == FLAG_BREAKDOWN) ++urgent;
+    else if (s.flag == FLAG_UPDATE && s.r2 <= 0.01 * s.delta2 * s.r2_ref) ++urgent;
+    else if (s.flag == FLAG_CHECK && s.r2 <= 0.01 * s.stop2) ++urgent;
+  }
+  if (nflag > 0 && (nflag == nact || urgent > 0)) *ctl = 1;
+}
 
 unsigned red_blocks(long n) {
   long b = (n + kThreads - 1) / kThreads;
@@ -501,6 +521,8 @@ struct Solver {
       QCD_LAUNCH_CK();
       k_bicg_check<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
       QCD_LAUNCH_CK();
+      k_decide<<<1, 32, 0, st>>>(sc, nrhs, ctl);
+      QCD_LAUNCH_CK();
     } else {
       k_cg_beta<<<1, 32, 0, st>>>(sc, nrhs, ctl);
       QCD_LAUNCH_CK();
@@ -516,6 +538,8 @@ struct Solver {
                                                 nn, partial, sc, ctl);
       QCD_LAUNCH_CK();
       k_cg_check<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
+      QCD_LAUNCH_CK();
+      k_decide<<<1, 32, 0, st>>>(sc, nrhs, ctl);
       QCD_LAUNCH_CK();
     }
   }
