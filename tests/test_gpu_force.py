@@ -67,14 +67,21 @@ def test_autograd_matches_oracle_gradient(config5):
     assert rel_err(pt.grad, 2 * X_o) < 1e-8
 
 
+# FD tolerance per step.  S = 2.08e6 here, one FP64 ulp of S is 4.6e-10, and at h = 1e-6 the
+# numerator S+ - S- of a gradient component of rms size (3.2) is 6.4e-6 = 1.4e4 ulps: the FP64
+# resolution of S itself caps the quotient at about 1e-4 per ulp of noise, and the two solves
+# differ by ~10 ulps (measured worst deviation 1.1e-3).  At h = 1e-4 the quotient resolves the
+# gradient to ~1e-5 (truncation O(h^2) is far below), so that step carries the tight bound;
+# the oracle gradient (test above) is the 1e-8 pin.
+FD_TOL = {1e-6: 5e-3, 1e-4: 1e-4}
+
+
 @pytest.mark.parametrize("h", [1e-6, 1e-4])
 def test_autograd_central_finite_differences(config5, h):
     """dS/dU on 64 random link components against (S(U + h e) - S(U - h e)) / 2h.
 
-    S is about 1e7 here, so at h = 1e-6 the difference S+ - S- is ~1e-11 of S: the two
-    perturbed solves must make (nearly) the same rounding errors.  Both start from the
-    unperturbed solution and run the same fixed number of FP64 iterations (deterministic
-    reductions), so their rounding errors cancel in the difference.
+    Both perturbed solves start from the unperturbed solution and run the same fixed number
+    of FP64 iterations (deterministic reductions), so their rounding errors largely cancel.
     """
     device()
     from paper_1712_01505_gb300.autograd import wilson_action
@@ -114,4 +121,4 @@ def test_autograd_central_finite_differences(config5, h):
         err = abs(fd - g[mu, x, a, b, ri]) / max(abs(fd), rms)
         worst = max(worst, err)
     print(f"h = {h:g}: S = {S.item():.6e}, worst relative FD deviation {worst:.2e} (rms gradient {rms:.3e})")
-    assert worst < 1e-4
+    assert worst < FD_TOL[h]
