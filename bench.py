@@ -207,7 +207,9 @@ def main():
     ap.add_argument("--workload", default="wilson32", choices=["wilson32", "dwf", "batched", "force"],
                     help="wilson32 (default, the bench line); the others characterise the other "
                          "configurations (domain-wall CG, 12-rhs propagator, force) and print their own line")
-    ap.add_argument("--delta", type=float, default=0.1, help="reliable-update factor of the mixed solve")
+    ap.add_argument("--delta", type=float, default=None,
+                    help="reliable-update factor of the mixed solves (default: 1e-3 for the FP32 Wilson solve "
+                         "of the bench line, the library's per-precision default elsewhere)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -248,7 +250,8 @@ def main():
     out64 = torch.empty(nb64, dtype=torch.uint8, device=dev)
     qcd.field_pack(g, f, "f32", 1, b_dev, in32)
     qcd.field_pack(g, f, "f64", 1, b_dev, in64)
-    solve_kw = dict(method=qcd.BICGSTAB, tol=TOL, inner="f32", use_graph=True, graph_chunk=32, delta=args.delta)
+    delta = 1e-3 if args.delta is None else args.delta
+    solve_kw = dict(method=qcd.BICGSTAB, tol=TOL, inner="f32", use_graph=True, graph_chunk=32, delta=delta)
 
     ev_d0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_d1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -378,7 +381,7 @@ def main():
         "data": "synthetic: smoothed-random SU(3) links and Z2 noise source (seeded)",
         "config": {"workload": WORKLOAD, "lattice": list(L), "kappa": KAPPA, "eps": EPS, "recon": RECON,
                    "solver": "EO BiCGStab, FP32 inner + FP64 reliable updates, CUDA graph chunks of 32",
-                   "tol": TOL, "ndslash_per_step": NDSLASH, "delta": args.delta,
+                   "tol": TOL, "ndslash_per_step": NDSLASH, "delta": delta,
                    "l2": "inputs larger than L2 (links 403 MB, each parity vector 101 MB)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "kernel": "k_hop<FP32,12-real> (D_eo)", "achieved": round(achieved, 1),

@@ -71,12 +71,12 @@ def run_dwf(args):
     for inner in ("f16", "f32", "f64"):
         x = torch.zeros_like(bd)
         qcd.solve(g, f, bd, x, method=qcd.CG_NORMAL, tol=1e-10, inner=inner, use_graph=True, graph_chunk=32,
-                  delta=args.delta)  # warm-up (tuning, workspace)
+                  delta=(args.delta or 0.0))  # warm-up (tuning, workspace)
         x.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         info, _ = qcd.solve(g, f, bd, x, method=qcd.CG_NORMAL, tol=1e-10, inner=inner, use_graph=True,
-                            graph_chunk=32, delta=args.delta)
+                            graph_chunk=32, delta=(args.delta or 0.0))
         torch.cuda.synchronize()
         res[inner] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "iters": info[0]["iters"],
                       "updates": info[0]["outer_updates"], "true_resid": info[0]["true_resid"]}
@@ -106,7 +106,7 @@ def run_batched(args):
     ms1 = _time_launches(lambda: qcd.dslash(g, f, "D_EO", a12[:nb1], o12[:nb1], prec="f32",
                                             layout=qcd.INTERNAL))
     alg12 = Vh * (8 * 48 + 12 * 192)
-    kw = dict(method=qcd.BICGSTAB, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32, delta=args.delta)
+    kw = dict(method=qcd.BICGSTAB, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32, delta=(args.delta or 0.0))
     x = torch.zeros_like(bd)
     qcd.solve(g, f, bd, x, nrhs=12, **kw)  # warm-up
     x.zero_()

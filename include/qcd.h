@@ -119,7 +119,8 @@ typedef struct {
  *   QCD_F32 / QCD_F16: mixed precision with double-precision reliable
  *   updates -- true residual recomputed and solution accumulated in FP64).
  * delta: a reliable update is made when the iterated residual has dropped by
- *   this factor since the last one (0 < delta < 1; 0 selects 0.1).
+ *   this factor since the last one (0 < delta < 1; 0 selects 0.01 for an FP32
+ *   and 0.1 for an FP16 inner solver).
  * use_graph: capture `graph_chunk` inner iterations in one CUDA graph and
  *   check convergence once per graph launch (0 = plain launches).
  * x0_given: x holds an initial guess on entry (warm start).

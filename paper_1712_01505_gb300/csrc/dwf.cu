@@ -29,22 +29,43 @@ struct AinvCoef {
   double mf;
 };
 
-// block: (32 sites) x (8 slices); grid: (ceil(Vh/32), nrhs, ceil(Ls/8))
+// The block stages the input of its SB sites for all Ls slices in shared
+// memory (one HBM read per 5D site), then each thread forms the outputs of its
+// site for slices s = threadIdx.y, threadIdx.y + blockDim.y, ...
+// block: (SB sites) x (256 / SB); grid: (ceil(Vh/SB), nrhs); dynamic shared
+// memory Ls * 24 * SB reals, laid out [s][real][site] (conflict-free reads).
 template <typename R>
 __global__ void __launch_bounds__(256) k_ainv(AinvCoef c, AnyView in, AnyView out, long Vh, int dagger, R scale,
                        AnyView x, int has_x, const int* stop) {
   if (stop && *stop) return;
-  int r = blockIdx.y;
-  long cb = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  int s = blockIdx.z * blockDim.y + threadIdx.y;
-  if (cb >= Vh || s >= c.Ls) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);
+  const int SB = blockDim.x;
+  const int r = blockIdx.y;
+  const int tx = threadIdx.x;
+  const long cb = blockIdx.x * (long)SB + tx;
   const int Ls = c.Ls;
+  for (int s = threadIdx.y; s < Ls; s += blockDim.y) {
+    Cx<R> v[12];
+    if (cb < Vh) {
+      any_load<R>(in, r, (long)s * Vh + cb, v);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = {R(0), R(0)};
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      sm[(s * 24 + 2 * k) * SB + tx] = v[k].re;
+      sm[(s * 24 + 2 * k + 1) * SB + tx] = v[k].im;
+    }
+  }
+  __syncthreads();
+  if (cb >= Vh) return;
+  for (int s = threadIdx.y; s < Ls; s += blockDim.y) {
   Cx<R> acc[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
   for (int sp = 0; sp < Ls; ++sp) {
-    Cx<R> v[12];
-    any_load<R>(in, r, (long)sp * Vh + cb, v);
     // coefficient for the lower-shift (P_+) inverse at (s, sp) and its transpose
     int k1 = s - sp;
     if (k1 < 0) k1 += Ls;
@@ -54,10 +75,13 @@ __global__ void __launch_bounds__(256) k_ainv(AinvCoef c, AnyView in, AnyView ou
     R up = (R)(c.apow[k2] * (sp >= s ? 1.0 : -c.mf));
     R cp = dagger ? up : lo;  // spins 0,1
     R cm = dagger ? lo : up;  // spins 2,3
+    const R* col = sm + (sp * 24) * SB + tx;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc[k] = {fma(cp, v[k].re, acc[k].re), fma(cp, v[k].im, acc[k].im)};
+    for (int k = 0; k < 6; ++k)
+      acc[k] = {fma(cp, col[(2 * k) * SB], acc[k].re), fma(cp, col[(2 * k + 1) * SB], acc[k].im)};
 #pragma unroll
-    for (int k = 6; k < 12; ++k) acc[k] = {fma(cm, v[k].re, acc[k].re), fma(cm, v[k].im, acc[k].im)};
+    for (int k = 6; k < 12; ++k)
+      acc[k] = {fma(cm, col[(2 * k) * SB], acc[k].re), fma(cm, col[(2 * k + 1) * SB], acc[k].im)};
   }
   if (has_x) {
     Cx<R> w[12];
@@ -69,6 +93,7 @@ __global__ void __launch_bounds__(256) k_ainv(AinvCoef c, AnyView in, AnyView ou
     for (int k = 0; k < 12; ++k) acc[k] = {scale * acc[k].re, scale * acc[k].im};
   }
   any_store<R>(out, r, (long)s * Vh + cb, acc);
+  }
 }
 
 // out = A in + c * y  (A^dag for dagger)
@@ -128,14 +153,26 @@ void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double 
   double a = 5.0 - p.M5;
   double den = 1.0 + p.mf * std::pow(a, -p.Ls);
   for (int k = 0; k < p.Ls; ++k) c.apow[k] = std::pow(a, -1.0 - k) / den;
-  dim3 blk = block_for(p.Ls);
-  dim3 grid = grid_for(in, blk, p.Ls);
-  if (in.prec == QCD_F64 || out.prec == QCD_F64)
-    k_ainv<double><<<grid, blk, 0, st>>>(c, any_view(in), any_view(out), in.Vh, dagger, scale, xv,
-                                         x != nullptr, stop);
+  const bool dbl = in.prec == QCD_F64 || out.prec == QCD_F64;
+  const size_t rb = dbl ? sizeof(double) : sizeof(float);
+  // sites per block: as many as fit 96 KB of staging (at least 8)
+  int SB = 32;
+  while (SB > 8 && (size_t)p.Ls * 24 * SB * rb > 96 * 1024) SB /= 2;
+  const size_t smem = (size_t)p.Ls * 24 * SB * rb;
+  dim3 blk(SB, 256 / SB);
+  dim3 grid((unsigned)((in.Vh + SB - 1) / SB), in.nrhs);
+  static bool attr_set = false;
+  if (!attr_set) {
+    QCD_CK(cudaFuncSetAttribute(k_ainv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    QCD_CK(cudaFuncSetAttribute(k_ainv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    attr_set = true;
+  }
+  if (dbl)
+    k_ainv<double><<<grid, blk, smem, st>>>(c, any_view(in), any_view(out), in.Vh, dagger, scale, xv,
+                                            x != nullptr, stop);
   else
-    k_ainv<float><<<grid, blk, 0, st>>>(c, any_view(in), any_view(out), in.Vh, dagger, (float)scale,
-                                        xv, x != nullptr, stop);
+    k_ainv<float><<<grid, blk, smem, st>>>(c, any_view(in), any_view(out), in.Vh, dagger, (float)scale,
+                                           xv, x != nullptr, stop);
   QCD_LAUNCH_CK();
 }
 

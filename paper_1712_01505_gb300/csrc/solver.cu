@@ -623,7 +623,9 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   const int ls = S.ls;
   const bool dwf = f.type == QCD_DWF;
   const int dag = prm.dagger;
-  const double delta = (prm.delta > 0 && prm.delta < 1) ? prm.delta : 0.1;
+  // default reliable-update factor: the FP32 recursion stays accurate over two decades,
+  // the FP16 one over one
+  const double delta = (prm.delta > 0 && prm.delta < 1) ? prm.delta : (prm.inner == QCD_F16 ? 0.1 : 0.01);
 
   S.b_e = ws_field(g, "s.b_e", QCD_F64, ls, nrhs);
   S.b_o = ws_field(g, "s.b_o", QCD_F64, ls, nrhs);
@@ -675,9 +677,13 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   // |b - A x| on the full system from the even-odd residual rhat = bhat - Mhat x_e:
   // Wilson: (rhat, 0);  DWF: (A rhat, 0)  (exact reconstruction of x_o)
   std::vector<double> rn(nrhs), rfull(nrhs);
-  auto true_residual = [&]() {
-    apply_mhat(S.op64, S.x64, S.t64, dag, st, "o64");
-    blas_axpby(1.0, S.bh, -1.0, S.t64, st);  // t64 = bhat - Mhat x
+  auto true_residual = [&](bool x_is_zero) {
+    if (x_is_zero) {
+      blas_copy(S.bh, S.t64, st);  // rhat = bhat
+    } else {
+      apply_mhat(S.op64, S.x64, S.t64, dag, st, "o64");
+      blas_axpby(1.0, S.bh, -1.0, S.t64, st);  // t64 = bhat - Mhat x
+    }
     if (dwf) {
       dw_block(dp, S.t64, S.u64, 0, 0.0, nullptr, st);
       blas_norm2(S.u64, rfull.data(), st, g);
@@ -694,7 +700,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     blas_norm2(S.r64, rn.data(), st, g);
   };
 
-  true_residual();
+  true_residual(!prm.x0_given);
   std::vector<double> target(nrhs);
   std::vector<int> conv(nrhs, 0), status(nrhs, QCD_OK), updates(nrhs, 0), restarts(nrhs, 0);
   int nactive = 0;
@@ -787,7 +793,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
       }
     }
     if (S.inner != QCD_F64) blas_axpby(1.0, S.xin, 1.0, S.x64, st);
-    true_residual();
+    true_residual(false);
     nactive = 0;
     for (int r = 0; r < nrhs; ++r) {
       if (conv[r]) continue;

@@ -232,7 +232,7 @@ def mhat_noalloc(gauge, fermion, inp, out, prec="f32", dagger=False, nrhs=1, str
     return out
 
 
-def solver_params(method=BICGSTAB, tol=1e-10, maxiter=100000, inner="f64", delta=0.1, use_graph=False,
+def solver_params(method=BICGSTAB, tol=1e-10, maxiter=100000, inner="f64", delta=0.0, use_graph=False,
                   graph_chunk=32, x0_given=False, dagger=False) -> SolverParams:
     return SolverParams(method, tol, maxiter, PREC[inner], delta, int(use_graph), graph_chunk, int(x0_given),
                         int(dagger))
