@@ -23,10 +23,12 @@ namespace {
 
 constexpr int kMaxLs = 64;
 
+// coefficients in the kernel's arithmetic type (no FP64 in the FP32 kernels)
+template <typename R>
 struct AinvCoef {
   int Ls;
-  double apow[kMaxLs];  // a^(-1-k) / (1 + m a^-Ls)
-  double mf;
+  R apow[kMaxLs];  // a^(-1-k) / (1 + m a^-Ls)
+  R mf;
 };
 
 // The block stages the input of its SB sites for all Ls slices in shared
@@ -35,7 +37,7 @@ struct AinvCoef {
 // block: (SB sites) x (256 / SB); grid: (ceil(Vh/SB), nrhs); dynamic shared
 // memory Ls * 24 * SB reals, laid out [s][real][site] (conflict-free reads).
 template <typename R>
-__global__ void __launch_bounds__(256) k_ainv(AinvCoef c, AnyView in, AnyView out, long Vh, int dagger, R scale,
+__global__ void __launch_bounds__(256) k_ainv(AinvCoef<R> c, AnyView in, AnyView out, long Vh, int dagger, R scale,
                        AnyView x, int has_x, const int* stop) {
   if (stop && *stop) return;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -69,10 +71,10 @@ __global__ void __launch_bounds__(256) k_ainv(AinvCoef c, AnyView in, AnyView ou
     // coefficient for the lower-shift (P_+) inverse at (s, sp) and its transpose
     int k1 = s - sp;
     if (k1 < 0) k1 += Ls;
-    R lo = (R)(c.apow[k1] * (s >= sp ? 1.0 : -c.mf));
+    R lo = c.apow[k1] * (s >= sp ? R(1) : -c.mf);
     int k2 = sp - s;
     if (k2 < 0) k2 += Ls;
-    R up = (R)(c.apow[k2] * (sp >= s ? 1.0 : -c.mf));
+    R up = c.apow[k2] * (sp >= s ? R(1) : -c.mf);
     R cp = dagger ? up : lo;  // spins 0,1
     R cm = dagger ? lo : up;  // spins 2,3
     const R* col = sm + (sp * 24) * SB + tx;
@@ -147,12 +149,17 @@ void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double 
   if (in.data == out.data || (x && x->data == out.data))
     raise(QCD_ERR_ARG, "dw_ainv: output aliases an input");
   AnyView xv = x ? any_view(*x) : any_view(out);
-  AinvCoef c;
-  c.Ls = p.Ls;
+  AinvCoef<double> c;
+  AinvCoef<float> cf;
+  c.Ls = cf.Ls = p.Ls;
   c.mf = p.mf;
+  cf.mf = (float)p.mf;
   double a = 5.0 - p.M5;
   double den = 1.0 + p.mf * std::pow(a, -p.Ls);
-  for (int k = 0; k < p.Ls; ++k) c.apow[k] = std::pow(a, -1.0 - k) / den;
+  for (int k = 0; k < p.Ls; ++k) {
+    c.apow[k] = std::pow(a, -1.0 - k) / den;
+    cf.apow[k] = (float)c.apow[k];
+  }
   const bool dbl = in.prec == QCD_F64 || out.prec == QCD_F64;
   const size_t rb = dbl ? sizeof(double) : sizeof(float);
   // sites per block: as many as fit 96 KB of staging (at least 8)
@@ -171,7 +178,7 @@ void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double 
     k_ainv<double><<<grid, blk, smem, st>>>(c, any_view(in), any_view(out), in.Vh, dagger, scale, xv,
                                             x != nullptr, stop);
   else
-    k_ainv<float><<<grid, blk, smem, st>>>(c, any_view(in), any_view(out), in.Vh, dagger, (float)scale,
+    k_ainv<float><<<grid, blk, smem, st>>>(cf, any_view(in), any_view(out), in.Vh, dagger, (float)scale,
                                            xv, x != nullptr, stop);
   QCD_LAUNCH_CK();
 }

@@ -110,6 +110,8 @@ LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
     QCD_LAUNCH_CK();
     float ms = 0;
     QCD_CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (getenv("QCD_TUNE_VERBOSE"))
+      fprintf(stderr, "[qcd tune]   %s block %d tile %d: %.4f ms\n", key.c_str(), c.block, c.tile, ms / reps);
     if (ms < best_ms) {
       best_ms = ms;
       best = c;
@@ -117,6 +119,9 @@ LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (getenv("QCD_TUNE_VERBOSE"))
+    fprintf(stderr, "[qcd tune] %s -> block %d tile %d (%.4f ms per launch)\n", key.c_str(), best.block,
+            best.tile, best_ms / reps);
   std::lock_guard<std::mutex> lk(g_mu);
   g_cache[key] = best;
   append_cache(key, best);

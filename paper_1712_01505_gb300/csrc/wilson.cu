@@ -189,6 +189,100 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
   }
 }
 
+// ----------------------------------------------------------------------------- shared-memory links
+// Many slices per site (domain-wall fifth dimension, several right-hand sides):
+// a block of 32 sites x BY slices loads the 8 links of each of its sites once,
+// rebuilds them (12-real) and keeps them in shared memory; every thread then
+// owns one (site, slice) and reads its links from there.  Link traffic per
+// block is 8 x 32 links whatever the number of slices.
+template <int P, int RECON, int MU>
+__device__ __forceinline__ void hop_dir_sm(const HopArgs<P, RECON>& A, const SiteCoords& c, int q,
+                                           typename MathType<P>::type sg,
+                                           const typename MathType<P>::type (*lsm)[18][32], int tx,
+                                           Cx<typename MathType<P>::type> acc[12]) {
+  using R = typename MathType<P>::type;
+  const Geom& g = A.g;
+  const int r = q / A.ls, s = q - r * A.ls;
+#pragma unroll
+  for (int back = 0; back < 2; ++back) {
+    int wrap;
+    int j = neighbour_index(g, c, MU, back ? -1 : +1, &wrap);
+    long ncb = j >> 1;
+    bool neg = wrap && g.apbc[MU];
+    Cx<R> U[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) U[k] = {lsm[2 * MU + back][2 * k][tx], lsm[2 * MU + back][2 * k + 1][tx]};
+    Cx<R> psi[12], h[6], gg[6];
+    A.in.offset_rhs(r).load((long)s * g.Vh + ncb, psi);
+    const R sgn = back ? -sg : sg;
+    project<MU>(psi, sgn, h);
+    if (neg)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) h[k] = -h[k];
+    if (back)
+      link_mul<true>(U, h, gg);
+    else
+      link_mul<false>(U, h, gg);
+    reconstruct_add<MU>(gg, sgn, acc);
+  }
+}
+
+template <int P, int RECON, int BY>
+__global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
+  using R = typename MathType<P>::type;
+  if (A.stop && *A.stop) return;
+  __shared__ R lsm[8][18][32];  // [2 mu + backward][real][site]
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int stile = blockIdx.x % A.ntiles;
+  const int sblock = blockIdx.x / A.ntiles;
+  const int cb = sblock * 32 + tx;
+  const bool valid = cb < A.g.Vh;
+  SiteCoords c;
+  if (valid) c = cb_to_site(A.g, cb, A.out_parity);
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    if (l % BY != ty || !valid) continue;
+    const int mu = l >> 1;
+    Cx<R> U[9];
+    if ((l & 1) == 0) {
+      A.U.load(A.out_parity, mu, cb, U);  // U_mu(x)
+    } else {
+      int wrap;
+      int j = neighbour_index(A.g, c, mu, -1, &wrap);
+      A.U.load(1 - A.out_parity, mu, j >> 1, U);  // U_mu(x - mu)
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      lsm[l][2 * k][tx] = U[k].re;
+      lsm[l][2 * k + 1][tx] = U[k].im;
+    }
+  }
+  __syncthreads();
+  const int q = stile * BY + ty;
+  if (!valid || q >= A.nslices) return;
+  Cx<R> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
+  const R sg = A.dagger ? R(1) : R(-1);
+  hop_dir_sm<P, RECON, 0>(A, c, q, sg, lsm, tx, acc);
+  hop_dir_sm<P, RECON, 1>(A, c, q, sg, lsm, tx, acc);
+  hop_dir_sm<P, RECON, 2>(A, c, q, sg, lsm, tx, acc);
+  hop_dir_sm<P, RECON, 3>(A, c, q, sg, lsm, tx, acc);
+  const R a = (R)A.a;
+  const int r = q / A.ls, s = q - r * A.ls;
+  const long site = (long)s * A.g.Vh + cb;
+  Cx<R> o[12];
+  if (A.xpay) {
+    A.x.offset_rhs(r).load(site, o);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = fmac(a, acc[k], o[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = a * acc[k];
+  }
+  A.out.offset_rhs(r).store(site, o);
+}
+
 Geom dev_geom(const Lattice& lat) {
   Geom g;
   for (int m = 0; m < 4; ++m) {
@@ -224,6 +318,16 @@ void launch_tile(HopLaunch<P, RECON>* L, int block) {
   k_hop<P, RECON, TILE><<<(unsigned)(sblocks * A.ntiles), block, 0, L->st>>>(A);
 }
 
+template <int P, int RECON, int BY>
+void launch_sm(HopLaunch<P, RECON>* L) {
+  HopArgs<P, RECON> A = L->args;
+  A.ntiles = (A.nslices + BY - 1) / BY;
+  long sblocks = (A.g.Vh + 31) / 32;
+  k_hop_sm<P, RECON, BY><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
+}
+
+// cfg.tile > 0: register tile of that many slices per thread (k_hop);
+// cfg.tile < 0: shared-memory links with -tile slices per block (k_hop_sm)
 template <int P, int RECON>
 void run_cfg(void* ctx, const LaunchCfg& cfg) {
   auto* L = (HopLaunch<P, RECON>*)ctx;
@@ -233,7 +337,9 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
     switch (cfg.tile) {
       case 1: launch_tile<P, RECON, 1>(L, cfg.block); break;
       case 2: launch_tile<P, RECON, 2>(L, cfg.block); break;
-      default: launch_tile<P, RECON, 4>(L, cfg.block); break;
+      case 4: launch_tile<P, RECON, 4>(L, cfg.block); break;
+      case -4: launch_sm<P, RECON, 4>(L); break;
+      default: launch_sm<P, RECON, 8>(L); break;
     }
   }
 }
@@ -266,6 +372,8 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
     if (t > 1 && A.nslices < t) continue;
     for (int b : blocks) cands.push_back({b, t});
   }
+  if (P != P64 && A.nslices >= 4) cands.push_back({128, -4});
+  if (P != P64 && A.nslices >= 8) cands.push_back({256, -8});
   char key[160];
   snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay);
