@@ -191,96 +191,121 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
 
 // ----------------------------------------------------------------------------- shared-memory links
 // Many slices per site (domain-wall fifth dimension, several right-hand sides):
-// a block of 32 sites x BY slices loads the 8 links of each of its sites once,
-// rebuilds them (12-real) and keeps them in shared memory; every thread then
-// owns one (site, slice) and reads its links from there.  Link traffic per
-// block is 8 x 32 links whatever the number of slices.
-template <int P, int RECON, int MU>
-__device__ __forceinline__ void hop_dir_sm(const HopArgs<P, RECON>& A, const SiteCoords& c, int q,
-                                           typename MathType<P>::type sg,
-                                           const typename MathType<P>::type (*lsm)[18][32], int tx,
-                                           Cx<typename MathType<P>::type> acc[12]) {
+// a block of 32 sites x BY thread rows loads the 8 links of each of its sites
+// once, rebuilds them (12-real) and keeps them in shared memory together with
+// the 8 neighbour indices and boundary signs of each site; every thread then
+// owns one site and TS slices, reads each link once from shared memory and
+// applies it to its TS slices.  Link traffic per block is 8 x 32 links
+// whatever the number of slices, and the per-site index arithmetic is done once.
+template <typename R>
+struct SmLinks {
+  Cx<R> U[8][9][32];      // [2 mu + backward][element][site]
+  int nb[8][32];          // neighbour checkerboard index
+  unsigned char neg[8][32];  // 1 if the hop carries the antiperiodic sign
+};
+
+template <int P, int RECON, int TS, int L>
+__device__ __forceinline__ void hop_link_sm(const HopArgs<P, RECON>& A, const SmLinks<typename MathType<P>::type>& sm,
+                                            int tx, typename MathType<P>::type sg, const SpinorView<P> (&in)[TS],
+                                            const long (&soff)[TS], int nt,
+                                            Cx<typename MathType<P>::type> (&acc)[TS][12]) {
   using R = typename MathType<P>::type;
-  const Geom& g = A.g;
-  const int r = q / A.ls, s = q - r * A.ls;
+  constexpr int MU = L >> 1;
+  constexpr bool BACK = (L & 1) != 0;
+  const long ncb = sm.nb[L][tx];
+  const bool neg = sm.neg[L][tx];
+  Cx<R> U[9];
 #pragma unroll
-  for (int back = 0; back < 2; ++back) {
-    int wrap;
-    int j = neighbour_index(g, c, MU, back ? -1 : +1, &wrap);
-    long ncb = j >> 1;
-    bool neg = wrap && g.apbc[MU];
-    Cx<R> U[9];
+  for (int k = 0; k < 9; ++k) U[k] = sm.U[L][k][tx];
+  const R sgn = BACK ? -sg : sg;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) U[k] = {lsm[2 * MU + back][2 * k][tx], lsm[2 * MU + back][2 * k + 1][tx]};
+  for (int t = 0; t < TS; ++t) {
+    if (TS > 1 && t >= nt) break;
     Cx<R> psi[12], h[6], gg[6];
-    A.in.offset_rhs(r).load((long)s * g.Vh + ncb, psi);
-    const R sgn = back ? -sg : sg;
+    in[t].load(soff[t] + ncb, psi);
     project<MU>(psi, sgn, h);
     if (neg)
 #pragma unroll
       for (int k = 0; k < 6; ++k) h[k] = -h[k];
-    if (back)
-      link_mul<true>(U, h, gg);
-    else
-      link_mul<false>(U, h, gg);
-    reconstruct_add<MU>(gg, sgn, acc);
+    link_mul<BACK>(U, h, gg);
+    reconstruct_add<MU>(gg, sgn, acc[t]);
   }
 }
 
-template <int P, int RECON, int BY>
+template <int P, int RECON, int BY, int TS>
 __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
   using R = typename MathType<P>::type;
   if (A.stop && *A.stop) return;
-  __shared__ R lsm[8][18][32];  // [2 mu + backward][real][site]
+  __shared__ SmLinks<R> sm;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int stile = blockIdx.x % A.ntiles;
   const int sblock = blockIdx.x / A.ntiles;
   const int cb = sblock * 32 + tx;
   const bool valid = cb < A.g.Vh;
-  SiteCoords c;
-  if (valid) c = cb_to_site(A.g, cb, A.out_parity);
+  if (valid) {
+    SiteCoords c = cb_to_site(A.g, cb, A.out_parity);
 #pragma unroll
-  for (int l = 0; l < 8; ++l) {
-    if (l % BY != ty || !valid) continue;
-    const int mu = l >> 1;
-    Cx<R> U[9];
-    if ((l & 1) == 0) {
-      A.U.load(A.out_parity, mu, cb, U);  // U_mu(x)
-    } else {
+    for (int l = 0; l < 8; ++l) {
+      if (l % BY != ty) continue;
+      const int mu = l >> 1;
       int wrap;
-      int j = neighbour_index(A.g, c, mu, -1, &wrap);
-      A.U.load(1 - A.out_parity, mu, j >> 1, U);  // U_mu(x - mu)
-    }
+      int j = neighbour_index(A.g, c, mu, (l & 1) ? -1 : +1, &wrap);
+      sm.nb[l][tx] = j >> 1;
+      sm.neg[l][tx] = (unsigned char)(wrap && A.g.apbc[mu]);
+      Cx<R> U[9];
+      if ((l & 1) == 0)
+        A.U.load(A.out_parity, mu, cb, U);  // U_mu(x)
+      else
+        A.U.load(1 - A.out_parity, mu, j >> 1, U);  // U_mu(x - mu)
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      lsm[l][2 * k][tx] = U[k].re;
-      lsm[l][2 * k + 1][tx] = U[k].im;
+      for (int k = 0; k < 9; ++k) sm.U[l][k][tx] = U[k];
     }
   }
   __syncthreads();
-  const int q = stile * BY + ty;
-  if (!valid || q >= A.nslices) return;
-  Cx<R> acc[12];
+  const int q0 = (stile * BY + ty) * TS;
+  if (!valid || q0 >= A.nslices) return;
+  const int nt = min(TS, A.nslices - q0);
+  SpinorView<P> in[TS];
+  long soff[TS];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
-  const R sg = A.dagger ? R(1) : R(-1);
-  hop_dir_sm<P, RECON, 0>(A, c, q, sg, lsm, tx, acc);
-  hop_dir_sm<P, RECON, 1>(A, c, q, sg, lsm, tx, acc);
-  hop_dir_sm<P, RECON, 2>(A, c, q, sg, lsm, tx, acc);
-  hop_dir_sm<P, RECON, 3>(A, c, q, sg, lsm, tx, acc);
-  const R a = (R)A.a;
-  const int r = q / A.ls, s = q - r * A.ls;
-  const long site = (long)s * A.g.Vh + cb;
-  Cx<R> o[12];
-  if (A.xpay) {
-    A.x.offset_rhs(r).load(site, o);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) o[k] = fmac(a, acc[k], o[k]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) o[k] = a * acc[k];
+  for (int t = 0; t < TS; ++t) {
+    const int q = min(q0 + t, A.nslices - 1);
+    const int r = q / A.ls, s = q - r * A.ls;
+    in[t] = A.in.offset_rhs(r);
+    soff[t] = (long)s * A.g.Vh;
   }
-  A.out.offset_rhs(r).store(site, o);
+  Cx<R> acc[TS][12];
+#pragma unroll
+  for (int t = 0; t < TS; ++t)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[t][k] = {R(0), R(0)};
+  const R sg = A.dagger ? R(1) : R(-1);
+  hop_link_sm<P, RECON, TS, 0>(A, sm, tx, sg, in, soff, nt, acc);
+  hop_link_sm<P, RECON, TS, 1>(A, sm, tx, sg, in, soff, nt, acc);
+  hop_link_sm<P, RECON, TS, 2>(A, sm, tx, sg, in, soff, nt, acc);
+  hop_link_sm<P, RECON, TS, 3>(A, sm, tx, sg, in, soff, nt, acc);
+  hop_link_sm<P, RECON, TS, 4>(A, sm, tx, sg, in, soff, nt, acc);
+  hop_link_sm<P, RECON, TS, 5>(A, sm, tx, sg, in, soff, nt, acc);
+  hop_link_sm<P, RECON, TS, 6>(A, sm, tx, sg, in, soff, nt, acc);
+  hop_link_sm<P, RECON, TS, 7>(A, sm, tx, sg, in, soff, nt, acc);
+  const R a = (R)A.a;
+#pragma unroll
+  for (int t = 0; t < TS; ++t) {
+    if (TS > 1 && t >= nt) break;
+    const int q = q0 + t;
+    const int r = q / A.ls;
+    const long site = soff[t] + cb;
+    Cx<R> o[12];
+    if (A.xpay) {
+      A.x.offset_rhs(r).load(site, o);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) o[k] = fmac(a, acc[t][k], o[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) o[k] = a * acc[t][k];
+    }
+    A.out.offset_rhs(r).store(site, o);
+  }
 }
 
 Geom dev_geom(const Lattice& lat) {
@@ -318,16 +343,17 @@ void launch_tile(HopLaunch<P, RECON>* L, int block) {
   k_hop<P, RECON, TILE><<<(unsigned)(sblocks * A.ntiles), block, 0, L->st>>>(A);
 }
 
-template <int P, int RECON, int BY>
+template <int P, int RECON, int BY, int TS>
 void launch_sm(HopLaunch<P, RECON>* L) {
   HopArgs<P, RECON> A = L->args;
-  A.ntiles = (A.nslices + BY - 1) / BY;
+  A.ntiles = (A.nslices + BY * TS - 1) / (BY * TS);
   long sblocks = (A.g.Vh + 31) / 32;
-  k_hop_sm<P, RECON, BY><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
+  k_hop_sm<P, RECON, BY, TS><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
 }
 
 // cfg.tile > 0: register tile of that many slices per thread (k_hop);
-// cfg.tile < 0: shared-memory links with -tile slices per block (k_hop_sm)
+// cfg.tile < 0: shared-memory links (k_hop_sm), -tile = 10 * BY + TS for
+// BY thread rows of TS slices each
 template <int P, int RECON>
 void run_cfg(void* ctx, const LaunchCfg& cfg) {
   auto* L = (HopLaunch<P, RECON>*)ctx;
@@ -338,8 +364,10 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case 1: launch_tile<P, RECON, 1>(L, cfg.block); break;
       case 2: launch_tile<P, RECON, 2>(L, cfg.block); break;
       case 4: launch_tile<P, RECON, 4>(L, cfg.block); break;
-      case -4: launch_sm<P, RECON, 4>(L); break;
-      default: launch_sm<P, RECON, 8>(L); break;
+      case -41: launch_sm<P, RECON, 4, 1>(L); break;
+      case -42: launch_sm<P, RECON, 4, 2>(L); break;
+      case -81: launch_sm<P, RECON, 8, 1>(L); break;
+      default: launch_sm<P, RECON, 8, 2>(L); break;
     }
   }
 }
@@ -372,8 +400,10 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
     if (t > 1 && A.nslices < t) continue;
     for (int b : blocks) cands.push_back({b, t});
   }
-  if (P != P64 && A.nslices >= 4) cands.push_back({128, -4});
-  if (P != P64 && A.nslices >= 8) cands.push_back({256, -8});
+  if (P != P64 && A.nslices >= 4) cands.push_back({128, -41});
+  if (P != P64 && A.nslices >= 8) cands.push_back({128, -42});
+  if (P != P64 && A.nslices >= 8) cands.push_back({256, -81});
+  if (P != P64 && A.nslices >= 16) cands.push_back({256, -82});
   char key[160];
   snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay);
