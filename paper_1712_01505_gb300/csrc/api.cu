@@ -76,12 +76,14 @@ void* Workspace::get(const std::string& name, size_t bytes) {
   void* p = nullptr;
   QCD_CK(cudaMalloc(&p, bytes));
   bufs[name] = {p, bytes};
+  ++generation;
   return p;
 }
 
 void Workspace::release() {
   for (auto& kv : bufs) cudaFree(kv.second.p);
   bufs.clear();
+  ++generation;
 }
 
 Field ws_field(qcd_gauge* g, const std::string& name, int prec, int ls, int nrhs) {
@@ -253,6 +255,8 @@ qcd_status qcd_gauge_load(const qcd_geom* geom, const void* U, void* stream, qcd
   if (s != QCD_OK) {
     if (g) {
       cudaDeviceSynchronize();
+      for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second.exec);
+      g->graphs.clear();
       g->ws.release();
       if (g->work) cudaStreamDestroy(g->work);
       if (g->ev_in) cudaEventDestroy(g->ev_in);
@@ -270,6 +274,8 @@ qcd_status qcd_gauge_free(qcd_gauge* g) {
   return guarded([&] {
     if (!g) return;
     cudaDeviceSynchronize();
+    for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second.exec);
+    g->graphs.clear();
     g->ws.release();
     cudaStreamDestroy(g->work);
     cudaEventDestroy(g->ev_in);

@@ -69,6 +69,7 @@ struct Workspace {
     size_t bytes = 0;
   };
   std::map<std::string, Buf> bufs;
+  long generation = 0;  // bumped whenever a buffer is (re)allocated or freed
   void* get(const std::string& name, size_t bytes);
   void release();
 };
@@ -76,7 +77,16 @@ struct Workspace {
 }  // namespace qcd
 
 // ----------------------------------------------------------------------------- the handle
+namespace qcd {
+// an instantiated CUDA graph of solver iterations and the kernels it holds
+struct CachedGraph {
+  cudaGraphExec_t exec = nullptr;
+  long nodes = 0;
+};
+}  // namespace qcd
+
 struct qcd_gauge {
+  std::map<std::string, qcd::CachedGraph> graphs;  // captured solver chunks, by graph key
   qcd::Lattice lat;
   void* U64 = nullptr;  // FP64, 18 reals
   void* U32 = nullptr;  // FP32, lat.recon reals

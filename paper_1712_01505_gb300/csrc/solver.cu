@@ -479,9 +479,6 @@ struct Solver {
   Field b_e, b_o, bh, x64, r64, t64, u64;   // FP64
   Field r, rt, p, v, s, t, q, w, xin;        // inner
   std::vector<Scal> hsc;
-  cudaGraphExec_t gexec = nullptr;
-  int gchunk = 0;
-  long gnodes = 0;
 
   bool bicg() const { return prm.method == QCD_BICGSTAB; }
   long n() const { return r.nsites(); }
@@ -544,11 +541,23 @@ struct Solver {
     }
   }
 
+  // Everything a captured chunk bakes into its kernel arguments: the fields'
+  // addresses (and the workspace generation, which changes whenever a buffer
+  // is reallocated), the operator's parameters and the chunk length.
+  std::string graph_key(int k) const {
+    char buf[512];
+    snprintf(buf, sizeof buf, "m%d i%d n%d l%d d%d t%d k%a M%a m%a L%d ws%ld c%d sc%p %p %p %p %p %p %p %p %p %p %p",
+             prm.method, inner, nrhs, ls, prm.dagger, f.type, f.kappa, f.M5, f.mf, f.Ls, g->ws.generation, k,
+             (void*)sc, (void*)ctl, (void*)partial, r.data, p.data, v.data, s.data, t.data, q.data, w.data,
+             rt.data);
+    return std::string(buf) + " x" + std::to_string((uintptr_t)xin.data);
+  }
+
   void run_chunk(int k, bool graph) {
     if (graph) {
-      if (!gexec || gchunk != k) {
-        if (gexec) cudaGraphExecDestroy(gexec);
-        gexec = nullptr;
+      std::string key = graph_key(k);
+      auto it = g->graphs.find(key);
+      if (it == g->graphs.end()) {
         cudaGraph_t gr;
         long c0 = launches_so_far();
         QCD_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -556,14 +565,15 @@ struct Solver {
         QCD_LAUNCH_CK();
         for (int i = 0; i < k; ++i) body();
         QCD_CK(cudaStreamEndCapture(st, &gr));
-        gnodes = launches_so_far() - c0;  // captured, not yet executed
+        CachedGraph cg;
+        cg.nodes = launches_so_far() - c0;  // captured, not yet executed
         set_launches(c0);
-        QCD_CK(cudaGraphInstantiate(&gexec, gr, 0));
+        QCD_CK(cudaGraphInstantiate(&cg.exec, gr, 0));
         cudaGraphDestroy(gr);
-        gchunk = k;
+        it = g->graphs.emplace(key, cg).first;
       }
-      QCD_CK(cudaGraphLaunch(gexec, st));
-      note_launches(gnodes);
+      QCD_CK(cudaGraphLaunch(it->second.exec, st));
+      note_launches(it->second.nodes);
     } else {
       k_reset<<<1, 1, 0, st>>>(ctl);
       QCD_LAUNCH_CK();
@@ -759,6 +769,11 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   const int chunk = graph ? (prm.graph_chunk > 0 ? prm.graph_chunk : 32) : 16;
   bool first = true;
   int done_reason = QCD_OK;
+  // Chunk length: the iterations between two outer steps are nearly constant
+  // (each removes the same factor delta), so after the first gap has been seen
+  // a chunk stops short of the expected next outer step and the last few
+  // iterations run in chunks of 8 / 2: few launches are wasted after a stop.
+  int last_stop = 0, gap = 0;
   while (nactive > 0) {
     int maxit = 0;
     for (int r = 0; r < nrhs; ++r)
@@ -767,19 +782,32 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
       done_reason = QCD_ERR_NOCONV;
       break;
     }
-    int k = std::min(chunk, maxiter - maxit);
+    int k = chunk;
+    if (gap > 0) {
+      int remaining = last_stop + gap - maxit;
+      k = remaining >= chunk ? chunk : (remaining >= 8 && chunk >= 8 ? 8 : std::min(2, chunk));
+    }
+    const bool capped = k > maxiter - maxit;
+    if (capped) k = maxiter - maxit;
     // the first iteration runs un-captured so that the stencil tuner can time
     if (first) {
       S.run_chunk(1, false);
       first = false;
     } else {
-      S.run_chunk(k, graph && k == chunk);
+      S.run_chunk(k, graph && !capped);
     }
     S.download();
     bool any = false;
     for (int r = 0; r < nrhs; ++r)
       if (S.hsc[r].active && S.hsc[r].flag != FLAG_NONE) any = true;
     if (!any) continue;
+    {
+      int now = 0;
+      for (int r = 0; r < nrhs; ++r)
+        if (!conv[r]) now = std::max(now, S.hsc[r].iters);
+      if (now > last_stop) gap = now - last_stop;
+      last_stop = now;
+    }
     // ---- outer FP64 step for every right-hand side
     bool need_full_restart = false;
     for (int r = 0; r < nrhs; ++r) {
@@ -806,7 +834,6 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     restart_from_residual(need_full_restart);
     S.upload();
   }
-  if (S.gexec) cudaGraphExecDestroy(S.gexec);
 
   // ---- reconstruct the odd sites and write the solution
   if (!dwf) {
