@@ -208,7 +208,7 @@ def main():
                     help="wilson32 (default, the bench line); the others characterise the other "
                          "configurations (domain-wall CG, 12-rhs propagator, force) and print their own line")
     ap.add_argument("--delta", type=float, default=None,
-                    help="reliable-update factor of the mixed solves (default: 1e-3 for the FP32 Wilson solve "
+                    help="reliable-update factor of the mixed solves (default: 1e-4 for the FP32 Wilson solves "
                          "of the bench line, the library's per-precision default elsewhere)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -250,7 +250,7 @@ def main():
     out64 = torch.empty(nb64, dtype=torch.uint8, device=dev)
     qcd.field_pack(g, f, "f32", 1, b_dev, in32)
     qcd.field_pack(g, f, "f64", 1, b_dev, in64)
-    delta = 1e-3 if args.delta is None else args.delta
+    delta = 1e-4 if args.delta is None else args.delta
     solve_kw = dict(method=qcd.BICGSTAB, tol=TOL, inner="f32", use_graph=True, graph_chunk=32, delta=delta)
 
     ev_d0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]

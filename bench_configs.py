@@ -125,7 +125,8 @@ def run_batched(args):
     ms1 = _time_launches(lambda: qcd.dslash(g, f, "D_EO", a12[:nb1], o12[:nb1], prec="f32",
                                             layout=qcd.INTERNAL))
     alg12 = Vh * (8 * 48 + 12 * 192)
-    kw = dict(method=qcd.BICGSTAB, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32, delta=(args.delta or 0.0))
+    kw = dict(method=qcd.BICGSTAB, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32,
+              delta=(args.delta or 1e-4))
     x = torch.zeros_like(bd)
     qcd.solve(g, f, bd, x, nrhs=12, **kw)  # warm-up
     x.zero_()

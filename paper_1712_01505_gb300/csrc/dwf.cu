@@ -29,13 +29,22 @@ struct AinvCoef {
   int Ls;
   R apow[kMaxLs];  // a^(-1-k) / (1 + m a^-Ls)
   R mf;
+  R ainv;  // 1 / a
 };
 
-// The block stages the input of its SB sites for all Ls slices in shared
-// memory (one HBM read per 5D site), then each thread forms the outputs of its
-// site for slices s = threadIdx.y, threadIdx.y + blockDim.y, ...
+// A^-1 per column (site, colour, spin) in O(Ls): on the P_+ spins A is
+// a - (lower shift, wrap -m), so with the first slice from the closed form,
+//   psi_0 = a^-1 chi_0 / den - m sum_{s'>0} a^(-1-(Ls-s')) chi_s' / den,
+// the rest follows by forward substitution psi_s = (chi_s + psi_{s-1}) / a;
+// on the P_- spins (upper shift) the last slice comes from the closed form,
+//   psi_{Ls-1} = a^-1 chi_{Ls-1} / den - m sum_{s'<Ls-1} a^(-2-s') chi_s' / den,
+// and backward substitution psi_s = (chi_s + psi_{s+1}) / a gives the rest.
+// A^dag = A^T exchanges the two recurrences between the chiralities.
+// The block stages its SB sites for all Ls slices in shared memory (one HBM
+// read per 5D site), runs the recurrences in place (thread (site, k) owns the
+// complex components k, k + blockDim.y, ...), then writes (site, slice) units.
 // block: (SB sites) x (256 / SB); grid: (ceil(Vh/SB), nrhs); dynamic shared
-// memory Ls * 24 * SB reals, laid out [s][real][site] (conflict-free reads).
+// memory Ls * 24 * SB reals laid out [s][real][site].
 template <typename R>
 __global__ void __launch_bounds__(256) k_ainv(AinvCoef<R> c, AnyView in, AnyView out, long Vh, int dagger, R scale,
                        AnyView x, int has_x, const int* stop) {
@@ -47,6 +56,7 @@ __global__ void __launch_bounds__(256) k_ainv(AinvCoef<R> c, AnyView in, AnyView
   const int tx = threadIdx.x;
   const long cb = blockIdx.x * (long)SB + tx;
   const int Ls = c.Ls;
+  const int cs = 24 * SB;  // stride between slices
   for (int s = threadIdx.y; s < Ls; s += blockDim.y) {
     Cx<R> v[12];
     if (cb < Vh) {
@@ -57,44 +67,64 @@ __global__ void __launch_bounds__(256) k_ainv(AinvCoef<R> c, AnyView in, AnyView
     }
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      sm[(s * 24 + 2 * k) * SB + tx] = v[k].re;
-      sm[(s * 24 + 2 * k + 1) * SB + tx] = v[k].im;
+      sm[s * cs + (2 * k) * SB + tx] = v[k].re;
+      sm[s * cs + (2 * k + 1) * SB + tx] = v[k].im;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 12; k += blockDim.y) {
+    R* re = sm + (2 * k) * SB + tx;
+    R* im = sm + (2 * k + 1) * SB + tx;
+    const bool lower = (k < 6) != (dagger != 0);
+    if (lower) {
+      R pr = c.apow[0] * re[0], pi = c.apow[0] * im[0];
+      for (int sp = 1; sp < Ls; ++sp) {
+        const R w = -c.mf * c.apow[Ls - sp];
+        pr = fma(w, re[sp * cs], pr);
+        pi = fma(w, im[sp * cs], pi);
+      }
+      re[0] = pr;
+      im[0] = pi;
+      for (int s = 1; s < Ls; ++s) {
+        pr = (re[s * cs] + pr) * c.ainv;
+        pi = (im[s * cs] + pi) * c.ainv;
+        re[s * cs] = pr;
+        im[s * cs] = pi;
+      }
+    } else {
+      const int l = Ls - 1;
+      R pr = c.apow[0] * re[l * cs], pi = c.apow[0] * im[l * cs];
+      for (int sp = 0; sp < l; ++sp) {
+        const R w = -c.mf * c.apow[sp + 1];
+        pr = fma(w, re[sp * cs], pr);
+        pi = fma(w, im[sp * cs], pi);
+      }
+      re[l * cs] = pr;
+      im[l * cs] = pi;
+      for (int s = l - 1; s >= 0; --s) {
+        pr = (re[s * cs] + pr) * c.ainv;
+        pi = (im[s * cs] + pi) * c.ainv;
+        re[s * cs] = pr;
+        im[s * cs] = pi;
+      }
     }
   }
   __syncthreads();
   if (cb >= Vh) return;
   for (int s = threadIdx.y; s < Ls; s += blockDim.y) {
-  Cx<R> acc[12];
+    Cx<R> acc[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
-  for (int sp = 0; sp < Ls; ++sp) {
-    // coefficient for the lower-shift (P_+) inverse at (s, sp) and its transpose
-    int k1 = s - sp;
-    if (k1 < 0) k1 += Ls;
-    R lo = c.apow[k1] * (s >= sp ? R(1) : -c.mf);
-    int k2 = sp - s;
-    if (k2 < 0) k2 += Ls;
-    R up = c.apow[k2] * (sp >= s ? R(1) : -c.mf);
-    R cp = dagger ? up : lo;  // spins 0,1
-    R cm = dagger ? lo : up;  // spins 2,3
-    const R* col = sm + (sp * 24) * SB + tx;
+    for (int k = 0; k < 12; ++k) acc[k] = {sm[s * cs + (2 * k) * SB + tx], sm[s * cs + (2 * k + 1) * SB + tx]};
+    if (has_x) {
+      Cx<R> w[12];
+      any_load<R>(x, r, (long)s * Vh + cb, w);
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
-      acc[k] = {fma(cp, col[(2 * k) * SB], acc[k].re), fma(cp, col[(2 * k + 1) * SB], acc[k].im)};
+      for (int k = 0; k < 12; ++k) acc[k] = {fma(scale, acc[k].re, w[k].re), fma(scale, acc[k].im, w[k].im)};
+    } else {
 #pragma unroll
-    for (int k = 6; k < 12; ++k)
-      acc[k] = {fma(cm, col[(2 * k) * SB], acc[k].re), fma(cm, col[(2 * k + 1) * SB], acc[k].im)};
-  }
-  if (has_x) {
-    Cx<R> w[12];
-    any_load<R>(x, r, (long)s * Vh + cb, w);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = {fma(scale, acc[k].re, w[k].re), fma(scale, acc[k].im, w[k].im)};
-  } else {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = {scale * acc[k].re, scale * acc[k].im};
-  }
-  any_store<R>(out, r, (long)s * Vh + cb, acc);
+      for (int k = 0; k < 12; ++k) acc[k] = {scale * acc[k].re, scale * acc[k].im};
+    }
+    any_store<R>(out, r, (long)s * Vh + cb, acc);
   }
 }
 
@@ -160,6 +190,8 @@ void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double 
     c.apow[k] = std::pow(a, -1.0 - k) / den;
     cf.apow[k] = (float)c.apow[k];
   }
+  c.ainv = 1.0 / a;
+  cf.ainv = (float)c.ainv;
   const bool dbl = in.prec == QCD_F64 || out.prec == QCD_F64;
   const size_t rb = dbl ? sizeof(double) : sizeof(float);
   // sites per block: as many as fit 96 KB of staging (at least 8)
