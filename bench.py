@@ -231,6 +231,7 @@ def main():
     dev = torch.device("cuda", local)
 
     from paper_1712_01505_gb300 import inputs, qcd
+    from paper_1712_01505_gb300.replicas import replica_reduce
 
     V = int(np.prod(L))
     Vh = V // 2
@@ -310,11 +311,6 @@ def main():
     n_launch = qcd.kernel_launches() - n0
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-        dist.barrier()
     d_ms = [ev_d0[i].elapsed_time(ev_d1[i]) / NDSLASH for i in range(args.steps)]
     s_ms = [ev_s0[i].elapsed_time(ev_s1[i]) for i in range(args.steps)]
     dslash_avg_ms = sum(d_ms) / len(d_ms)
@@ -323,13 +319,16 @@ def main():
             raise SystemExit(f"solve failed to converge: {inf}")
 
     def hops_in_solve(inf):
-        # 4 inner half-dslashes per BiCGStab iteration; FP64: 1 (source) + 2 per true
-        # residual (outer_updates + 1 of them) + 1 (reconstruction) + 2 (final residual)
-        return 4 * inf["iters"] + 1 + 2 * (inf["outer_updates"] + 1) + 1 + 2
+        # 4 inner half-dslashes per BiCGStab iteration; FP64: 1 (source), 2 per outer step
+        # (the true residual; none before the first since x0 = 0), 1 (reconstruction),
+        # 2 (final full-system residual)
+        return 4 * inf["iters"] + 1 + 2 * inf["outer_updates"] + 1 + 2
 
     hops = sum(NDSLASH + 1 + hops_in_solve(inf) for inf in infos)
-    flops = FLOP_SITE * Vh * hops
-    value = flops / (total_ms / 1e3) / 1e9 * world
+    # whole job: the slowest rank's time, every rank's work
+    total_ms, hops_all = replica_reduce(total_ms, hops, dist, dev)
+    flops = FLOP_SITE * Vh * hops_all
+    value = flops / (total_ms / 1e3) / 1e9
     hbm, peak_kind = peaks()
     alg_bytes = BYTES_SITE_FP32[RECON] * Vh
     achieved = alg_bytes / (dslash_avg_ms / 1e3) / 1e9
@@ -370,7 +369,8 @@ def main():
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_hops = 1 + hops_in_solve(info_e[0])
-    e2e_val = FLOP_SITE * Vh * e2e_hops / (min(e2e_ms) / 1e3) / 1e9 * world
+    e2e_t, e2e_hops_all = replica_reduce(min(e2e_ms), e2e_hops, dist, dev)
+    e2e_val = FLOP_SITE * Vh * e2e_hops_all / (e2e_t / 1e3) / 1e9
     spinor_bytes = V * 12 * 16
 
     mixed_ms = statistics.median(s_ms)
