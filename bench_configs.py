@@ -178,6 +178,15 @@ def run_force(args):
     X = torch.from_numpy(inputs.gaussian_source((V, 4, 3), 1)).to(dev)
     out_t = torch.empty((4, V, 3, 3, 2), dtype=torch.float64, device=dev)
     ms = _time_launches(lambda: qcd.force(g, f, X, pt, out_t))
+    if args.profile != "none":  # ncu: profile 3 launches of the force kernel
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(3):
+            qcd.force(g, f, X, pt, out_t)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print("profile force done", flush=True)
+        return
     out = {"workload": "force_wilson_16x16x16x16_kappa0.12", "backward_ms": round(min(times[1:]) * 1e3, 3),
            "force_kernel_ms": round(ms, 4),
            "force_kernel_gbs": round(V * (2 * 192 + 4 * 144) / ms / 1e6, 1)}

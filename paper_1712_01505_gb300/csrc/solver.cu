@@ -23,6 +23,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -716,8 +717,14 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   int nactive = 0;
   for (int r = 0; r < nrhs; ++r) {
     target[r] = prm.tol * bnorm[r];
-    if (bnorm[r] == 0.0 || rfull[r] <= target[r]) conv[r] = 1;
-    else ++nactive;
+    if (!std::isfinite(bnorm[r])) {  // NaN or Inf in the source: nothing to iterate on
+      status[r] = QCD_ERR_NAN;
+      conv[r] = 2;
+    } else if (bnorm[r] == 0.0 || rfull[r] <= target[r]) {
+      conv[r] = 1;
+    } else {
+      ++nactive;
+    }
   }
 
   auto restart_from_residual = [&](bool full) {
@@ -859,7 +866,9 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     qcd_solve_info& in = info[r];
     in.iters = S.hsc[r].iters;
     in.outer_updates = updates[r];
-    double res = bnorm[r] > 0 ? std::sqrt(re_[r] + ro_[r]) / bnorm[r] : 0.0;
+    // |b| = 0 gives x = 0 exactly; a non-finite |b| or residual is reported as such
+    double res = bnorm[r] > 0 ? std::sqrt(re_[r] + ro_[r]) / bnorm[r]
+                              : (bnorm[r] == 0.0 ? 0.0 : std::numeric_limits<double>::quiet_NaN());
     in.true_resid = res;
     in.converged = res <= prm.tol;
     in.status = in.converged ? QCD_OK : (status[r] != QCD_OK ? status[r] : (int)QCD_ERR_NOCONV);
