@@ -45,17 +45,19 @@ __device__ __forceinline__ void project(const Cx<R> psi[12], R sg, Cx<R> h[6]) {
   }
 }
 
-// acc += (g, sg B^dag g)
+// acc += f (g, sg B^dag g), f = +-1 the boundary factor of the hop (folded into
+// the accumulating FMAs instead of negating the half spinor)
 template <int MU, typename R>
-__device__ __forceinline__ void reconstruct_add(const Cx<R> g[6], R sg, Cx<R> acc[12]) {
+__device__ __forceinline__ void reconstruct_add(const Cx<R> g[6], R sg, R f, Cx<R> acc[12]) {
+  const R fs = f * sg;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     Cx<R> b0, b1;
     apply_Bdag<MU>(g[c], g[3 + c], b0, b1);
-    acc[c] = acc[c] + g[c];
-    acc[3 + c] = acc[3 + c] + g[3 + c];
-    acc[6 + c] = fmac(sg, b0, acc[6 + c]);
-    acc[9 + c] = fmac(sg, b1, acc[9 + c]);
+    acc[c] = fmac(f, g[c], acc[c]);
+    acc[3 + c] = fmac(f, g[3 + c], acc[3 + c]);
+    acc[6 + c] = fmac(fs, b0, acc[6 + c]);
+    acc[9 + c] = fmac(fs, b1, acc[9 + c]);
   }
 }
 
@@ -104,7 +106,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCo
     int wrap;
     int j = neighbour_index(g, c, MU, +1, &wrap);
     long ncb = j >> 1;
-    bool neg = wrap && g.apbc[MU];
+    const R f = (wrap && g.apbc[MU]) ? R(-1) : R(1);
     Cx<R> U[9];
     A.U.load(A.out_parity, MU, cb, U);
 #pragma unroll
@@ -115,11 +117,8 @@ __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCo
       Cx<R> psi[12], h[6], gg[6];
       A.in.offset_rhs(r).load((long)s * g.Vh + ncb, psi);
       project<MU>(psi, sg, h);
-      if (neg)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) h[k] = -h[k];
       link_mul<false>(U, h, gg);
-      reconstruct_add<MU>(gg, sg, acc[t]);
+      reconstruct_add<MU>(gg, sg, f, acc[t]);
     }
   }
   // backward: (1 - sg gamma) U_mu(x - mu)^dag in(x - mu)
@@ -127,7 +126,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCo
     int wrap;
     int j = neighbour_index(g, c, MU, -1, &wrap);
     long ncb = j >> 1;
-    bool neg = wrap && g.apbc[MU];
+    const R f = (wrap && g.apbc[MU]) ? R(-1) : R(1);
     Cx<R> U[9];
     A.U.load(1 - A.out_parity, MU, ncb, U);
 #pragma unroll
@@ -138,11 +137,8 @@ __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCo
       Cx<R> psi[12], h[6], gg[6];
       A.in.offset_rhs(r).load((long)s * g.Vh + ncb, psi);
       project<MU>(psi, -sg, h);
-      if (neg)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) h[k] = -h[k];
       link_mul<true>(U, h, gg);
-      reconstruct_add<MU>(gg, -sg, acc[t]);
+      reconstruct_add<MU>(gg, -sg, f, acc[t]);
     }
   }
 }
@@ -213,7 +209,7 @@ __device__ __forceinline__ void hop_link_sm(const HopArgs<P, RECON>& A, const Sm
   constexpr int MU = L >> 1;
   constexpr bool BACK = (L & 1) != 0;
   const long ncb = sm.nb[L][tx];
-  const bool neg = sm.neg[L][tx];
+  const R f = sm.neg[L][tx] ? R(-1) : R(1);
   Cx<R> U[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) U[k] = sm.U[L][k][tx];
@@ -224,11 +220,8 @@ __device__ __forceinline__ void hop_link_sm(const HopArgs<P, RECON>& A, const Sm
     Cx<R> psi[12], h[6], gg[6];
     in[t].load(soff[t] + ncb, psi);
     project<MU>(psi, sgn, h);
-    if (neg)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) h[k] = -h[k];
     link_mul<BACK>(U, h, gg);
-    reconstruct_add<MU>(gg, sgn, acc[t]);
+    reconstruct_add<MU>(gg, sgn, f, acc[t]);
   }
 }
 
