@@ -106,7 +106,10 @@ __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCo
     int wrap;
     int j = neighbour_index(g, c, MU, +1, &wrap);
     long ncb = j >> 1;
-    const R f = (wrap && g.apbc[MU]) ? R(-1) : R(1);
+    // boundary sign: folded into the accumulating FMAs in FP64 (ALU-bound,
+    // saves instructions), applied to the half spinor in FP32/FP16 (memory-bound)
+    const bool neg = wrap && g.apbc[MU];
+    const R f = (P == P64 && neg) ? R(-1) : R(1);
     Cx<R> U[9];
     A.U.load(A.out_parity, MU, cb, U);
 #pragma unroll
@@ -117,8 +120,14 @@ __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCo
       Cx<R> psi[12], h[6], gg[6];
       A.in.offset_rhs(r).load((long)s * g.Vh + ncb, psi);
       project<MU>(psi, sg, h);
+      if (P != P64 && neg)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) h[k] = -h[k];
       link_mul<false>(U, h, gg);
-      reconstruct_add<MU>(gg, sg, f, acc[t]);
+      if constexpr (P == P64)
+        reconstruct_add<MU>(gg, sg, f, acc[t]);
+      else
+        reconstruct_add<MU>(gg, sg, R(1), acc[t]);
     }
   }
   // backward: (1 - sg gamma) U_mu(x - mu)^dag in(x - mu)
@@ -126,7 +135,8 @@ __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCo
     int wrap;
     int j = neighbour_index(g, c, MU, -1, &wrap);
     long ncb = j >> 1;
-    const R f = (wrap && g.apbc[MU]) ? R(-1) : R(1);
+    const bool neg = wrap && g.apbc[MU];
+    const R f = (P == P64 && neg) ? R(-1) : R(1);
     Cx<R> U[9];
     A.U.load(1 - A.out_parity, MU, ncb, U);
 #pragma unroll
@@ -137,8 +147,14 @@ __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCo
       Cx<R> psi[12], h[6], gg[6];
       A.in.offset_rhs(r).load((long)s * g.Vh + ncb, psi);
       project<MU>(psi, -sg, h);
+      if (P != P64 && neg)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) h[k] = -h[k];
       link_mul<true>(U, h, gg);
-      reconstruct_add<MU>(gg, -sg, f, acc[t]);
+      if constexpr (P == P64)
+        reconstruct_add<MU>(gg, -sg, f, acc[t]);
+      else
+        reconstruct_add<MU>(gg, -sg, R(1), acc[t]);
     }
   }
 }
@@ -209,7 +225,7 @@ __device__ __forceinline__ void hop_link_sm(const HopArgs<P, RECON>& A, const Sm
   constexpr int MU = L >> 1;
   constexpr bool BACK = (L & 1) != 0;
   const long ncb = sm.nb[L][tx];
-  const R f = sm.neg[L][tx] ? R(-1) : R(1);
+  const bool neg = sm.neg[L][tx];
   Cx<R> U[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) U[k] = sm.U[L][k][tx];
@@ -220,8 +236,11 @@ __device__ __forceinline__ void hop_link_sm(const HopArgs<P, RECON>& A, const Sm
     Cx<R> psi[12], h[6], gg[6];
     in[t].load(soff[t] + ncb, psi);
     project<MU>(psi, sgn, h);
+    if (neg)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) h[k] = -h[k];
     link_mul<BACK>(U, h, gg);
-    reconstruct_add<MU>(gg, sgn, f, acc[t]);
+    reconstruct_add<MU>(gg, sgn, R(1), acc[t]);
   }
 }
 
