@@ -115,8 +115,20 @@ void zero_parity_canon(const Lattice& lat, int parity, double* canon, int nvec, 
 // with H -> H^dag for dagger; all slices (ls) and right-hand sides of `in`.
 // `stop` (device int, may be null): the kernel does nothing when *stop != 0
 // (used by the solver's captured iteration chunks).
+// `red` (may be null; single right-hand side, FP32/FP64, x given): an inner
+// product fused into the epilogue, written as FP64 per-block partial sums
+// partial[block * 4 + k] with the number of blocks in *npartial:
+//   mode 1: (rt, out)          -> k = 0, 1 (re, im)
+//   mode 2: (out, x), |out|^2  -> k = 0, 1, 2
+struct RedSpec {
+  int mode;
+  const Field* rt;
+  double* partial;
+  int* npartial;
+};
 void hop(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int dagger, double a,
-         const Field* x, cudaStream_t st, const int* stop = nullptr, bool allow_tuning = true);
+         const Field* x, cudaStream_t st, const int* stop = nullptr, bool allow_tuning = true,
+         const RedSpec* red = nullptr);
 
 // ----------------------------------------------------------------------------- domain wall (dwf.cu)
 struct DwParams {
@@ -148,8 +160,9 @@ struct OpCtx {
   int prec;
 };
 // Schur operator on even sites: out = Mhat in (dagger: Mhat^dag); uses workspace temporaries
+// `red` (Wilson only) is forwarded to the final stencil, whose epilogue forms out.
 void apply_mhat(const OpCtx& c, const Field& in, Field& out, int dagger, cudaStream_t st,
-                const char* tag, const int* stop = nullptr);
+                const char* tag, const int* stop = nullptr, const RedSpec* red = nullptr);
 // out_p = in_p - kappa H in_other (Wilson) or A in_p - 1/2 H in_other (DWF), parity p
 void apply_full_parity(const OpCtx& c, const Field& in_same, const Field& in_other, Field& out,
                        int parity, int dagger, cudaStream_t st, const char* tag);

@@ -16,15 +16,16 @@
 namespace qcd {
 
 void apply_mhat(const OpCtx& c, const Field& in, Field& out, int dagger, cudaStream_t st,
-                const char* tag, const int* stop) {
+                const char* tag, const int* stop, const RedSpec* red) {
   std::string t = tag;
   if (c.f.type == QCD_WILSON) {
     Field tmp = ws_field(c.g, t + ".mhat.t", c.prec, in.ls, in.nrhs);
     const double k2 = c.f.kappa * c.f.kappa;
     hop(c.g, in, tmp, 1, dagger, 1.0, nullptr, st, stop);
-    hop(c.g, tmp, out, 0, dagger, -k2, &in, st, stop);
+    hop(c.g, tmp, out, 0, dagger, -k2, &in, st, stop, true, red);
     return;
   }
+  if (red) raise(QCD_ERR_UNSUPPORTED, "fused reductions are for the Wilson operator");
   DwParams p{c.f.Ls, c.f.M5, c.f.mf};
   Field t1 = ws_field(c.g, t + ".mhat.t1", c.prec, in.ls, in.nrhs);
   Field t2 = ws_field(c.g, t + ".mhat.t2", c.prec, in.ls, in.nrhs);

@@ -149,13 +149,14 @@ __global__ void k_cdot(AnyView a_, AnyView b_, long n, double* partial, const Sc
 }
 
 // alpha = rho / (rt, v)                                        <<<nrhs, 256>>>
-__global__ void k_bicg_alpha(Scal* sc, const double* partial, int nblk, int* ctl) {
+// nblk_dev (may be null): number of partials written by a stencil with a fused reduction
+__global__ void k_bicg_alpha(Scal* sc, const double* partial, int nblk, int* ctl, const int* nblk_dev) {
   if (STOPPED(ctl)) return;
   int r = blockIdx.x;
   Scal& s = sc[r];
   if (!s.active) return;
   double d[2];
-  sum_partials<2>(partial, nblk, r, d);
+  sum_partials<2>(partial, nblk_dev ? *nblk_dev : nblk, r, d);
   if (threadIdx.x) return;
   double2 rv = make_double2(d[0], d[1]);
   double2 rho = make_double2(s.rho[0], s.rho[1]);
@@ -219,13 +220,13 @@ __global__ void k_ts_tt(AnyView t_, AnyView s_, long n, double* partial, const S
 }
 
 // omega = (t, s) / (t, t)
-__global__ void k_bicg_omega(Scal* sc, const double* partial, int nblk, int* ctl) {
+__global__ void k_bicg_omega(Scal* sc, const double* partial, int nblk, int* ctl, const int* nblk_dev) {
   if (STOPPED(ctl)) return;
   int r = blockIdx.x;
   Scal& s = sc[r];
   if (!s.active) return;
   double d[3];
-  sum_partials<3>(partial, nblk, r, d);
+  sum_partials<3>(partial, nblk_dev ? *nblk_dev : nblk, r, d);
   if (threadIdx.x) return;
   if (bad(d[0]) || bad(d[1]) || bad(d[2])) {
     s.flag = FLAG_NAN;
@@ -482,6 +483,9 @@ struct Solver {
   std::vector<Scal> hsc;
 
   bool bicg() const { return prm.method == QCD_BICGSTAB; }
+  // BiCGStab inner products fused into the stencil epilogue: one Wilson
+  // right-hand side stored in FP32 or FP64
+  bool fused() const { return bicg() && f.type == QCD_WILSON && nrhs == 1 && inner != QCD_F16; }
   long n() const { return r.nsites(); }
 
   void body() {
@@ -502,18 +506,32 @@ struct Solver {
       QCD_LAUNCH_CK();
       k_bicg_p<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(p), any_view(v), nn, sc, ctl);
       QCD_LAUNCH_CK();
-      apply_mhat(opin, p, v, dag, st, "in", ctl);
-      k_cdot<R><<<grid, kThreads, 0, st>>>(any_view(rt), any_view(v), nn, partial, sc, ctl);
-      QCD_LAUNCH_CK();
-      k_bicg_alpha<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
-      QCD_LAUNCH_CK();
-      k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl);
-      QCD_LAUNCH_CK();
-      apply_mhat(opin, s, t, dag, st, "in", ctl);
-      k_ts_tt<R><<<grid, kThreads, 0, st>>>(any_view(t), any_view(s), nn, partial, sc, ctl);
-      QCD_LAUNCH_CK();
-      k_bicg_omega<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
-      QCD_LAUNCH_CK();
+      if (fused()) {
+        // (rt, v) and (t, s), |t|^2 formed in the epilogue of the stencil that writes v / t
+        int* npart = ctl + 2;
+        RedSpec red1{1, &rt, partial, npart}, red2{2, nullptr, partial, npart};
+        apply_mhat(opin, p, v, dag, st, "in", ctl, &red1);
+        k_bicg_alpha<<<nrhs, 1024, 0, st>>>(sc, partial, nblk, ctl, npart);
+        QCD_LAUNCH_CK();
+        k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl);
+        QCD_LAUNCH_CK();
+        apply_mhat(opin, s, t, dag, st, "in", ctl, &red2);
+        k_bicg_omega<<<nrhs, 1024, 0, st>>>(sc, partial, nblk, ctl, npart);
+        QCD_LAUNCH_CK();
+      } else {
+        apply_mhat(opin, p, v, dag, st, "in", ctl);
+        k_cdot<R><<<grid, kThreads, 0, st>>>(any_view(rt), any_view(v), nn, partial, sc, ctl);
+        QCD_LAUNCH_CK();
+        k_bicg_alpha<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl, nullptr);
+        QCD_LAUNCH_CK();
+        k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl);
+        QCD_LAUNCH_CK();
+        apply_mhat(opin, s, t, dag, st, "in", ctl);
+        k_ts_tt<R><<<grid, kThreads, 0, st>>>(any_view(t), any_view(s), nn, partial, sc, ctl);
+        QCD_LAUNCH_CK();
+        k_bicg_omega<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl, nullptr);
+        QCD_LAUNCH_CK();
+      }
       k_bicg_xr<R, RX><<<grid, kThreads, 0, st>>>(any_view(xin), any_view(p), any_view(s), any_view(t),
                                                   any_view(r), any_view(rt), nn, partial, sc, ctl);
       QCD_LAUNCH_CK();
@@ -660,7 +678,9 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   S.nblk = red_blocks(S.r.nsites());
   S.sc = (Scal*)g->ws.get("s.scal", sizeof(Scal) * nrhs);
   S.ctl = (int*)g->ws.get("s.ctl", sizeof(int) * 4);
-  S.partial = (double*)g->ws.get("s.partial", sizeof(double) * S.nblk * nrhs * kMaxPartial);
+  // room for the reduction kernels' partials and for one per stencil block (64 sites)
+  const size_t npart = std::max<size_t>((size_t)S.nblk * nrhs, (size_t)(lat.Vh / 64 + 1));
+  S.partial = (double*)g->ws.get("s.partial", sizeof(double) * npart * kMaxPartial);
   S.hsc.assign(nrhs, Scal{});
 
   // ---- even-odd source: b_hat on the even sites

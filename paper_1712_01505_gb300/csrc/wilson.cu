@@ -93,6 +93,10 @@ struct HopArgs {
   LinkView<P, RECON> U;
   SpinorView<P> in, out, x;
   const int* stop;
+  int red;             // 0: none; 1: (rt, out); 2: (out, x) and |out|^2
+  SpinorView<P> rt;
+  double* partial;     // [block][4]
+  int* npartial;
 };
 
 template <int P, int RECON, int TILE, int MU>
@@ -198,6 +202,59 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
       for (int k = 0; k < 12; ++k) o[k] = a * acc[t][k];
     }
     A.out.offset_rhs(r).store(site, o);
+  }
+}
+
+// Single right-hand side, out = x + a H in, with a BiCGStab inner product
+// formed in the epilogue from the values just stored (FP32 / FP64 storage,
+// so the stored and the computed values agree): RED = 1 gives (rt, out),
+// RED = 2 gives (out, x) and |out|^2.  Per-site sums in R, per-thread and
+// per-block sums in FP64; one partial per block, block 0 records the count.
+template <int P, int RECON, int RED>
+__global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
+  using R = typename MathType<P>::type;
+  if (A.stop && *A.stop) return;
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[3] = {0.0, 0.0, 0.0};
+  if (cb < A.g.Vh) {
+    SiteCoords c = cb_to_site(A.g, cb, A.out_parity);
+    Cx<R> acc[1][12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
+    const R sg = A.dagger ? R(1) : R(-1);
+    hop_dir<P, RECON, 1, 0>(A, c, cb, 0, sg, acc);
+    hop_dir<P, RECON, 1, 1>(A, c, cb, 0, sg, acc);
+    hop_dir<P, RECON, 1, 2>(A, c, cb, 0, sg, acc);
+    hop_dir<P, RECON, 1, 3>(A, c, cb, 0, sg, acc);
+    const R a = (R)A.a;
+    Cx<R> xs[12], o[12];
+    A.x.load(cb, xs);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = fmac(a, acc[0][k], xs[k]);
+    A.out.store(cb, o);
+    Cx<R> d = {R(0), R(0)};
+    if (RED == 1) {
+      Cx<R> w[12];
+      A.rt.load(cb, w);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) d = cjmadd(w[k], o[k], d);
+    } else {
+      R oo = R(0);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        d = cjmadd(o[k], xs[k], d);
+        oo = fma(o[k].re, o[k].re, fma(o[k].im, o[k].im, oo));
+      }
+      v[2] = (double)oo;
+    }
+    v[0] = (double)d.re;
+    v[1] = (double)d.im;
+  }
+  block_sum<3>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) A.partial[(long)blockIdx.x * 4 + k] = v[k];
+    if (blockIdx.x == 0) *A.npartial = gridDim.x;
   }
 }
 
@@ -352,6 +409,16 @@ void launch_tile(HopLaunch<P, RECON>* L, int block) {
   HopArgs<P, RECON> A = L->args;
   A.ntiles = (A.nslices + TILE - 1) / TILE;
   long sblocks = (A.g.Vh + block - 1) / block;
+  if constexpr (TILE == 1 && P != P16) {
+    if (A.red == 1) {
+      k_hop_red<P, RECON, 1><<<(unsigned)sblocks, block, 0, L->st>>>(A);
+      return;
+    }
+    if (A.red == 2) {
+      k_hop_red<P, RECON, 2><<<(unsigned)sblocks, block, 0, L->st>>>(A);
+      return;
+    }
+  }
   k_hop<P, RECON, TILE><<<(unsigned)(sblocks * A.ntiles), block, 0, L->st>>>(A);
 }
 
@@ -387,9 +454,20 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
 template <int P, int RECON>
 void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& out, int out_parity,
               int dagger, double a, const Field* x, cudaStream_t st, const int* stop,
-              bool allow_tuning) {
+              bool allow_tuning, const RedSpec* red) {
   HopLaunch<P, RECON> L;
   HopArgs<P, RECON>& A = L.args;
+  A.red = 0;
+  A.partial = nullptr;
+  A.npartial = nullptr;
+  if (red && red->mode) {
+    if (P == P16 || in.nrhs * in.ls != 1 || !x || (red->mode == 1 && !red->rt))
+      raise(QCD_ERR_ARG, "fused reduction needs one FP32/FP64 right-hand side and an x term");
+    A.red = red->mode;
+    A.partial = red->partial;
+    A.npartial = red->npartial;
+    if (red->rt) A.rt = sview<P>(*red->rt);
+  }
   A.g = dev_geom(gh->lat);
   A.out_parity = out_parity;
   A.ls = in.ls;
@@ -416,9 +494,13 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64 && A.nslices >= 8) cands.push_back({128, -42});
   if (P != P64 && A.nslices >= 8) cands.push_back({256, -81});
   if (P != P64 && A.nslices >= 16) cands.push_back({256, -82});
+  if (A.red) {  // the fused reduction exists for one slice per thread only
+    cands.clear();
+    for (int b : blocks) cands.push_back({b, 1});
+  }
   char key[160];
-  snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d", P, RECON, gh->lat.L[0],
-           gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay);
+  snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d red%d", P, RECON, gh->lat.L[0],
+           gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay, A.red);
   LaunchCfg cfg = tune(key, cands, &run_cfg<P, RECON>, &L, st, allow_tuning);
   run_cfg<P, RECON>(&L, cfg);
   QCD_LAUNCH_CK();
@@ -427,7 +509,7 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
 }  // namespace
 
 void hop(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int dagger, double a,
-         const Field* x, cudaStream_t st, const int* stop, bool allow_tuning) {
+         const Field* x, cudaStream_t st, const int* stop, bool allow_tuning, const RedSpec* red) {
   if (in.prec != out.prec || (x && x->prec != out.prec))
     raise(QCD_ERR_ARG, "hop: mixed precisions are not supported");
   if (in.data == out.data || (x && x->data == out.data))
@@ -435,19 +517,19 @@ void hop(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int da
   if (in.Vh == 0 || in.nrhs * in.ls == 0) return;
   switch (in.prec) {
     case QCD_F64:
-      hop_impl<P64, 18>(g, g->U64, in, out, out_parity, dagger, a, x, st, stop, allow_tuning);
+      hop_impl<P64, 18>(g, g->U64, in, out, out_parity, dagger, a, x, st, stop, allow_tuning, red);
       break;
     case QCD_F32:
       if (g->lat.recon == 12)
-        hop_impl<P32, 12>(g, g->U32, in, out, out_parity, dagger, a, x, st, stop, allow_tuning);
+        hop_impl<P32, 12>(g, g->U32, in, out, out_parity, dagger, a, x, st, stop, allow_tuning, red);
       else
-        hop_impl<P32, 18>(g, g->U32, in, out, out_parity, dagger, a, x, st, stop, allow_tuning);
+        hop_impl<P32, 18>(g, g->U32, in, out, out_parity, dagger, a, x, st, stop, allow_tuning, red);
       break;
     default:
       if (g->lat.recon == 12)
-        hop_impl<P16, 12>(g, g->U16, in, out, out_parity, dagger, a, x, st, stop, allow_tuning);
+        hop_impl<P16, 12>(g, g->U16, in, out, out_parity, dagger, a, x, st, stop, allow_tuning, red);
       else
-        hop_impl<P16, 18>(g, g->U16, in, out, out_parity, dagger, a, x, st, stop, allow_tuning);
+        hop_impl<P16, 18>(g, g->U16, in, out, out_parity, dagger, a, x, st, stop, allow_tuning, red);
   }
 }
 
