@@ -476,6 +476,8 @@ struct Solver {
   Scal* sc = nullptr;
   int* ctl = nullptr;
   double* partial = nullptr;
+  double* bpartial = nullptr;  // per-block partials of the fused stencil reductions
+  int* counters = nullptr;     // their group counters (zero between launches)
   unsigned nblk = 1;
   // fields
   Field b_e, b_o, bh, x64, r64, t64, u64;   // FP64
@@ -509,7 +511,8 @@ struct Solver {
       if (fused()) {
         // (rt, v) and (t, s), |t|^2 formed in the epilogue of the stencil that writes v / t
         int* npart = ctl + 2;
-        RedSpec red1{1, &rt, partial, npart}, red2{2, nullptr, partial, npart};
+        RedSpec red1{1, &rt, bpartial, partial, counters, npart};
+        RedSpec red2{2, nullptr, bpartial, partial, counters, npart};
         apply_mhat(opin, p, v, dag, st, "in", ctl, &red1);
         k_bicg_alpha<<<nrhs, 1024, 0, st>>>(sc, partial, nblk, ctl, npart);
         QCD_LAUNCH_CK();
@@ -678,9 +681,19 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   S.nblk = red_blocks(S.r.nsites());
   S.sc = (Scal*)g->ws.get("s.scal", sizeof(Scal) * nrhs);
   S.ctl = (int*)g->ws.get("s.ctl", sizeof(int) * 4);
-  // room for the reduction kernels' partials and for one per stencil block (64 sites)
-  const size_t npart = std::max<size_t>((size_t)S.nblk * nrhs, (size_t)(lat.Vh / 64 + 1));
+  // partials of the reduction kernels (and the group sums of the fused stencil
+  // reductions); per-block partials of the fused reductions (blocks of >= 64
+  // sites) and one counter per group of 64 blocks, zeroed once here
+  const size_t nstencil_blocks = (size_t)(lat.Vh / 64 + 1);
+  const size_t npart = std::max<size_t>((size_t)S.nblk * nrhs, nstencil_blocks / 64 + 1);
   S.partial = (double*)g->ws.get("s.partial", sizeof(double) * npart * kMaxPartial);
+  if (S.fused()) {
+    S.bpartial = (double*)g->ws.get("s.bpartial", sizeof(double) * nstencil_blocks * kMaxPartial);
+    const size_t ngroups = nstencil_blocks / 64 + 2;
+    const long gen = g->ws.generation;
+    S.counters = (int*)g->ws.get("s.counters", sizeof(int) * ngroups);
+    if (g->ws.generation != gen) QCD_CK(cudaMemsetAsync(S.counters, 0, sizeof(int) * ngroups, st));
+  }
   S.hsc.assign(nrhs, Scal{});
 
   // ---- even-odd source: b_hat on the even sites
