@@ -262,44 +262,34 @@ __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
   for (int k = 0; k < 3; ++k)
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
   __shared__ double wsum[8][3];
-  __shared__ int last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0)
 #pragma unroll
     for (int k = 0; k < 3; ++k) wsum[warp][k] = (double)v[k];
   __syncthreads();
+  if (threadIdx.x != 0) return;
+  // thread 0 alone: block partial, then, in the group's last block, the group sum
   const int ngroups = (gridDim.x + kRedGroup - 1) / kRedGroup;
   const int grp = blockIdx.x / kRedGroup;
-  if (threadIdx.x == 0) {
-    double b[3] = {0.0, 0.0, 0.0};
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+  double b[3] = {0.0, 0.0, 0.0};
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) b[k] += wsum[w][k];
+    for (int k = 0; k < 3; ++k) b[k] += wsum[w][k];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) A.partial[(long)blockIdx.x * 4 + k] = b[k];
-    __threadfence();
-    const int members = min(kRedGroup, (int)gridDim.x - grp * kRedGroup);
-    last = (atomicAdd(&A.counters[grp], 1) == members - 1);
-    if (blockIdx.x == 0) *A.npartial = ngroups;
-  }
-  __syncthreads();
-  if (last && warp == 0) {  // the group's last block: sum its members in order
-    __threadfence();
-    const int first = grp * kRedGroup;
-    const int members = min(kRedGroup, (int)gridDim.x - first);
-    double g[3] = {0.0, 0.0, 0.0};
-    for (int m = lane; m < members; m += 32)
+  for (int k = 0; k < 3; ++k) A.partial[(long)blockIdx.x * 4 + k] = b[k];
+  if (blockIdx.x == 0) *A.npartial = ngroups;
+  __threadfence();
+  const int first = grp * kRedGroup;
+  const int members = min(kRedGroup, (int)gridDim.x - first);
+  if (atomicAdd(&A.counters[grp], 1) != members - 1) return;
+  __threadfence();
+  double g[3] = {0.0, 0.0, 0.0};
+  for (int m = 0; m < members; ++m)  // fixed order
 #pragma unroll
-      for (int k = 0; k < 3; ++k) g[k] += __ldcg(&A.partial[(long)(first + m) * 4 + k]);  // L2, not a stale L1
+    for (int k = 0; k < 3; ++k) g[k] += __ldcg(&A.partial[(long)(first + m) * 4 + k]);  // L2, not a stale L1
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-      for (int o = 16; o > 0; o >>= 1) g[k] += __shfl_down_sync(0xffffffffu, g[k], o);
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) A.gpartial[(long)grp * 4 + k] = g[k];
-      A.counters[grp] = 0;
-    }
-  }
+  for (int k = 0; k < 3; ++k) A.gpartial[(long)grp * 4 + k] = g[k];
+  A.counters[grp] = 0;
 }
 
 // ----------------------------------------------------------------------------- shared-memory links
