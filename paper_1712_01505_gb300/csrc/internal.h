@@ -116,15 +116,18 @@ void zero_parity_canon(const Lattice& lat, int parity, double* canon, int nvec, 
 // `stop` (device int, may be null): the kernel does nothing when *stop != 0
 // (used by the solver's captured iteration chunks).
 // `red` (may be null; single right-hand side, FP32/FP64, x given): an inner
-// product fused into the epilogue.  Every warp writes an FP64 partial sum to
-// partial[k * n + warp] with n, the number of warps, in *npartial (room for
-// Vh / 32 + 8 warps):
+// product fused into the epilogue.  Every block writes an FP64 partial sum to
+// partial[block * 4 + k]; the last block of each group of 64 blocks to finish
+// (counted in counters[group], which start at 0 and are reset) sums its group
+// in order into gpartial[group * 4 + k]; *npartial receives the number of groups.
 //   mode 1: (rt, out)          -> k = 0, 1 (re, im)
 //   mode 2: (out, x), |out|^2  -> k = 0, 1, 2
 struct RedSpec {
   int mode;
   const Field* rt;
   double* partial;
+  double* gpartial;
+  int* counters;
   int* npartial;
 };
 void hop(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int dagger, double a,

@@ -77,21 +77,6 @@ __device__ void sum_partials(const double* partial, int nblk, int r, double out[
   for (int k = 0; k < NR; ++k) out[k] = v[k];
 }
 
-// Sum n component-major partials partial[k * n + i] (one right-hand side),
-// each thread over a fixed stride, then the block tree: a fixed order.
-template <int NR>
-__device__ void sum_partials_soa(const double* partial, int n, double out[NR]) {
-  double v[NR];
-#pragma unroll
-  for (int k = 0; k < NR; ++k) v[k] = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < NR; ++k) v[k] += partial[(long)k * n + i];
-  block_sum<NR>(v);
-#pragma unroll
-  for (int k = 0; k < NR; ++k) out[k] = v[k];
-}
-
 template <int NR>
 __device__ __forceinline__ void write_partial(double v[NR], double* partial, int r) {
   block_sum<NR>(v);
@@ -164,18 +149,14 @@ __global__ void k_cdot(AnyView a_, AnyView b_, long n, double* partial, const Sc
 }
 
 // alpha = rho / (rt, v)                                        <<<nrhs, 256>>>
-// nblk_dev (may be null): number of component-major per-warp partials written
-// by a stencil with a fused reduction (one right-hand side)
+// nblk_dev (may be null): number of partials written by a stencil with a fused reduction
 __global__ void k_bicg_alpha(Scal* sc, const double* partial, int nblk, int* ctl, const int* nblk_dev) {
   if (STOPPED(ctl)) return;
   int r = blockIdx.x;
   Scal& s = sc[r];
   if (!s.active) return;
   double d[2];
-  if (nblk_dev)
-    sum_partials_soa<2>(partial, *nblk_dev, d);
-  else
-    sum_partials<2>(partial, nblk, r, d);
+  sum_partials<2>(partial, nblk_dev ? *nblk_dev : nblk, r, d);
   if (threadIdx.x) return;
   double2 rv = make_double2(d[0], d[1]);
   double2 rho = make_double2(s.rho[0], s.rho[1]);
@@ -245,10 +226,7 @@ __global__ void k_bicg_omega(Scal* sc, const double* partial, int nblk, int* ctl
   Scal& s = sc[r];
   if (!s.active) return;
   double d[3];
-  if (nblk_dev)
-    sum_partials_soa<3>(partial, *nblk_dev, d);
-  else
-    sum_partials<3>(partial, nblk, r, d);
+  sum_partials<3>(partial, nblk_dev ? *nblk_dev : nblk, r, d);
   if (threadIdx.x) return;
   if (bad(d[0]) || bad(d[1]) || bad(d[2])) {
     s.flag = FLAG_NAN;
@@ -498,7 +476,8 @@ struct Solver {
   Scal* sc = nullptr;
   int* ctl = nullptr;
   double* partial = nullptr;
-  double* wpartial = nullptr;  // per-warp partials of the fused stencil reductions
+  double* bpartial = nullptr;  // per-block partials of the fused stencil reductions
+  int* counters = nullptr;     // their group counters (zero between launches)
   unsigned nblk = 1;
   // fields
   Field b_e, b_o, bh, x64, r64, t64, u64;   // FP64
@@ -532,14 +511,15 @@ struct Solver {
       if (fused()) {
         // (rt, v) and (t, s), |t|^2 formed in the epilogue of the stencil that writes v / t
         int* npart = ctl + 2;
-        RedSpec red1{1, &rt, wpartial, npart}, red2{2, nullptr, wpartial, npart};
+        RedSpec red1{1, &rt, bpartial, partial, counters, npart};
+        RedSpec red2{2, nullptr, bpartial, partial, counters, npart};
         apply_mhat(opin, p, v, dag, st, "in", ctl, &red1);
-        k_bicg_alpha<<<nrhs, 1024, 0, st>>>(sc, wpartial, nblk, ctl, npart);
+        k_bicg_alpha<<<nrhs, 1024, 0, st>>>(sc, partial, nblk, ctl, npart);
         QCD_LAUNCH_CK();
         k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl, &red2);
-        k_bicg_omega<<<nrhs, 1024, 0, st>>>(sc, wpartial, nblk, ctl, npart);
+        k_bicg_omega<<<nrhs, 1024, 0, st>>>(sc, partial, nblk, ctl, npart);
         QCD_LAUNCH_CK();
       } else {
         apply_mhat(opin, p, v, dag, st, "in", ctl);
@@ -701,11 +681,19 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   S.nblk = red_blocks(S.r.nsites());
   S.sc = (Scal*)g->ws.get("s.scal", sizeof(Scal) * nrhs);
   S.ctl = (int*)g->ws.get("s.ctl", sizeof(int) * 4);
-  // partials of the reduction kernels; per-warp partials of the fused stencil
-  // reductions (component-major, room for Vh / 32 + 8 warps)
-  S.partial = (double*)g->ws.get("s.partial", sizeof(double) * S.nblk * nrhs * kMaxPartial);
-  if (S.fused())
-    S.wpartial = (double*)g->ws.get("s.wpartial", sizeof(double) * (lat.Vh / 32 + 8) * kMaxPartial);
+  // partials of the reduction kernels (and the group sums of the fused stencil
+  // reductions); per-block partials of the fused reductions (blocks of >= 64
+  // sites) and one counter per group of 64 blocks, zeroed once here
+  const size_t nstencil_blocks = (size_t)(lat.Vh / 64 + 1);
+  const size_t npart = std::max<size_t>((size_t)S.nblk * nrhs, nstencil_blocks / 64 + 1);
+  S.partial = (double*)g->ws.get("s.partial", sizeof(double) * npart * kMaxPartial);
+  if (S.fused()) {
+    S.bpartial = (double*)g->ws.get("s.bpartial", sizeof(double) * nstencil_blocks * kMaxPartial);
+    const size_t ngroups = nstencil_blocks / 64 + 2;
+    const long gen = g->ws.generation;
+    S.counters = (int*)g->ws.get("s.counters", sizeof(int) * ngroups);
+    if (g->ws.generation != gen) QCD_CK(cudaMemsetAsync(S.counters, 0, sizeof(int) * ngroups, st));
+  }
   S.hsc.assign(nrhs, Scal{});
 
   // ---- even-odd source: b_hat on the even sites

@@ -95,7 +95,9 @@ struct HopArgs {
   const int* stop;
   int red;             // 0: none; 1: (rt, out); 2: (out, x) and |out|^2
   SpinorView<P> rt;
-  double* partial;     // [component][warp]
+  double* partial;     // [block][4]
+  double* gpartial;    // [group of 64 blocks][4]
+  int* counters;       // [group]
   int* npartial;
 };
 
@@ -209,9 +211,11 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
 // formed in the epilogue from the values just stored (FP32 / FP64 storage,
 // so the stored and the computed values agree): RED = 1 gives (rt, out),
 // RED = 2 gives (out, x) and |out|^2.  Sums within a warp in R (FP64 adds
-// on 1M threads would cost GB300's slow FP64 pipe tens of microseconds); each
-// warp stores its sum as one FP64 partial, which the solver's scalar kernel
-// adds up in a fixed order.  No barrier, fence or atomic in the stencil.
+// on 1M threads would cost GB300's slow FP64 pipe tens of microseconds),
+// across warps and blocks in FP64: one partial per block, then the last
+// block of each group of 64 blocks sums the group (fixed order, so the result
+// does not depend on block scheduling).
+constexpr int kRedGroup = 64;
 
 template <int P, int RECON, int RED>
 __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
@@ -257,13 +261,45 @@ __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
 #pragma unroll
   for (int k = 0; k < 3; ++k)
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-  // one FP64 partial per warp, stored component-major: partial[k * nwarps + warp]
-  const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
-  const long gw = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if ((threadIdx.x & 31) == 0)
+  __shared__ double wsum[8][3];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) A.partial[k * nwarps + gw] = (double)v[k];
-  if (blockIdx.x == 0 && threadIdx.x == 0) *A.npartial = (int)nwarps;
+    for (int k = 0; k < 3; ++k) wsum[warp][k] = (double)v[k];
+  __syncthreads();
+  const int ngroups = (gridDim.x + kRedGroup - 1) / kRedGroup;
+  const int grp = blockIdx.x / kRedGroup;
+  if (threadIdx.x == 0) {
+    double b[3] = {0.0, 0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) b[k] += wsum[w][k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) A.partial[(long)blockIdx.x * 4 + k] = b[k];
+    __threadfence();
+    const int members = min(kRedGroup, (int)gridDim.x - grp * kRedGroup);
+    last = (atomicAdd(&A.counters[grp], 1) == members - 1);
+    if (blockIdx.x == 0) *A.npartial = ngroups;
+  }
+  __syncthreads();
+  if (last && warp == 0) {  // the group's last block: sum its members in order
+    __threadfence();
+    const int first = grp * kRedGroup;
+    const int members = min(kRedGroup, (int)gridDim.x - first);
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int m = lane; m < members; m += 32)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) g[k] += __ldcg(&A.partial[(long)(first + m) * 4 + k]);  // L2, not a stale L1
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      for (int o = 16; o > 0; o >>= 1) g[k] += __shfl_down_sync(0xffffffffu, g[k], o);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) A.gpartial[(long)grp * 4 + k] = g[k];
+      A.counters[grp] = 0;
+    }
+  }
 }
 
 // ----------------------------------------------------------------------------- shared-memory links
@@ -467,12 +503,16 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   HopArgs<P, RECON>& A = L.args;
   A.red = 0;
   A.partial = nullptr;
+  A.gpartial = nullptr;
+  A.counters = nullptr;
   A.npartial = nullptr;
   if (red && red->mode) {
     if (P == P16 || in.nrhs * in.ls != 1 || !x || (red->mode == 1 && !red->rt))
       raise(QCD_ERR_ARG, "fused reduction needs one FP32/FP64 right-hand side and an x term");
     A.red = red->mode;
     A.partial = red->partial;
+    A.gpartial = red->gpartial;
+    A.counters = red->counters;
     A.npartial = red->npartial;
     if (red->rt) A.rt = sview<P>(*red->rt);
   }
