@@ -38,6 +38,7 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+from paper_1712_01505_gb300 import metrics  # noqa: E402  (flop / byte model, no GPU code)
 
 METRIC = "dslash GFLOP/s & %HBM roofline; mixed vs FP64 solve time to rel. residual 1e-10"
 L = (32, 32, 32, 64)
@@ -46,9 +47,9 @@ EPS, GAUGE_SEED, KAPPA, SRC_SEED = 0.2, 2, 0.125, 0
 RECON = 12
 TOL = 1e-10
 NDSLASH = 10
-FLOP_SITE = 1320                       # per output site of one half-dslash (hopping term)
-BYTES_SITE_FP32 = {12: 8 * 48 + 96 + 96, 18: 8 * 72 + 96 + 96}   # compulsory: links + in + out
-BYTES_SITE_FP64 = 8 * 144 + 192 + 192
+FLOP_SITE = metrics.HOP_FLOP_SITE      # 1320 per output site of one half-dslash (hopping term)
+BYTES_SITE_FP32 = {r: int(metrics.hop_compulsory_bytes("f32", r)) for r in (12, 18)}  # links + in + out
+BYTES_SITE_FP64 = int(metrics.hop_compulsory_bytes("f64", 18))
 WORKLOAD = "wilson_32x32x32x64_kappa0.125_eps0.2_z2"
 PROFILE = os.path.join(ROOT, "profiles", "wilson_dslash_fp32_32x32x32x64.md")
 KERNEL_SOURCES = ["paper_1712_01505_gb300/csrc/wilson.cu", "paper_1712_01505_gb300/csrc/common.cuh"]

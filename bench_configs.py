@@ -18,7 +18,7 @@ import time
 import numpy as np
 import torch
 
-from paper_1712_01505_gb300 import inputs, qcd
+from paper_1712_01505_gb300 import inputs, metrics, qcd
 
 BC = (1, 1, 1, -1)
 
@@ -75,7 +75,7 @@ def run_dwf(args):
         ms = _time_launches(lambda: qcd.dslash(g, f, "D_EO", a_, o_, prec=prec, layout=qcd.INTERNAL))
         ms_m = _time_launches(lambda: qcd.dslash(g, f, "MHAT", a_, o_, prec=prec, layout=qcd.INTERNAL), n=10)
         alg = Vh * (8 * link_b + Ls * 2 * site_b)
-        hop[prec] = {"hop_ms": round(ms, 4), "hop_gflops": round(1320 * Vh * Ls / ms / 1e6, 1),
+        hop[prec] = {"hop_ms": round(ms, 4), "hop_gflops": round(metrics.HOP_FLOP_SITE * Vh * Ls / ms / 1e6, 1),
                      "hop_gbs": round(alg / ms / 1e6, 1), "hop_frac": round(alg / ms / 1e6 / _peak(), 4),
                      "mhat_ms": round(ms_m, 4)}
     res = {}
@@ -144,7 +144,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     out = {"workload": "wilson_24x24x24x48_kappa0.124_12pointsources", "x0": x0,
-           "dslash12_ms": round(ms12, 4), "dslash12_gflops": round(1320 * Vh * 12 / ms12 / 1e6, 1),
+           "dslash12_ms": round(ms12, 4), "dslash12_gflops": round(metrics.HOP_FLOP_SITE * Vh * 12 / ms12 / 1e6, 1),
            "dslash12_gbs": round(alg12 / ms12 / 1e6, 1), "dslash12_frac": round(alg12 / ms12 / 1e6 / _peak(), 4),
            "dslash1_x12_ms": round(12 * ms1, 4),
            "solve12_s": round(t_batch, 4), "solve_12x1_s": round(t_seq, 4),
