@@ -205,9 +205,14 @@ def main():
     ap.add_argument("--profile", default="none", choices=["none", "dslash", "step"],
                     help="for ncu: 'dslash' runs only the standalone FP32 D_eo launches, 'step' one step "
                          "between cudaProfilerStart/Stop (use ncu --profile-from-start off); no JSON line")
+    ap.add_argument("--profile-prec", default="f32", choices=["f32", "f64", "df64"],
+                    help="precision of the D_eo launches of --profile dslash")
     ap.add_argument("--workload", default="wilson32", choices=["wilson32", "dwf", "batched", "force"],
                     help="wilson32 (default, the bench line); the others characterise the other "
                          "configurations (domain-wall CG, 12-rhs propagator, force) and print their own line")
+    ap.add_argument("--outer", default="df64", choices=["f64", "df64"],
+                    help="precision of the outer steps of the mixed solve: df64 = double-float stencil "
+                         "(FP32 pairs), f64 = IEEE FP64 stencil; the final residual is FP64 either way")
     ap.add_argument("--delta", type=float, default=None,
                     help="reliable-update factor of the mixed solves (default: 1e-4 for the FP32 Wilson solves "
                          "of the bench line, the library's per-precision default elsewhere)")
@@ -253,7 +258,8 @@ def main():
     qcd.field_pack(g, f, "f32", 1, b_dev, in32)
     qcd.field_pack(g, f, "f64", 1, b_dev, in64)
     delta = 1e-4 if args.delta is None else args.delta
-    solve_kw = dict(method=qcd.BICGSTAB, tol=TOL, inner="f32", use_graph=True, graph_chunk=32, delta=delta)
+    solve_kw = dict(method=qcd.BICGSTAB, tol=TOL, inner="f32", use_graph=True, graph_chunk=32, delta=delta,
+                    outer=args.outer)
 
     ev_d0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_d1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -277,12 +283,21 @@ def main():
         return info[0]
 
     if args.profile == "dslash":
+        pp = args.profile_prec
+        if pp == "f32":
+            pin, pout = in32, out32
+        elif pp == "f64":
+            pin, pout = in64, out64
+        else:
+            pin = torch.empty(qcd.field_bytes(g, f, pp), dtype=torch.uint8, device=dev)
+            pout = torch.empty_like(pin)
+            qcd.field_pack(g, f, pp, 1, b_dev, pin)
         for _ in range(3):  # tuning and warm-up, then the profiled launches
-            qcd.dslash(g, f, "D_EO", in32, out32, prec="f32", layout=qcd.INTERNAL)
+            qcd.dslash(g, f, "D_EO", pin, pout, prec=pp, layout=qcd.INTERNAL)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        for _ in range(NDSLASH):
-            qcd.dslash(g, f, "D_EO", in32, out32, prec="f32", layout=qcd.INTERNAL)
+        for _ in range(NDSLASH if pp == "f32" else 3):
+            qcd.dslash(g, f, "D_EO", pin, pout, prec=pp, layout=qcd.INTERNAL)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         print("profile dslash done", flush=True)
@@ -320,10 +335,10 @@ def main():
             raise SystemExit(f"solve failed to converge: {inf}")
 
     def hops_in_solve(inf):
-        # 4 inner half-dslashes per BiCGStab iteration; FP64: 1 (source), 2 per outer step
-        # (the true residual; none before the first since x0 = 0), 1 (reconstruction),
-        # 1 (even part of the final full-system residual; the odd part reuses the
-        # reconstruction's H_oe x_e)
+        # 4 inner half-dslashes per BiCGStab iteration; outer precision (FP64 or double-float):
+        # 1 (source), 2 per outer step (the true residual; none before the first since x0 = 0),
+        # 1 (reconstruction); FP64: 1 (even part of the final full-system residual; the odd
+        # part reuses the reconstruction's H_oe x_e)
         return 4 * inf["iters"] + 1 + 2 * inf["outer_updates"] + 1 + 1
 
     hops = sum(NDSLASH + 1 + hops_in_solve(inf) for inf in infos)
@@ -349,6 +364,19 @@ def main():
         fp64 = {"ms": round(e0.elapsed_time(e1), 3), "iters": info64[0]["iters"],
                 "true_resid": info64[0]["true_resid"]}
 
+    # ---- the same mixed solve with the other outer precision, once (for comparison)
+    other = "f64" if args.outer == "df64" else "df64"
+    x_dev.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    qcd.solve(g, f, b_dev, x_dev, **dict(solve_kw, outer=other))  # warm-up (workspace, graphs)
+    x_dev.zero_()
+    e0.record(stream)
+    info_o, _ = qcd.solve(g, f, b_dev, x_dev, **dict(solve_kw, outer=other))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    other_outer = {"outer": other, "ms": round(e0.elapsed_time(e1), 3), "iters": info_o[0]["iters"],
+                   "updates": info_o[0]["outer_updates"], "true_resid": info_o[0]["true_resid"]}
+
     # ---- standalone FP64 D_eo rate (ALU-bound on GB300)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -357,6 +385,19 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     d64_ms = e0.elapsed_time(e1) / 3
+    # ---- standalone double-float D_eo (the outer-step stencil)
+    nbdf = qcd.field_bytes(g, f, "df64")
+    indf = torch.empty(nbdf, dtype=torch.uint8, device=dev)
+    outdf = torch.empty(nbdf, dtype=torch.uint8, device=dev)
+    qcd.field_pack(g, f, "df64", 1, b_dev, indf)
+    qcd.dslash(g, f, "D_EO", indf, outdf, prec="df64", layout=qcd.INTERNAL)
+    e0.record(stream)
+    for _ in range(3):
+        qcd.dslash(g, f, "D_EO", indf, outdf, prec="df64", layout=qcd.INTERNAL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ddf_ms = e0.elapsed_time(e1) / 3
+    del indf, outdf
 
     # ---- end to end through the C ABI with host buffers (pinned), one step
     b_host = torch.from_numpy(psi).pin_memory().numpy()
@@ -382,7 +423,10 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic: smoothed-random SU(3) links and Z2 noise source (seeded)",
         "config": {"workload": WORKLOAD, "lattice": list(L), "kappa": KAPPA, "eps": EPS, "recon": RECON,
-                   "solver": "EO BiCGStab, FP32 inner + FP64 reliable updates, CUDA graph chunks of 32",
+                   "solver": "EO BiCGStab, FP32 inner + reliable updates in "
+                             + ("double-float (FP32 pairs)" if args.outer == "df64" else "FP64")
+                             + ", FP64 final residual, CUDA graph chunks of 32",
+                   "outer": args.outer,
                    "tol": TOL, "ndslash_per_step": NDSLASH, "delta": delta,
                    "l2": "inputs larger than L2 (links 403 MB, each parity vector 101 MB)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
@@ -396,10 +440,14 @@ def main():
                    "fp64_gflops": round(FLOP_SITE * Vh / (d64_ms / 1e3) / 1e9, 1),
                    "fp64_bound": "alu", "fp64_peak_tflops": FP64_PEAK_TFLOPS,
                    "fp64_frac": round(FLOP_SITE * Vh / (d64_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, 4),
-                   "fp64_gbs": round(BYTES_SITE_FP64 * Vh / (d64_ms / 1e3) / 1e9, 1)},
+                   "fp64_gbs": round(BYTES_SITE_FP64 * Vh / (d64_ms / 1e3) / 1e9, 1),
+                   "df64_ms": round(ddf_ms, 4),
+                   "df64_gflops": round(FLOP_SITE * Vh / (ddf_ms / 1e3) / 1e9, 1),
+                   "df64_gbs": round(BYTES_SITE_FP64 * Vh / (ddf_ms / 1e3) / 1e9, 1)},
         "solve": {"mixed_ms": round(mixed_ms, 3), "mixed_iters": infos[-1]["iters"],
                   "mixed_updates": infos[-1]["outer_updates"], "mixed_true_resid": infos[-1]["true_resid"],
-                  "fp64": fp64, "speedup_vs_fp64": round(fp64["ms"] / mixed_ms, 3) if fp64 else None},
+                  "fp64": fp64, "speedup_vs_fp64": round(fp64["ms"] / mixed_ms, 3) if fp64 else None,
+                  "other_outer": other_outer},
         "e2e": {"value": round(e2e_val, 3), "unit": "GFLOP/s", "ms": round(min(e2e_ms), 3),
                 "h2d_bytes_per_step": 2 * spinor_bytes, "d2h_bytes_per_step": 2 * spinor_bytes},
         "gpu_launches": n_launch,

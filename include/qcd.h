@@ -70,7 +70,17 @@ typedef enum {
   QCD_ERR_UNSUPPORTED = 8  /* valid but unsupported combination of arguments        */
 } qcd_status;
 
-typedef enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2 } qcd_prec;
+/* Storage / arithmetic precision of internal fields and operator applications.
+ * QCD_DF64 ("double-float") keeps every real as an unevaluated sum hi + lo of
+ * two FP32 numbers (|lo| <= ulp(hi)/2 on store) and multiplies and sums with
+ * error-free transformations (TwoSum, TwoProd by FMA; the compensated dot
+ * product "Dot2" of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)):
+ * about 48 significant bits from FP32 instructions, for GPUs whose FP64 rate
+ * is a small fraction of FP32.  Converting a double gives hi = fl32(x),
+ * lo = fl32(x - hi), exact to 2^-48 |x| for 2^-100 < |x| < 2^100.
+ * QCD_DF64 is available for the Wilson operator (qcd_dslash, qcd_field_pack /
+ * unpack, and as the outer precision of qcd_solve). */
+typedef enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_DF64 = 3 } qcd_prec;
 
 typedef enum { QCD_WILSON = 0, QCD_DWF = 1 } qcd_fermion_type;
 
@@ -124,7 +134,13 @@ typedef struct {
  * use_graph: capture `graph_chunk` inner iterations in one CUDA graph and
  *   check convergence once per graph launch (0 = plain launches).
  * x0_given: x holds an initial guess on entry (warm start).
- * dagger: solve with the adjoint operator (A^dag x = b); Wilson only. */
+ * dagger: solve with the adjoint operator (A^dag x = b); Wilson only.
+ * outer: precision of the operator applications of the outer steps of a
+ *   mixed solve (source preparation, reliable-update residuals b - Mhat x,
+ *   reconstruction of the odd sites): QCD_F64 (IEEE double, the default when
+ *   zero-initialised) or QCD_DF64 (double-float, Wilson only).  The solution
+ *   is accumulated in FP64 and the final true_resid is computed with IEEE
+ *   FP64 operators either way; ignored when inner = QCD_F64. */
 typedef struct {
   int32_t method;
   double tol;
@@ -135,6 +151,7 @@ typedef struct {
   int32_t graph_chunk;
   int32_t x0_given;
   int32_t dagger;
+  int32_t outer;
 } qcd_solver_params;
 
 /* Per right-hand side result of qcd_solve. */
@@ -151,8 +168,9 @@ typedef struct qcd_gauge qcd_gauge;
 
 /* Load a gauge field (Sec. II A: links U_mu(x) in SU(3)).
  * U: canonical complex128 (4, V, 3, 3), device or host.  The library keeps
- * even-odd reordered copies in FP64 (18 reals) and in FP32 and FP16 (geom->recon
- * reals); the caller's buffer is not referenced after the call returns.
+ * even-odd reordered copies in FP64 (18 reals), in FP32 and FP16 (geom->recon
+ * reals) and in double-float (18 hi/lo FP32 pairs); the caller's buffer is not
+ * referenced after the call returns.
  * Errors: QCD_ERR_ARG for a NULL pointer, odd or non-positive extents, bc not
  * +-1, recon not 12/18, or V >= 2^31; QCD_ERR_OOM if the copies do not fit. */
 qcd_status qcd_gauge_load(const qcd_geom* geom, const void* U, void* stream, qcd_gauge** out);

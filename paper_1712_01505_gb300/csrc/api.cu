@@ -48,6 +48,7 @@ size_t spinor_site_bytes(int prec) {
   switch (prec) {
     case QCD_F64: return 24 * sizeof(double);
     case QCD_F32: return 24 * sizeof(float);
+    case QCD_DF64: return 24 * 2 * sizeof(float);
     default: return 24 * 2;
   }
 }
@@ -146,7 +147,8 @@ int check_fermion(const qcd_fermion* f) {
 }
 
 void check_prec(int prec) {
-  if (prec != QCD_F64 && prec != QCD_F32 && prec != QCD_F16) raise(QCD_ERR_ARG, "unknown precision %d", prec);
+  if (prec != QCD_F64 && prec != QCD_F32 && prec != QCD_F16 && prec != QCD_DF64)
+    raise(QCD_ERR_ARG, "unknown precision %d", prec);
 }
 
 void check_gauge(const qcd_gauge* g) {
@@ -247,9 +249,11 @@ qcd_status qcd_gauge_load(const qcd_geom* geom, const void* U, void* stream, qcd
     g->U64 = g->ws.get("gauge.U64", links * 18 * sizeof(double));
     g->U32 = g->ws.get("gauge.U32", links * lat.recon * sizeof(float));
     g->U16 = g->ws.get("gauge.U16", links * lat.recon * 2);
+    g->Udf = g->ws.get("gauge.Udf", links * 18 * 2 * sizeof(float));
     size_t bytes = links * 18 * sizeof(double);
     Staged su = stage_in(g, "io.gauge", U, bytes, st, true);
     gauge_reorder(g, su.dev, st);
+    links_to_df(g, st);
     QCD_CK(cudaStreamSynchronize(st));
   });
   if (s != QCD_OK) {
@@ -355,6 +359,7 @@ qcd_status qcd_dslash(const qcd_gauge* gc, const qcd_fermion* fermion, qcd_prec 
     cudaStream_t st = (cudaStream_t)stream;
     OpCtx c{g, *fermion, prec};
     const bool dwf = fermion->type == QCD_DWF;
+    if (dwf && prec == QCD_DF64) raise(QCD_ERR_UNSUPPORTED, "double-float is available for the Wilson operator");
     if (layout == QCD_LAYOUT_INTERNAL) {
       if (op == QCD_OP_FULL || op == QCD_OP_FULL_DAG) raise(QCD_ERR_UNSUPPORTED, "FULL ops need the canonical layout");
       if (!is_device_ptr(in) || !is_device_ptr(out)) raise(QCD_ERR_ARG, "internal buffers must be device memory");
@@ -418,7 +423,12 @@ qcd_status qcd_solve(const qcd_gauge* gc, const qcd_fermion* fermion, const qcd_
       raise(QCD_ERR_UNSUPPORTED, "domain-wall needs CG on the normal equations (BiCGStab fails on its spectrum)");
     if (fermion->type == QCD_DWF && p.dagger) raise(QCD_ERR_UNSUPPORTED, "dagger solves are Wilson only");
     if (!(p.tol > 0) || !std::isfinite(p.tol)) raise(QCD_ERR_ARG, "tol must be finite and > 0");
-    check_prec(p.inner);
+    if (p.inner != QCD_F64 && p.inner != QCD_F32 && p.inner != QCD_F16)
+      raise(QCD_ERR_ARG, "inner precision must be QCD_F64, QCD_F32 or QCD_F16 (got %d)", p.inner);
+    if (p.outer != QCD_F64 && p.outer != QCD_DF64)
+      raise(QCD_ERR_ARG, "outer precision must be QCD_F64 or QCD_DF64 (got %d)", p.outer);
+    if (p.outer == QCD_DF64 && fermion->type == QCD_DWF)
+      raise(QCD_ERR_UNSUPPORTED, "a double-float outer precision is available for Wilson fermions");
     if (p.maxiter < 0) raise(QCD_ERR_ARG, "maxiter must be >= 0");
     if (p.delta < 0 || p.delta >= 1) raise(QCD_ERR_ARG, "delta must be in [0, 1)");
     cudaStream_t user = (cudaStream_t)stream;

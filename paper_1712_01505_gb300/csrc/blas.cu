@@ -120,6 +120,10 @@ void blas_copy(const Field& src, Field& dst, cudaStream_t st) {
     if (src.norm) QCD_CK(cudaMemcpyAsync(dst.norm, src.norm, src.norm_bytes(), cudaMemcpyDeviceToDevice, st));
     return;
   }
+  if (src.prec == QCD_DF64 || dst.prec == QCD_DF64) {
+    df_copy(src, dst, st);
+    return;
+  }
   dim3 grid(grid_for(n), src.nrhs);
   if (src.prec == QCD_F64 || dst.prec == QCD_F64)
     k_copy<double><<<grid, kThreads, 0, st>>>(any_view(src), any_view(dst), n);
@@ -132,6 +136,10 @@ void blas_axpby(double a, const Field& x, double b, Field& y, cudaStream_t st) {
   if (x.nsites() != y.nsites() || x.nrhs != y.nrhs) raise(QCD_ERR_ARG, "axpby: shape mismatch");
   long n = x.nsites();
   if (n == 0) return;
+  if (x.prec == QCD_DF64 || y.prec == QCD_DF64) {
+    df_axpby(a, x, b, y, st);
+    return;
+  }
   dim3 grid(grid_for(n), x.nrhs);
   if (x.prec == QCD_F64 || y.prec == QCD_F64)
     k_axpby<double><<<grid, kThreads, 0, st>>>(a, any_view(x), b, any_view(y), n);
@@ -146,14 +154,18 @@ void blas_norm2(const Field& x, double* out_host, cudaStream_t st, qcd_gauge* g)
     for (int r = 0; r < x.nrhs; ++r) out_host[r] = 0;
     return;
   }
-  unsigned nb = grid_for(n);
+  unsigned nb = x.prec == QCD_DF64 ? df_norm2_blocks(n) : grid_for(n);
   double* partial = (double*)g->ws.get("blas.norm2.partial", sizeof(double) * nb * x.nrhs);
   dim3 grid(nb, x.nrhs);
-  if (x.prec == QCD_F64)
-    k_norm2<double><<<grid, kThreads, 0, st>>>(any_view(x), n, partial);
-  else
-    k_norm2<float><<<grid, kThreads, 0, st>>>(any_view(x), n, partial);
-  QCD_LAUNCH_CK();
+  if (x.prec == QCD_DF64) {
+    df_norm2_partials(x, partial, nb, st);
+  } else {
+    if (x.prec == QCD_F64)
+      k_norm2<double><<<grid, kThreads, 0, st>>>(any_view(x), n, partial);
+    else
+      k_norm2<float><<<grid, kThreads, 0, st>>>(any_view(x), n, partial);
+    QCD_LAUNCH_CK();
+  }
   std::vector<double> h((size_t)nb * x.nrhs);
   QCD_CK(cudaMemcpyAsync(h.data(), partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
   QCD_CK(cudaStreamSynchronize(st));

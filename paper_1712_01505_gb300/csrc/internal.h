@@ -91,6 +91,7 @@ struct qcd_gauge {
   void* U64 = nullptr;  // FP64, 18 reals
   void* U32 = nullptr;  // FP32, lat.recon reals
   void* U16 = nullptr;  // FP16, lat.recon reals
+  void* Udf = nullptr;  // double-float, 18 reals as hi/lo FP32 pairs
   qcd::Workspace ws;
   cudaStream_t work = nullptr;  // private stream (capturable) for the solver
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -133,6 +134,18 @@ struct RedSpec {
 void hop(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int dagger, double a,
          const Field* x, cudaStream_t st, const int* stop = nullptr, bool allow_tuning = true,
          const RedSpec* red = nullptr);
+
+// ----------------------------------------------------------------------------- double float (wilson_df.cu)
+// out = [x1 + c2 x2 +] a * H_{p,1-p} in on double-float fields (x2 only with x1)
+void hop_df(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int dagger, double a,
+            const Field* x1, const Field* x2, double c2, cudaStream_t st, const int* stop = nullptr,
+            bool allow_tuning = true);
+void links_to_df(qcd_gauge* g, cudaStream_t st);  // Udf from U64
+// conversions and y = a x + b y with a double-float operand (called by blas.cu)
+void df_copy(const Field& src, Field& dst, cudaStream_t st);
+void df_axpby(double a, const Field& x, double b, Field& y, cudaStream_t st);
+unsigned df_norm2_blocks(long n);
+void df_norm2_partials(const Field& x, double* partial, unsigned nb, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- domain wall (dwf.cu)
 struct DwParams {

@@ -3,6 +3,7 @@
 // pack / unpack).  These run once per solve (gauge load, source preparation,
 // solution write-back).
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace qcd {
@@ -178,6 +179,9 @@ void pack_field(const Lattice& lat, int parity, const double* canon, Field& f, c
     case QCD_F32:
       k_pack<P32><<<blocks_for(n, 256), 256, 0, st>>>(dg, parity, c, view_of<P32>(f), f.ls, f.nrhs);
       break;
+    case QCD_DF64:
+      k_pack<PDF><<<blocks_for(n, 256), 256, 0, st>>>(dg, parity, c, view_of<PDF>(f), f.ls, f.nrhs);
+      break;
     default:
       k_pack<P16><<<blocks_for(n, 256), 256, 0, st>>>(dg, parity, c, view_of<P16>(f), f.ls, f.nrhs);
   }
@@ -195,6 +199,9 @@ void unpack_field(const Lattice& lat, int parity, const Field& f, double* canon,
       break;
     case QCD_F32:
       k_unpack<P32><<<blocks_for(n, 256), 256, 0, st>>>(dg, parity, view_of<P32>(f), c, f.ls, f.nrhs);
+      break;
+    case QCD_DF64:
+      k_unpack<PDF><<<blocks_for(n, 256), 256, 0, st>>>(dg, parity, view_of<PDF>(f), c, f.ls, f.nrhs);
       break;
     default:
       k_unpack<P16><<<blocks_for(n, 256), 256, 0, st>>>(dg, parity, view_of<P16>(f), c, f.ls, f.nrhs);

@@ -11,7 +11,9 @@
 // recursion from it while keeping the search direction (reliable update,
 // Sleijpen & van der Vorst 1996).  FP64 therefore appears on the device only in
 // the true-residual recomputation, the solution accumulation and the global
-// sums of the dot products.
+// sums of the dot products.  With outer = QCD_DF64 (Wilson) the outer steps
+// run in double-float instead (FP32 pairs, about 48 bits; see wilson_df.cu),
+// and only the final true residual uses the IEEE-FP64 stencil.
 //
 // The scalars (alpha, beta, omega, rho, |r|^2) never leave the device during
 // the inner iteration: small kernels turn per-block partial sums into them.
@@ -695,6 +697,23 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     if (g->ws.generation != gen) QCD_CK(cudaMemsetAsync(S.counters, 0, sizeof(int) * ngroups, st));
   }
   S.hsc.assign(nrhs, Scal{});
+  // Double-float outer steps (Wilson, mixed): the prepared source, the solution
+  // and the outer residual live in FP32 pairs and the outer operator
+  // applications use the double-float stencil; the true residual reported at
+  // the end is recomputed with the IEEE-FP64 operator all the same.
+  const bool dfo = prm.outer == QCD_DF64 && !dwf && S.inner != QCD_F64;
+  const OpCtx opdf{g, f, QCD_DF64};
+  Field be_d, bo_d, bh_d, x_d, t_d, u_d, r_d;
+  if (dfo) {
+    be_d = ws_field(g, "s.be_d", QCD_DF64, ls, nrhs);
+    bo_d = ws_field(g, "s.bo_d", QCD_DF64, ls, nrhs);
+    bh_d = ws_field(g, "s.bh_d", QCD_DF64, ls, nrhs);
+    x_d = ws_field(g, "s.x_d", QCD_DF64, ls, nrhs);
+    t_d = ws_field(g, "s.t_d", QCD_DF64, ls, nrhs);
+    u_d = ws_field(g, "s.u_d", QCD_DF64, ls, nrhs);
+    if (!S.bicg()) r_d = ws_field(g, "s.r_d", QCD_DF64, ls, nrhs);
+  }
+  const Field& r_outer = dfo ? (S.bicg() ? t_d : r_d) : S.r64;
 
   // ---- even-odd source: b_hat on the even sites
   pack_field(lat, 0, b, S.b_e, st);
@@ -704,7 +723,11 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   blas_norm2(S.b_o, bn_o.data(), st, g);
   for (int r = 0; r < nrhs; ++r) bnorm[r] = std::sqrt(bn_e[r] + bn_o[r]);
   DwParams dp{f.Ls, f.M5, f.mf};
-  if (!dwf) {
+  if (dfo) {
+    blas_copy(S.b_e, be_d, st);
+    blas_copy(S.b_o, bo_d, st);
+    hop_df(g, bo_d, bh_d, 0, dag, f.kappa, &be_d, nullptr, 0.0, st);
+  } else if (!dwf) {
     // bhat = b_e + kappa H_eo b_o
     hop(g, S.b_o, S.bh, 0, dag, f.kappa, &S.b_e, st);
   } else {
@@ -717,11 +740,26 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     pack_field(lat, 0, x, S.x64, st);
   else
     blas_zero(S.x64, st);
+  if (dfo) blas_copy(S.x64, x_d, st);
 
   // |b - A x| on the full system from the even-odd residual rhat = bhat - Mhat x_e:
   // Wilson: (rhat, 0);  DWF: (A rhat, 0)  (exact reconstruction of x_o)
   std::vector<double> rn(nrhs), rfull(nrhs);
   auto true_residual = [&](bool x_is_zero) {
+    if (dfo) {
+      if (x_is_zero) {
+        blas_copy(bh_d, t_d, st);
+      } else {
+        // rhat = bhat - x + kappa^2 H_eo H_oe x  (H -> H^dag for the adjoint system)
+        hop_df(g, x_d, u_d, 1, dag, 1.0, nullptr, nullptr, 0.0, st);
+        hop_df(g, u_d, t_d, 0, dag, f.kappa * f.kappa, &bh_d, &x_d, -1.0, st);
+      }
+      blas_norm2(t_d, rfull.data(), st, g);
+      for (int r = 0; r < nrhs; ++r) rfull[r] = std::sqrt(rfull[r]);
+      if (!S.bicg()) apply_mhat(opdf, t_d, r_d, 1, st, "odf");
+      blas_norm2(r_outer, rn.data(), st, g);
+      return;
+    }
     if (x_is_zero) {
       blas_copy(S.bh, S.t64, st);  // rhat = bhat
     } else {
@@ -761,8 +799,8 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   }
 
   auto restart_from_residual = [&](bool full) {
-    // r (inner) = r64; the recursion continues from the true residual
-    blas_copy(S.r64, S.r, st);
+    // r (inner) = outer residual; the recursion continues from the true residual
+    blas_copy(r_outer, S.r, st);
     if (S.inner != QCD_F64) blas_zero(S.xin, st);
     std::vector<double> re, im;
     if (S.bicg()) {
@@ -860,7 +898,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
         need_full_restart = true;
       }
     }
-    if (S.inner != QCD_F64) blas_axpby(1.0, S.xin, 1.0, S.x64, st);
+    if (S.inner != QCD_F64) blas_axpby(1.0, S.xin, 1.0, dfo ? x_d : S.x64, st);
     true_residual(false);
     nactive = 0;
     for (int r = 0; r < nrhs; ++r) {
@@ -880,9 +918,18 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   Field xe = S.x64, xo = S.t64;
   if (!dwf) {
     // h = H_oe x_e (kept), x_o = b_o + kappa h
-    hop(g, S.x64, S.u64, 1, dag, 1.0, nullptr, st);
-    blas_copy(S.b_o, S.t64, st);
-    blas_axpby(f.kappa, S.u64, 1.0, S.t64, st);
+    if (dfo) {
+      hop_df(g, x_d, u_d, 1, dag, 1.0, nullptr, nullptr, 0.0, st);
+      blas_copy(bo_d, t_d, st);
+      blas_axpby(f.kappa, u_d, 1.0, t_d, st);
+      blas_copy(x_d, S.x64, st);
+      blas_copy(t_d, S.t64, st);
+      blas_copy(u_d, S.u64, st);
+    } else {
+      hop(g, S.x64, S.u64, 1, dag, 1.0, nullptr, st);
+      blas_copy(S.b_o, S.t64, st);
+      blas_axpby(f.kappa, S.u64, 1.0, S.t64, st);
+    }
     unpack_field(lat, 0, S.x64, x, st);
     unpack_field(lat, 1, S.t64, x, st);
     // true residual on the full system: even part with a fresh FP64 stencil on

@@ -564,6 +564,10 @@ void hop(const qcd_gauge* g, const Field& in, Field& out, int out_parity, int da
     raise(QCD_ERR_ARG, "hop: output aliases an input");
   if (in.Vh == 0 || in.nrhs * in.ls == 0) return;
   switch (in.prec) {
+    case QCD_DF64:
+      if (red) raise(QCD_ERR_UNSUPPORTED, "fused reductions are not available in double-float");
+      hop_df(g, in, out, out_parity, dagger, a, x, nullptr, 0.0, st, stop, allow_tuning);
+      break;
     case QCD_F64:
       hop_impl<P64, 18>(g, g->U64, in, out, out_parity, dagger, a, x, st, stop, allow_tuning, red);
       break;

@@ -27,8 +27,8 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOCONV, ERR_BREAKDOWN, ERR_NAN, ERR_TIMEOUT,
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_OOM", "ERR_NOCONV", "ERR_BREAKDOWN", "ERR_NAN",
                 "ERR_TIMEOUT", "ERR_UNSUPPORTED"]
 # qcd_prec
-F64, F32, F16 = 0, 1, 2
-PREC = {"f64": F64, "f32": F32, "f16": F16, F64: F64, F32: F32, F16: F16}
+F64, F32, F16, DF64 = 0, 1, 2, 3
+PREC = {"f64": F64, "f32": F32, "f16": F16, "df64": DF64, F64: F64, F32: F32, F16: F16, DF64: DF64}
 # qcd_fermion_type
 WILSON, DWF = 0, 1
 # qcd_op
@@ -64,7 +64,8 @@ class Fermion(ctypes.Structure):
 class SolverParams(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("tol", ctypes.c_double), ("maxiter", ctypes.c_int32),
                 ("inner", ctypes.c_int32), ("delta", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("graph_chunk", ctypes.c_int32), ("x0_given", ctypes.c_int32), ("dagger", ctypes.c_int32)]
+                ("graph_chunk", ctypes.c_int32), ("x0_given", ctypes.c_int32), ("dagger", ctypes.c_int32),
+                ("outer", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -233,9 +234,9 @@ def mhat_noalloc(gauge, fermion, inp, out, prec="f32", dagger=False, nrhs=1, str
 
 
 def solver_params(method=BICGSTAB, tol=1e-10, maxiter=100000, inner="f64", delta=0.0, use_graph=False,
-                  graph_chunk=32, x0_given=False, dagger=False) -> SolverParams:
+                  graph_chunk=32, x0_given=False, dagger=False, outer="f64") -> SolverParams:
     return SolverParams(method, tol, maxiter, PREC[inner], delta, int(use_graph), graph_chunk, int(x0_given),
-                        int(dagger))
+                        int(dagger), PREC[outer])
 
 
 def solve(gauge, fermion, b, x, nrhs=1, stream=None, check=True, **kw):

@@ -40,7 +40,39 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(qcd.Geom) == 36
     assert qcd.Fermion.kappa.offset == 8 and qcd.Fermion.Ls.offset == 16 and qcd.Fermion.mf.offset == 32
     assert qcd.SolverParams.tol.offset == 8 and qcd.SolverParams.delta.offset == 24
+    assert qcd.SolverParams.outer.offset == 48 and ctypes.sizeof(qcd.SolverParams) == 56
     assert ctypes.sizeof(qcd.SolveInfo) == 32
+
+
+def test_struct_layouts_match_a_c_compiler(tmp_path):
+    """Every field offset and struct size of the binding equals what gcc makes of include/qcd.h."""
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    structs = {"qcd_geom": qcd.Geom, "qcd_fermion": qcd.Fermion, "qcd_solver_params": qcd.SolverParams,
+               "qcd_solve_info": qcd.SolveInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qcd.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append(f'  printf("enum QCD_DF64 %d\\n", (int)QCD_DF64);')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, c = line.split()
+        got[(a, b)] = int(c)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+    assert got[("enum", "QCD_DF64")] == qcd.DF64
 
 
 def test_field_bytes_host_validation(lib):
@@ -50,6 +82,7 @@ def test_field_bytes_host_validation(lib):
     assert lib.qcd_field_bytes(ctypes.byref(g), ctypes.byref(f), qcd.F32, 1) == Vh * 96
     assert lib.qcd_field_bytes(ctypes.byref(g), ctypes.byref(f), qcd.F64, 2) == 2 * Vh * 192
     assert lib.qcd_field_bytes(ctypes.byref(g), ctypes.byref(f), qcd.F16, 1) == Vh * (48 + 4)
+    assert lib.qcd_field_bytes(ctypes.byref(g), ctypes.byref(f), qcd.DF64, 1) == Vh * 192
     d = qcd.dwf(8, 1.8, 0.02)
     assert lib.qcd_field_bytes(ctypes.byref(g), ctypes.byref(d), qcd.F32, 1) == 8 * Vh * 96
     bad = qcd.Geom((ctypes.c_int32 * 4)(4, 3, 4, 8), (ctypes.c_int32 * 4)(1, 1, 1, -1), 18)
