@@ -43,7 +43,7 @@ void load_cache_locked() {
     if (!t1) continue;
     *t1 = 0;
     int b = 0, t = 0;
-    if (sscanf(t1 + 1, "%d\t%d", &b, &t) == 2 && b > 0 && t > 0) g_cache[line] = {b, t};
+    if (sscanf(t1 + 1, "%d\t%d", &b, &t) == 2 && b > 0 && t != 0) g_cache[line] = {b, t};
   }
   fclose(f);
 }

@@ -165,7 +165,57 @@ __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCo
   }
 }
 
-template <int P, int RECON, int TILE>
+// ----------------------------------------------------------------------------- prefetch
+// Register-free prefetches of the neighbour spinors and links of a direction,
+// so that more of the stencil's DRAM traffic is in flight than the registers
+// of the resident threads can hold.  PF = 0: none; PF = 1: into L1, one
+// direction ahead of its loads; PF = 2: into L1, two directions ahead.
+__device__ __forceinline__ void prefetch_line(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+template <int P>
+__host__ __device__ constexpr int spinor_comps() {
+  return P == P64 ? 12 : (P == P32 ? 6 : 3);
+}
+template <int P, int RECON>
+__host__ __device__ constexpr int link_comps() {
+  return (P == P64 || RECON == 18) ? 9 : 3;
+}
+
+template <int P, int RECON, int MU>
+__device__ __forceinline__ void prefetch_dir(const HopArgs<P, RECON>& A, const SiteCoords& c, int cb, int q0) {
+  const int r = q0 / A.ls, s = q0 - r * A.ls;
+  const SpinorView<P> in = A.in.offset_rhs(r);
+  int wrap;
+  const long jf = neighbour_index(A.g, c, MU, +1, &wrap) >> 1;
+  const long jb = neighbour_index(A.g, c, MU, -1, &wrap) >> 1;
+  const long so = (long)s * A.g.Vh;
+#pragma unroll
+  for (int k = 0; k < spinor_comps<P>(); ++k) {
+    prefetch_line(in.p + k * in.stride + so + jf);
+    prefetch_line(in.p + k * in.stride + so + jb);
+  }
+  if (P == P16) {
+    prefetch_line(in.norm + so + jf);
+    prefetch_line(in.norm + so + jb);
+  }
+  constexpr int NL = link_comps<P, RECON>();
+  const auto* qf = A.U.p + (long)(A.out_parity * 4 + MU) * NL * A.U.Vh + cb;
+  const auto* qb = A.U.p + (long)((1 - A.out_parity) * 4 + MU) * NL * A.U.Vh + jb;
+#pragma unroll
+  for (int k = 0; k < NL; ++k) {
+    prefetch_line(qf + k * A.U.Vh);
+    prefetch_line(qb + k * A.U.Vh);
+  }
+}
+
+template <int PF, int P, int RECON, int MU>
+__device__ __forceinline__ void prefetch_before(const HopArgs<P, RECON>& A, const SiteCoords& c, int cb, int q0) {
+  if constexpr (PF == 1 && MU < 3) prefetch_dir<P, RECON, MU + 1>(A, c, cb, q0);
+  if constexpr (PF == 2 && MU == 0) prefetch_dir<P, RECON, 1>(A, c, cb, q0);
+  if constexpr (PF == 2 && MU < 2) prefetch_dir<P, RECON, MU + 2>(A, c, cb, q0);
+}
+
+template <int P, int RECON, int TILE, int PF>
 __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
   using R = typename MathType<P>::type;
   if (A.stop && *A.stop) return;
@@ -183,8 +233,11 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[t][k] = {R(0), R(0)};
   const R sg = A.dagger ? R(1) : R(-1);
+  prefetch_before<PF, P, RECON, 0>(A, c, cb, q0);
   hop_dir<P, RECON, TILE, 0>(A, c, cb, q0, sg, acc);
+  prefetch_before<PF, P, RECON, 1>(A, c, cb, q0);
   hop_dir<P, RECON, TILE, 1>(A, c, cb, q0, sg, acc);
+  prefetch_before<PF, P, RECON, 2>(A, c, cb, q0);
   hop_dir<P, RECON, TILE, 2>(A, c, cb, q0, sg, acc);
   hop_dir<P, RECON, TILE, 3>(A, c, cb, q0, sg, acc);
   const R a = (R)A.a;
@@ -217,7 +270,7 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
 // does not depend on block scheduling).
 constexpr int kRedGroup = 64;
 
-template <int P, int RECON, int RED>
+template <int P, int RECON, int RED, int PF>
 __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
   using R = typename MathType<P>::type;
   if (A.stop && *A.stop) return;
@@ -229,8 +282,11 @@ __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
     const R sg = A.dagger ? R(1) : R(-1);
+    prefetch_before<PF, P, RECON, 0>(A, c, cb, 0);
     hop_dir<P, RECON, 1, 0>(A, c, cb, 0, sg, acc);
+    prefetch_before<PF, P, RECON, 1>(A, c, cb, 0);
     hop_dir<P, RECON, 1, 1>(A, c, cb, 0, sg, acc);
+    prefetch_before<PF, P, RECON, 2>(A, c, cb, 0);
     hop_dir<P, RECON, 1, 2>(A, c, cb, 0, sg, acc);
     hop_dir<P, RECON, 1, 3>(A, c, cb, 0, sg, acc);
     const R a = (R)A.a;
@@ -448,22 +504,22 @@ struct HopLaunch {
   cudaStream_t st;
 };
 
-template <int P, int RECON, int TILE>
+template <int P, int RECON, int TILE, int PF = 0>
 void launch_tile(HopLaunch<P, RECON>* L, int block) {
   HopArgs<P, RECON> A = L->args;
   A.ntiles = (A.nslices + TILE - 1) / TILE;
   long sblocks = (A.g.Vh + block - 1) / block;
   if constexpr (TILE == 1 && P != P16) {
     if (A.red == 1) {
-      k_hop_red<P, RECON, 1><<<(unsigned)sblocks, block, 0, L->st>>>(A);
+      k_hop_red<P, RECON, 1, PF><<<(unsigned)sblocks, block, 0, L->st>>>(A);
       return;
     }
     if (A.red == 2) {
-      k_hop_red<P, RECON, 2><<<(unsigned)sblocks, block, 0, L->st>>>(A);
+      k_hop_red<P, RECON, 2, PF><<<(unsigned)sblocks, block, 0, L->st>>>(A);
       return;
     }
   }
-  k_hop<P, RECON, TILE><<<(unsigned)(sblocks * A.ntiles), block, 0, L->st>>>(A);
+  k_hop<P, RECON, TILE, PF><<<(unsigned)(sblocks * A.ntiles), block, 0, L->st>>>(A);
 }
 
 template <int P, int RECON, int BY, int TS>
@@ -474,7 +530,8 @@ void launch_sm(HopLaunch<P, RECON>* L) {
   k_hop_sm<P, RECON, BY, TS><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
 }
 
-// cfg.tile > 0: register tile of that many slices per thread (k_hop);
+// cfg.tile > 0: register tile of that many slices per thread (k_hop), 101 /
+// 201: one slice per thread with prefetch mode 1 / 2;
 // cfg.tile < 0: shared-memory links (k_hop_sm), -tile = 10 * BY + TS for
 // BY thread rows of TS slices each
 template <int P, int RECON>
@@ -485,6 +542,8 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
   } else {
     switch (cfg.tile) {
       case 1: launch_tile<P, RECON, 1>(L, cfg.block); break;
+      case 101: launch_tile<P, RECON, 1, 1>(L, cfg.block); break;
+      case 201: launch_tile<P, RECON, 1, 2>(L, cfg.block); break;
       case 2: launch_tile<P, RECON, 2>(L, cfg.block); break;
       case 4: launch_tile<P, RECON, 4>(L, cfg.block); break;
       case -41: launch_sm<P, RECON, 4, 1>(L); break;
@@ -546,6 +605,9 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
     cands.clear();
     for (int b : blocks) cands.push_back({b, 1});
   }
+  if (P != P64)  // one slice per thread with prefetches (memory-bound precisions)
+    for (int pf : {101, 201})
+      for (int b : blocks) cands.push_back({b, pf});
   char key[160];
   snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d red%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay, A.red);

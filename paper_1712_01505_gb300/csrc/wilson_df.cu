@@ -117,7 +117,7 @@ __device__ __forceinline__ void prefetch_dir(const HopDfArgs& A, const SpinorVie
 
 // one thread per (output site, slice); blockIdx.y = slice of all right-hand sides
 template <int DAG>
-__global__ void __launch_bounds__(256) k_hop_df(HopDfArgs A) {
+__global__ void __launch_bounds__(128, 3) k_hop_df(HopDfArgs A) {
   if (A.stop && *A.stop) return;
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   if (cb >= A.g.Vh) return;
@@ -432,7 +432,7 @@ void hop_df(const qcd_gauge* gh, const Field& in, Field& out, int out_parity, in
   L.nslices = in.ls * in.nrhs;
   L.st = st;
   if (L.nslices > 65535) raise(QCD_ERR_ARG, "hop_df: too many slices");
-  std::vector<LaunchCfg> cands = {{128, 1}, {64, 1}, {256, 1}};
+  std::vector<LaunchCfg> cands = {{128, 1}, {64, 1}};
   char key[128];
   snprintf(key, sizeof key, "hopdf L%dx%dx%dx%d ns%d x%d%d", gh->lat.L[0], gh->lat.L[1], gh->lat.L[2],
            gh->lat.L[3], L.nslices, A.x1, A.x2);

@@ -1,0 +1,102 @@
+"""Every launch shape the stencil autotuner can choose computes the same operator.
+
+Each candidate (register tiles of 1 / 2 / 4 slices, the L1-prefetching single-slice
+kernels, the shared-memory link kernels, and the fused-reduction stencils of the
+BiCGStab iteration with and without prefetches) is forced through a tuning-cache
+file (QCD_TUNECACHE) in a child process, on a lattice of its own so that every
+cache key names one candidate, and its result is compared with the oracle."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+from tests.gpu_util import device
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import json, sys
+import numpy as np, torch
+from oracle import oracle as ora
+from paper_1712_01505_gb300 import inputs, qcd
+BC = (1, 1, 1, -1)
+res = []
+for case in json.loads(sys.argv[1]):
+    L = tuple(case["L"])
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.4 if case["kind"] == "hop" else 0.3, 3)
+    g = qcd.Gauge.load(torch.from_numpy(U).cuda(), L, BC, recon=case["recon"])
+    if case["kind"] == "hop":
+        nrhs = case["nrhs"]
+        f = qcd.wilson(0.12)
+        psi = inputs.gaussian_source((nrhs, V, 4, 3), 11)
+        o = torch.empty((nrhs, V, 4, 3), dtype=torch.complex128, device="cuda")
+        qcd.dslash(g, f, "D_EO", torch.from_numpy(psi).cuda(), o, prec=case["prec"], nrhs=nrhs)
+        torch.cuda.synchronize()
+        par = ora.parity(L)
+        err = 0.0
+        for r in range(nrhs):
+            inp = psi[r].copy()
+            inp[par == 0] = 0
+            ref = ora.hop(L, BC, U, inp, out_parity=0)
+            a = o[r].cpu().numpy()
+            err = max(err, float(np.linalg.norm(a - ref) / np.linalg.norm(ref)))
+        res.append(err)
+    else:
+        kappa = 0.124
+        f = qcd.wilson(kappa)
+        b = inputs.z2_source((V, 4, 3), 0)
+        x = torch.zeros((V, 4, 3), dtype=torch.complex128, device="cuda")
+        qcd.solve(g, f, torch.from_numpy(b).cuda(), x, tol=1e-10, inner="f32", use_graph=True, graph_chunk=8)
+        xr = x.cpu().numpy()
+        res.append(float(np.linalg.norm(b - ora.wilson(L, BC, kappa, U, xr)) / np.linalg.norm(b)))
+    g.free()
+print(json.dumps(res))
+"""
+
+
+def _key(L, prec, recon, ns, xp, red):
+    p = {"f32": 1, "f16": 2}[prec]
+    return f"hop p{p} r{recon} L{L[0]}x{L[1]}x{L[2]}x{L[3]} ns{ns} xp{xp} red{red}"
+
+
+def test_every_stencil_candidate_matches_the_oracle(tmp_path):
+    device()
+    # (tile code, block) of every candidate family; the shared-memory kernels fix their block
+    shapes = [(1, 128), (2, 64), (4, 256), (101, 64), (201, 128), (-41, 128), (-42, 128), (-81, 256), (-82, 256)]
+    cases, lines, tol = [], [], []
+    t = 4
+    for prec, recon in (("f32", 12), ("f32", 18), ("f16", 12)):
+        for tile, block in shapes:
+            L = (4, 4, 4, t)
+            t += 2
+            cases.append({"kind": "hop", "L": L, "prec": prec, "recon": recon, "nrhs": 16})
+            lines.append(f"{_key(L, prec, recon, 16, 0, 0)}\t{block}\t{tile}")
+            tol.append(1e-6 if prec == "f32" else 2e-3)
+    # the fused-reduction stencils of the FP32 BiCGStab iteration, plain and with prefetches
+    for tile, block in ((1, 64), (101, 128), (201, 64)):
+        L = (8, 8, 8, t)
+        t += 2
+        cases.append({"kind": "solve", "L": L, "recon": 12})
+        for xp, red in ((0, 0), (1, 1), (1, 2)):
+            lines.append(f"{_key(L, 'f32', 12, 1, xp, red)}\t{block}\t{tile}")
+        tol.append(1e-10)
+    cache = tmp_path / "tune.txt"
+    cache.write_text("\n".join(lines) + "\n")
+    env = dict(os.environ, QCD_TUNECACHE=str(cache), PYTHONPATH=ROOT + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    env.pop("QCD_TUNE_VERBOSE", None)
+    out = subprocess.run([sys.executable, "-c", CHILD, json.dumps(cases)], cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=900)
+    assert out.returncode == 0, out.stderr[-2000:]
+    errs = json.loads(out.stdout.strip().splitlines()[-1])
+    assert len(errs) == len(cases)
+    for case, e, tl in zip(cases, errs, tol):
+        assert e <= tl, (case, e)
+    # the forced entries were accepted as they stand: none of their keys was tuned again
+    final = cache.read_text().splitlines()
+    for line in lines:
+        assert sum(1 for f in final if f.split("\t")[0] == line.split("\t")[0]) == 1, line
