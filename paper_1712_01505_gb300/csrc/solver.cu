@@ -16,7 +16,8 @@
 // and only the final true residual uses the IEEE-FP64 stencil.
 //
 // The scalars (alpha, beta, omega, rho, |r|^2) never leave the device during
-// the inner iteration: small kernels turn per-block partial sums into them.
+// the inner iteration: per-block partial sums become scalars either in small
+// one-block kernels or in the prologue of the next vector kernel (alpha, omega).
 // Every kernel of the iteration first reads a stop word; when an iteration
 // raises it (convergence check due, reliable update due, breakdown, NaN) the
 // remaining launches of the chunk do nothing, so a chunk of K iterations can
@@ -150,42 +151,86 @@ __global__ void k_cdot(AnyView a_, AnyView b_, long n, double* partial, const Sc
   write_partial<2>(v, partial, r);
 }
 
-// alpha = rho / (rt, v)                                        <<<nrhs, 256>>>
-// nblk_dev (may be null): number of partials written by a stencil with a fused reduction
-__global__ void k_bicg_alpha(Scal* sc, const double* partial, int nblk, int* ctl, const int* nblk_dev) {
-  if (STOPPED(ctl)) return;
-  int r = blockIdx.x;
-  Scal& s = sc[r];
-  if (!s.active) return;
+// The scalars alpha and omega are formed by every block of the vector kernel
+// that first needs them, from the partial sums the previous kernel left (the
+// same sums in the same order in every block, so every block gets the same
+// value); block 0 stores the value for later kernels and raises the flags.
+// This saves a one-block kernel and its launch gap per scalar.
+// nb_dev (may be null): number of partials written by a stencil with a fused reduction.
+
+// alpha = rho / (rt, v); false (for every block) on NaN or breakdown
+__device__ __forceinline__ bool block_alpha(Scal& s, const double* partial, int nb, int r, int* ctl,
+                                            double2* al) {
+  __shared__ double2 sh;
+  __shared__ int ok;
   double d[2];
-  sum_partials<2>(partial, nblk_dev ? *nblk_dev : nblk, r, d);
-  if (threadIdx.x) return;
-  double2 rv = make_double2(d[0], d[1]);
-  double2 rho = make_double2(s.rho[0], s.rho[1]);
-  if (bad(rv.x) || bad(rv.y)) {
-    s.flag = FLAG_NAN;
-    *ctl = 1;
-    return;
+  sum_partials<2>(partial, nb, r, d);
+  if (threadIdx.x == 0) {
+    const double2 rv = make_double2(d[0], d[1]);
+    const double2 rho = make_double2(s.rho[0], s.rho[1]);
+    const double mag = sqrt(rv.x * rv.x + rv.y * rv.y);
+    int flag = FLAG_NONE;
+    if (bad(rv.x) || bad(rv.y))
+      flag = FLAG_NAN;
+    else if (mag <= 1e-300 || mag < 1e-24 * sqrt(rho.x * rho.x + rho.y * rho.y))
+      flag = FLAG_BREAKDOWN;
+    ok = flag == FLAG_NONE;
+    if (ok) sh = cdiv(rho, rv);
+    if (blockIdx.x == 0) {
+      if (ok) {
+        s.alpha[0] = sh.x;
+        s.alpha[1] = sh.y;
+      } else {
+        s.flag = flag;
+        *ctl = 1;
+      }
+    }
   }
-  double mag = sqrt(rv.x * rv.x + rv.y * rv.y);
-  if (mag <= 1e-300 || mag < 1e-24 * sqrt(rho.x * rho.x + rho.y * rho.y)) {
-    s.flag = FLAG_BREAKDOWN;
-    *ctl = 1;
-    return;
-  }
-  double2 al = cdiv(rho, rv);
-  s.alpha[0] = al.x;
-  s.alpha[1] = al.y;
+  __syncthreads();
+  *al = sh;
+  return ok;
 }
 
-// s = r - alpha v
+// omega = (t, s) / (t, t); false (for every block) on NaN or t = 0
+__device__ __forceinline__ bool block_omega(Scal& s, const double* partial, int nb, int r, int* ctl,
+                                            double2* om) {
+  __shared__ double2 sh;
+  __shared__ int ok;
+  double d[3];
+  sum_partials<3>(partial, nb, r, d);
+  if (threadIdx.x == 0) {
+    int flag = FLAG_NONE;
+    if (bad(d[0]) || bad(d[1]) || bad(d[2]))
+      flag = FLAG_NAN;
+    else if (d[2] <= 0.0)  // t = 0: s is (numerically) zero or the operator annihilated it
+      flag = FLAG_BREAKDOWN;
+    ok = flag == FLAG_NONE;
+    sh = ok ? make_double2(d[0] / d[2], d[1] / d[2]) : make_double2(0.0, 0.0);
+    if (blockIdx.x == 0) {
+      s.omega[0] = sh.x;
+      s.omega[1] = sh.y;
+      if (!ok) {
+        s.flag = flag;
+        *ctl = 1;
+      }
+    }
+  }
+  __syncthreads();
+  *om = sh;
+  return ok;
+}
+
+// alpha from the (rt, v) partials, then s = r - alpha v
 template <typename R>
-__global__ void k_bicg_s(AnyView r_, AnyView v_, AnyView s_, long n, const Scal* sc, const int* ctl) {
+__global__ void k_bicg_s(AnyView r_, AnyView v_, AnyView s_, long n, Scal* sc, int* ctl, const double* partial,
+                         int nblk, const int* nb_dev) {
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
-  const Scal& s = sc[r];
+  Scal& s = sc[r];
   if (!s.active) return;
-  const Cx<R> al = {(R)s.alpha[0], (R)s.alpha[1]};
+  double2 a;
+  if (!block_alpha(s, partial, nb_dev ? *nb_dev : nblk, r, ctl, &a)) return;
+  const Cx<R> al = {(R)a.x, (R)a.y};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vr[12], vv[12];
     any_load<R>(r_, r, i, vr);
@@ -221,58 +266,39 @@ __global__ void k_ts_tt(AnyView t_, AnyView s_, long n, double* partial, const S
   write_partial<3>(v, partial, r);
 }
 
-// omega = (t, s) / (t, t)
-__global__ void k_bicg_omega(Scal* sc, const double* partial, int nblk, int* ctl, const int* nblk_dev) {
-  if (STOPPED(ctl)) return;
-  int r = blockIdx.x;
-  Scal& s = sc[r];
-  if (!s.active) return;
-  double d[3];
-  sum_partials<3>(partial, nblk_dev ? *nblk_dev : nblk, r, d);
-  if (threadIdx.x) return;
-  if (bad(d[0]) || bad(d[1]) || bad(d[2])) {
-    s.flag = FLAG_NAN;
-    *ctl = 1;
-    return;
-  }
-  if (d[2] <= 0.0) {  // t = 0: s is (numerically) zero or the operator annihilated it
-    s.omega[0] = s.omega[1] = 0.0;
-    s.flag = FLAG_BREAKDOWN;
-    *ctl = 1;
-    return;
-  }
-  s.omega[0] = d[0] / d[2];
-  s.omega[1] = d[1] / d[2];
-}
-
-// x += alpha p + omega s;  r = s - omega t;  partials (rt, r) and |r|^2
+// omega from the (t, s), |t|^2 partials, then x += alpha p + omega s;  r = s - omega t;
+// partials (rt, r) and |r|^2 into partial_out (not the array omega is read from)
 template <typename R, typename RX>
 __global__ void k_bicg_xr(AnyView x_, AnyView p_, AnyView s_, AnyView t_, AnyView r_, AnyView rt_,
-                          long n, double* partial, const Scal* sc, const int* ctl) {
+                          long n, const double* partial_in, int nblk, const int* nb_dev, double* partial_out,
+                          Scal* sc, int* ctl) {
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
-  const Scal& s = sc[r];
+  Scal& s = sc[r];
   if (!s.active) return;
-  const Cx<R> al = {(R)s.alpha[0], (R)s.alpha[1]}, om = {(R)s.omega[0], (R)s.omega[1]};
-  const Cx<RX> alx = {(RX)s.alpha[0], (RX)s.alpha[1]}, omx = {(RX)s.omega[0], (RX)s.omega[1]};
+  double2 o;
+  if (!block_omega(s, partial_in, nb_dev ? *nb_dev : nblk, r, ctl, &o)) return;
+  const Cx<R> al = {(R)s.alpha[0], (R)s.alpha[1]}, om = {(R)o.x, (R)o.y};
+  const Cx<RX> alx = {(RX)s.alpha[0], (RX)s.alpha[1]}, omx = {(RX)o.x, (RX)o.y};
   double v[3] = {0.0, 0.0, 0.0};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    // every input first: the stores below may alias nothing the compiler can prove
     Cx<R> vp[12], vs[12], vt[12], vrt[12];
     Cx<RX> vx[12];
     any_load<RX>(x_, r, i, vx);
     any_load<R>(p_, r, i, vp);
     any_load<R>(s_, r, i, vs);
+    any_load<R>(t_, r, i, vt);
+    any_load<R>(rt_, r, i, vrt);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       Cx<RX> pp = {(RX)vp[k].re, (RX)vp[k].im}, ss = {(RX)vs[k].re, (RX)vs[k].im};
       vx[k] = vx[k] + cmul(alx, pp) + cmul(omx, ss);
     }
     any_store<RX>(x_, r, i, vx);
-    any_load<R>(t_, r, i, vt);
 #pragma unroll
     for (int k = 0; k < 12; ++k) vs[k] = vs[k] - cmul(om, vt[k]);
     any_store<R>(r_, r, i, vs);
-    any_load<R>(rt_, r, i, vrt);
     Cx<R> acc = {R(0), R(0)};
     R rr = 0;
 #pragma unroll
@@ -284,7 +310,7 @@ __global__ void k_bicg_xr(AnyView x_, AnyView p_, AnyView s_, AnyView t_, AnyVie
     v[1] += (double)acc.im;
     v[2] += (double)rr;
   }
-  write_partial<3>(v, partial, r);
+  write_partial<3>(v, partial_out, r);
 }
 
 // end of an iteration: rho_new, |r|^2, iteration count, stop decisions
@@ -478,6 +504,7 @@ struct Solver {
   Scal* sc = nullptr;
   int* ctl = nullptr;
   double* partial = nullptr;
+  double* partial2 = nullptr;  // the end-of-iteration partials (k_bicg_xr reads omega's from `partial`)
   double* bpartial = nullptr;  // per-block partials of the fused stencil reductions
   int* counters = nullptr;     // their group counters (zero between launches)
   unsigned nblk = 1;
@@ -516,31 +543,26 @@ struct Solver {
         RedSpec red1{1, &rt, bpartial, partial, counters, npart};
         RedSpec red2{2, nullptr, bpartial, partial, counters, npart};
         apply_mhat(opin, p, v, dag, st, "in", ctl, &red1);
-        k_bicg_alpha<<<nrhs, 1024, 0, st>>>(sc, partial, nblk, ctl, npart);
-        QCD_LAUNCH_CK();
-        k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl);
+        k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
+                                               npart);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl, &red2);
-        k_bicg_omega<<<nrhs, 1024, 0, st>>>(sc, partial, nblk, ctl, npart);
-        QCD_LAUNCH_CK();
       } else {
         apply_mhat(opin, p, v, dag, st, "in", ctl);
         k_cdot<R><<<grid, kThreads, 0, st>>>(any_view(rt), any_view(v), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
-        k_bicg_alpha<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl, nullptr);
-        QCD_LAUNCH_CK();
-        k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl);
+        k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
+                                               nullptr);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl);
         k_ts_tt<R><<<grid, kThreads, 0, st>>>(any_view(t), any_view(s), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
-        k_bicg_omega<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl, nullptr);
-        QCD_LAUNCH_CK();
       }
       k_bicg_xr<R, RX><<<grid, kThreads, 0, st>>>(any_view(xin), any_view(p), any_view(s), any_view(t),
-                                                  any_view(r), any_view(rt), nn, partial, sc, ctl);
+                                                  any_view(r), any_view(rt), nn, partial, nblk,
+                                                  fused() ? ctl + 2 : nullptr, partial2, sc, ctl);
       QCD_LAUNCH_CK();
-      k_bicg_check<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
+      k_bicg_check<<<nrhs, kThreads, 0, st>>>(sc, partial2, nblk, ctl);
       QCD_LAUNCH_CK();
       k_decide<<<1, 32, 0, st>>>(sc, nrhs, ctl);
       QCD_LAUNCH_CK();
@@ -570,10 +592,10 @@ struct Solver {
   // is reallocated), the operator's parameters and the chunk length.
   std::string graph_key(int k) const {
     char buf[512];
-    snprintf(buf, sizeof buf, "m%d i%d n%d l%d d%d t%d k%a M%a m%a L%d ws%ld c%d sc%p %p %p %p %p %p %p %p %p %p %p",
+    snprintf(buf, sizeof buf, "m%d i%d n%d l%d d%d t%d k%a M%a m%a L%d ws%ld c%d sc%p %p %p %p %p %p %p %p %p %p %p %p",
              prm.method, inner, nrhs, ls, prm.dagger, f.type, f.kappa, f.M5, f.mf, f.Ls, g->ws.generation, k,
-             (void*)sc, (void*)ctl, (void*)partial, r.data, p.data, v.data, s.data, t.data, q.data, w.data,
-             rt.data);
+             (void*)sc, (void*)ctl, (void*)partial, (void*)partial2, r.data, p.data, v.data, s.data, t.data, q.data,
+             w.data, rt.data);
     return std::string(buf) + " x" + std::to_string((uintptr_t)xin.data);
   }
 
@@ -689,6 +711,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   const size_t nstencil_blocks = (size_t)(lat.Vh / 64 + 1);
   const size_t npart = std::max<size_t>((size_t)S.nblk * nrhs, nstencil_blocks / 64 + 1);
   S.partial = (double*)g->ws.get("s.partial", sizeof(double) * npart * kMaxPartial);
+  S.partial2 = (double*)g->ws.get("s.partial2", sizeof(double) * (size_t)S.nblk * nrhs * kMaxPartial);
   if (S.fused()) {
     S.bpartial = (double*)g->ws.get("s.bpartial", sizeof(double) * nstencil_blocks * kMaxPartial);
     const size_t ngroups = nstencil_blocks / 64 + 2;
