@@ -76,8 +76,9 @@ typedef enum {
  * error-free transformations (TwoSum, TwoProd by FMA; the compensated dot
  * product "Dot2" of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)):
  * about 48 significant bits from FP32 instructions, for GPUs whose FP64 rate
- * is a small fraction of FP32.  Converting a double gives hi = fl32(x),
- * lo = fl32(x - hi), exact to 2^-48 |x| for 2^-100 < |x| < 2^100.
+ * is a small fraction of FP32.  Converting a double gives hi = x rounded to
+ * 24 significant bits and lo = fl32(x - hi): hi + lo is within 2^-48 |x| of x
+ * for 2^-100 <= |x| < 2^100 (below that the low part may underflow).
  * QCD_DF64 is available for the Wilson operator (qcd_dslash, qcd_field_pack /
  * unpack, and as the outer precision of qcd_solve). */
 typedef enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_DF64 = 3 } qcd_prec;

@@ -87,12 +87,49 @@ __device__ __forceinline__ DCx dcx_mul_i(const DCx& a) { return {df_neg(a.im), a
 __device__ __forceinline__ DCx dcx_mul_mi(const DCx& a) { return {a.im, df_neg(a.re)}; }
 
 // ----------------------------------------------------------------------------- conversions
+// FP64 <-> double-float by integer operations on the IEEE bit patterns (a
+// conversion through GB300's FP64 pipe, at 1/58 of the FP32 rate, costs three
+// or four FP64 operations per real).  For 2^-100 <= |x| < 2^100:
+//   hi = x rounded to 24 significant bits (mantissa rounded half up),
+//   lo = fl32(x - hi), with x - hi formed exactly as an integer count of
+//        units in the last place of x (|x - hi| <= 2^28 units);
+// |x - (hi + lo)| <= 2^-48 |x|.  Zeros map to zeros; other values (tiny,
+// huge, non-finite) take the FP64 conversions.
 __device__ __forceinline__ F2 df_from_double(double x) {
-  const float h = __double2float_rn(x);
-  const float l = __double2float_rn(x - (double)h);  // x - h is exact in FP64
-  return {h, l};
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = bits & 0x7fffffffffffffffull;
+  const unsigned e = (unsigned)(mag >> 52);
+  if (mag == 0) return {0.f, 0.f};
+  if (e < 923u || e > 1122u) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};  // x - h is exact in FP64
+  }
+  const unsigned long long hm = (mag + (1ull << 28)) & ~((1ull << 29) - 1);
+  const unsigned eh = (unsigned)(hm >> 52);  // e, or e + 1 after a carry out of the mantissa
+  float hi = __uint_as_float(((eh - 896u) << 23) | (unsigned)((hm >> 29) & 0x7fffffull));
+  const int r = (int)((long long)mag - (long long)hm);  // x - hi in units of 2^(e - 1075)
+  // r * 2^(e - 1075) = (r * 2^(e - 1027)) * 2^-48, both factors normal FP32 numbers
+  const float up = __uint_as_float((e - 900u) << 23);
+  float lo = __fmul_rn(__fmul_rn(__int2float_rn(r), up), 3.5527136788005009e-15f);
+  if (bits >> 63) {
+    hi = -hi;
+    lo = -lo;
+  }
+  return {hi, lo};
 }
-__device__ __forceinline__ double df_to_double(F2 a) { return (double)a.h + (double)a.l; }
+
+// FP32 -> FP64, exact, by bit manipulation for normal numbers and zero
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xffu;
+  if (ef == 0u && (u & 0x7fffffffu) == 0u) return 0.0;
+  if (ef == 0u || ef == 255u) return (double)f;
+  const unsigned long long d = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(ef + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+__device__ __forceinline__ double df_to_double(F2 a) { return f32_to_f64(a.h) + f32_to_f64(a.l); }
 
 __device__ __forceinline__ DCx dcx_load(const float4* p) {
   const float4 d = __ldg(p);

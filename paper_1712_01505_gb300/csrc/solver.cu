@@ -763,7 +763,12 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     pack_field(lat, 0, x, S.x64, st);
   else
     blas_zero(S.x64, st);
-  if (dfo) blas_copy(S.x64, x_d, st);
+  if (dfo) {
+    if (prm.x0_given)
+      blas_copy(S.x64, x_d, st);
+    else
+      blas_zero(x_d, st);
+  }
 
   // |b - A x| on the full system from the even-odd residual rhat = bhat - Mhat x_e:
   // Wilson: (rhat, 0);  DWF: (A rhat, 0)  (exact reconstruction of x_o)

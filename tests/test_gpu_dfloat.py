@@ -42,8 +42,9 @@ def test_pack_unpack_roundtrip_within_2_pow_48():
         qcd.field_unpack(g, f, "df64", parity, buf, back)
     torch.cuda.synchronize()
     b = back.cpu().numpy()
+    # split error <= 2^-48 |x|, plus the rounding of the FP64 sum hi + lo on unpack
     for part in (np.real, np.imag):
-        assert np.all(np.abs(part(b) - part(psi)) <= 2.0 ** -48 * np.abs(part(psi)))
+        assert np.all(np.abs(part(b) - part(psi)) <= 2.0 ** -47 * np.abs(part(psi)))
     # exactly representable values survive unchanged
     exact = np.round(psi.real / scale) * scale + 0j
     qcd.field_pack(g, f, "df64", 0, to_dev(exact), buf)
@@ -51,6 +52,35 @@ def test_pack_unpack_roundtrip_within_2_pow_48():
     qcd.field_unpack(g, f, "df64", 0, buf, back)
     par = ora.parity(L)
     assert np.array_equal(back.cpu().numpy()[par == 0], exact[par == 0])
+
+
+def test_split_edge_values():
+    """Values at the edges of the split: a mantissa of all ones (the rounding carries into the
+    exponent), powers of two, FP32-exact values, zeros, and magnitudes outside 2^-100 .. 2^100
+    (the FP64 conversion path), each within 2^-47 of its value after a pack / unpack."""
+    device()
+    L = (2, 2, 2, 2)
+    V = 16
+    vals = [np.nextafter(2.0, 0.0), -np.nextafter(1.0, 0.0), 1.0, -0.5, 2.0 ** 99, 2.0 ** -99,
+            np.nextafter(2.0 ** 100, 0.0), 1.0 + 2.0 ** -24, 1.0 + 2.0 ** -25, 1.0 - 2.0 ** -53, 0.0, -0.0,
+            3.0e-35, -7.0e-40, 1.0e35, -2.0e31, 0.1, -1.0 / 3.0, np.pi, 2.0 ** -60 * np.e]
+    vals = np.array(vals * ((V * 12 + len(vals) - 1) // len(vals)))[: V * 12]
+    psi = (vals + 1j * vals[::-1]).reshape(V, 4, 3)
+    U = inputs.gauge_field(L, 0.3, 1)
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    f = qcd.wilson(0.1)
+    buf = torch.empty(qcd.field_bytes(g, f, "df64"), dtype=torch.uint8, device=device())
+    back = torch.zeros((V, 4, 3), dtype=torch.complex128, device=device())
+    for parity in (0, 1):
+        qcd.field_pack(g, f, "df64", parity, to_dev(psi), buf)
+        qcd.field_unpack(g, f, "df64", parity, buf, back)
+    torch.cuda.synchronize()
+    b = back.cpu().numpy()
+    for part in (np.real, np.imag):
+        err = np.abs(part(b) - part(psi))
+        big = np.abs(part(psi)) >= 1e-30  # below FP32's normal range the low part underflows
+        assert np.all(err[big] <= 2.0 ** -47 * np.abs(part(psi))[big])
+        assert np.all(err[~big] <= 1e-44)
 
 
 @pytest.mark.parametrize("L", [(4, 4, 4, 4), (6, 4, 6, 10), (2, 2, 2, 2)])
