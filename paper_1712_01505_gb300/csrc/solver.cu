@@ -16,8 +16,9 @@
 // and only the final true residual uses the IEEE-FP64 stencil.
 //
 // The scalars (alpha, beta, omega, rho, |r|^2) never leave the device during
-// the inner iteration: per-block partial sums become scalars either in small
-// one-block kernels or in the prologue of the next vector kernel (alpha, omega).
+// the inner iteration: per-block partial sums become scalars in the prologue of
+// the next vector kernel (alpha, omega) or in the one-block kernel that ends an
+// iteration (rho_new, |r|^2, beta and the stop decision).
 // Every kernel of the iteration first reads a stop word; when an iteration
 // raises it (convergence check due, reliable update due, breakdown, NaN) the
 // remaining launches of the chunk do nothing, so a chunk of K iterations can
@@ -25,6 +26,7 @@
 // synchronisation per chunk.
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <limits>
 #include <string>
@@ -91,32 +93,22 @@ __device__ __forceinline__ void write_partial(double v[NR], double* partial, int
 #define STOPPED(ctl) (*(ctl) != 0)
 
 // ----------------------------------------------------------------------------- BiCGStab kernels
-// beta = (rho_new / rho)(alpha / omega); rho = rho_new        <<<1, 32>>>
-__global__ void k_bicg_beta(Scal* sc, int nrhs, const int* ctl) {
-  if (STOPPED(ctl)) return;
-  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
-    Scal& s = sc[r];
-    if (!s.active) continue;
-    double2 rn = make_double2(s.rho_new[0], s.rho_new[1]);
-    double2 ro = make_double2(s.rho[0], s.rho[1]);
-    double2 al = make_double2(s.alpha[0], s.alpha[1]);
-    double2 om = make_double2(s.omega[0], s.omega[1]);
-    double2 b = cmul2(cdiv(rn, ro), cdiv(al, om));
-    s.beta[0] = b.x;
-    s.beta[1] = b.y;
-    s.rho[0] = rn.x;
-    s.rho[1] = rn.y;
-  }
-}
+// beta = (rho_new / rho)(alpha / omega) is formed at the end of an iteration by
+// k_bicg_check (and by the host when the recursion restarts); the first vector
+// kernel of the next iteration moves rho_new into rho.
 
-// p = r + beta (p - omega v)
+// p = r + beta (p - omega v); rho = rho_new
 template <typename R>
-__global__ void k_bicg_p(AnyView r_, AnyView p_, AnyView v_, long n, const Scal* sc, const int* ctl) {
+__global__ void k_bicg_p(AnyView r_, AnyView p_, AnyView v_, long n, Scal* sc, const int* ctl) {
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
-  const Scal& s = sc[r];
+  Scal& s = sc[r];
   if (!s.active) return;
   const Cx<R> be = {(R)s.beta[0], (R)s.beta[1]}, om = {(R)s.omega[0], (R)s.omega[1]};
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // no block of this kernel reads rho
+    s.rho[0] = s.rho_new[0];
+    s.rho[1] = s.rho_new[1];
+  }
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vr[12], vp[12], vv[12];
     any_load<R>(r_, r, i, vr);
@@ -314,7 +306,9 @@ __global__ void k_bicg_xr(AnyView x_, AnyView p_, AnyView s_, AnyView t_, AnyVie
 }
 
 // end of an iteration: rho_new, |r|^2, iteration count, stop decisions
-__global__ void k_bicg_check(Scal* sc, const double* partial, int nblk, int* ctl) {
+// and the next beta; with decide != 0 (one right-hand side) any flag stops the chunk
+// at once, otherwise k_decide weighs the flags of all right-hand sides
+__global__ void k_bicg_check(Scal* sc, const double* partial, int nblk, int* ctl, int decide) {
   if (STOPPED(ctl)) return;
   int r = blockIdx.x;
   Scal& s = sc[r];
@@ -333,28 +327,27 @@ __global__ void k_bicg_check(Scal* sc, const double* partial, int nblk, int* ctl
   } else if (s.delta2 > 0.0 && d[2] <= s.delta2 * s.r2_ref) {
     s.flag = FLAG_UPDATE;
   }
+  const double2 b = cmul2(cdiv(make_double2(d[0], d[1]), make_double2(s.rho[0], s.rho[1])),
+                          cdiv(make_double2(s.alpha[0], s.alpha[1]), make_double2(s.omega[0], s.omega[1])));
+  s.beta[0] = b.x;
+  s.beta[1] = b.y;
+  if (decide && s.flag != FLAG_NONE) *ctl = 1;
 }
 
 // ----------------------------------------------------------------------------- CG kernels
-__global__ void k_cg_beta(Scal* sc, int nrhs, const int* ctl) {
-  if (STOPPED(ctl)) return;
-  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
-    Scal& s = sc[r];
-    if (!s.active) continue;
-    s.beta[0] = s.rr_new / s.rr;
-    s.beta[1] = 0.0;
-    s.rr = s.rr_new;
-  }
-}
+// beta = rr_new / rr is formed at the end of an iteration by k_cg_check (and by
+// the host when the recursion restarts); the first vector kernel of the next
+// iteration moves rr_new into rr.
 
-// p = r + beta p
+// p = r + beta p; rr = rr_new
 template <typename R>
-__global__ void k_cg_p(AnyView r_, AnyView p_, long n, const Scal* sc, const int* ctl) {
+__global__ void k_cg_p(AnyView r_, AnyView p_, long n, Scal* sc, const int* ctl) {
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
-  const Scal& s = sc[r];
+  Scal& s = sc[r];
   if (!s.active) return;
   const R be = (R)s.beta[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) s.rr = s.rr_new;  // no block of this kernel reads rr
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vr[12], vp[12];
     any_load<R>(r_, r, i, vr);
@@ -365,51 +358,58 @@ __global__ void k_cg_p(AnyView r_, AnyView p_, long n, const Scal* sc, const int
   }
 }
 
-// alpha = rr / Re(p, q)
-__global__ void k_cg_alpha(Scal* sc, const double* partial, int nblk, int* ctl) {
-  if (STOPPED(ctl)) return;
-  int r = blockIdx.x;
-  Scal& s = sc[r];
-  if (!s.active) return;
+// alpha = rr / Re(p, q) from the k_rdot partials, formed by every block (see
+// block_alpha); false (for every block) on NaN or breakdown
+__device__ __forceinline__ bool block_cg_alpha(Scal& s, const double* partial, int nb, int r, int* ctl,
+                                               double* al) {
+  __shared__ double sh;
+  __shared__ int ok;
   double d[2];
-  sum_partials<2>(partial, nblk, r, d);
-  if (threadIdx.x) return;
-  if (bad(d[0])) {
-    s.flag = FLAG_NAN;
-    *ctl = 1;
-    return;
+  sum_partials<2>(partial, nb, r, d);
+  if (threadIdx.x == 0) {
+    const int flag = bad(d[0]) ? FLAG_NAN : (d[0] <= 0.0 ? FLAG_BREAKDOWN : FLAG_NONE);
+    ok = flag == FLAG_NONE;
+    sh = ok ? s.rr / d[0] : 0.0;
+    if (blockIdx.x == 0) {
+      if (ok) {
+        s.alpha[0] = sh;
+        s.alpha[1] = 0.0;
+      } else {
+        s.flag = flag;
+        *ctl = 1;
+      }
+    }
   }
-  if (d[0] <= 0.0) {
-    s.flag = FLAG_BREAKDOWN;
-    *ctl = 1;
-    return;
-  }
-  s.alpha[0] = s.rr / d[0];
-  s.alpha[1] = 0.0;
+  __syncthreads();
+  *al = sh;
+  return ok;
 }
 
-// x += alpha p; r -= alpha q; partial |r|^2
+// alpha from the Re(p, q) partials, then x += alpha p; r -= alpha q; partial |r|^2
+// into partial_out (not the array alpha is read from)
 template <typename R, typename RX>
-__global__ void k_cg_xr(AnyView x_, AnyView p_, AnyView q_, AnyView r_, long n, double* partial,
-                        const Scal* sc, const int* ctl) {
+__global__ void k_cg_xr(AnyView x_, AnyView p_, AnyView q_, AnyView r_, long n, const double* partial_in,
+                        int nblk, double* partial_out, Scal* sc, int* ctl) {
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
-  const Scal& s = sc[r];
+  Scal& s = sc[r];
   if (!s.active) return;
-  const R al = (R)s.alpha[0];
-  const RX alx = (RX)s.alpha[0];
+  double a;
+  if (!block_cg_alpha(s, partial_in, nblk, r, ctl, &a)) return;
+  const R al = (R)a;
+  const RX alx = (RX)a;
   double v[1] = {0.0};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vp[12], vq[12], vr[12];
     Cx<RX> vx[12];
     any_load<RX>(x_, r, i, vx);
     any_load<R>(p_, r, i, vp);
+    any_load<R>(q_, r, i, vq);
+    any_load<R>(r_, r, i, vr);
 #pragma unroll
     for (int k = 0; k < 12; ++k)
       vx[k] = {fma(alx, (RX)vp[k].re, vx[k].re), fma(alx, (RX)vp[k].im, vx[k].im)};
     any_store<RX>(x_, r, i, vx);
-    any_load<R>(q_, r, i, vq);
-    any_load<R>(r_, r, i, vr);
     R rr = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -419,10 +419,11 @@ __global__ void k_cg_xr(AnyView x_, AnyView p_, AnyView q_, AnyView r_, long n, 
     any_store<R>(r_, r, i, vr);
     v[0] += (double)rr;
   }
-  write_partial<1>(v, partial, r);
+  write_partial<1>(v, partial_out, r);
 }
 
-__global__ void k_cg_check(Scal* sc, const double* partial, int nblk, int* ctl) {
+// end of an iteration: rr_new, flags and the next beta; decide as in k_bicg_check
+__global__ void k_cg_check(Scal* sc, const double* partial, int nblk, int* ctl, int decide) {
   if (STOPPED(ctl)) return;
   int r = blockIdx.x;
   Scal& s = sc[r];
@@ -439,6 +440,9 @@ __global__ void k_cg_check(Scal* sc, const double* partial, int nblk, int* ctl) 
     s.flag = FLAG_CHECK;
   else if (s.delta2 > 0.0 && d[0] <= s.delta2 * s.r2_ref)
     s.flag = FLAG_UPDATE;
+  s.beta[0] = d[0] / s.rr;
+  s.beta[1] = 0.0;
+  if (decide && s.flag != FLAG_NONE) *ctl = 1;
 }
 
 // partial sums of Re(a, b)
@@ -533,8 +537,6 @@ struct Solver {
   template <typename R, typename RX>
   void body_t(dim3 grid, long nn, int dag) {
     if (bicg()) {
-      k_bicg_beta<<<1, 32, 0, st>>>(sc, nrhs, ctl);
-      QCD_LAUNCH_CK();
       k_bicg_p<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(p), any_view(v), nn, sc, ctl);
       QCD_LAUNCH_CK();
       if (fused()) {
@@ -562,28 +564,28 @@ struct Solver {
                                                   any_view(r), any_view(rt), nn, partial, nblk,
                                                   fused() ? ctl + 2 : nullptr, partial2, sc, ctl);
       QCD_LAUNCH_CK();
-      k_bicg_check<<<nrhs, kThreads, 0, st>>>(sc, partial2, nblk, ctl);
+      k_bicg_check<<<nrhs, kThreads, 0, st>>>(sc, partial2, nblk, ctl, nrhs == 1);
       QCD_LAUNCH_CK();
-      k_decide<<<1, 32, 0, st>>>(sc, nrhs, ctl);
-      QCD_LAUNCH_CK();
+      if (nrhs > 1) {
+        k_decide<<<1, 32, 0, st>>>(sc, nrhs, ctl);
+        QCD_LAUNCH_CK();
+      }
     } else {
-      k_cg_beta<<<1, 32, 0, st>>>(sc, nrhs, ctl);
-      QCD_LAUNCH_CK();
       k_cg_p<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(p), nn, sc, ctl);
       QCD_LAUNCH_CK();
       apply_mhat(opin, p, w, 0, st, "in", ctl);
       apply_mhat(opin, w, q, 1, st, "in", ctl);
       k_rdot<R><<<grid, kThreads, 0, st>>>(any_view(p), any_view(q), nn, partial, sc, ctl);
       QCD_LAUNCH_CK();
-      k_cg_alpha<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
-      QCD_LAUNCH_CK();
       k_cg_xr<R, RX><<<grid, kThreads, 0, st>>>(any_view(xin), any_view(p), any_view(q), any_view(r),
-                                                nn, partial, sc, ctl);
+                                                nn, partial, nblk, partial2, sc, ctl);
       QCD_LAUNCH_CK();
-      k_cg_check<<<nrhs, kThreads, 0, st>>>(sc, partial, nblk, ctl);
+      k_cg_check<<<nrhs, kThreads, 0, st>>>(sc, partial2, nblk, ctl, nrhs == 1);
       QCD_LAUNCH_CK();
-      k_decide<<<1, 32, 0, st>>>(sc, nrhs, ctl);
-      QCD_LAUNCH_CK();
+      if (nrhs > 1) {
+        k_decide<<<1, 32, 0, st>>>(sc, nrhs, ctl);
+        QCD_LAUNCH_CK();
+      }
     }
   }
 
@@ -858,9 +860,18 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
         }
         s.rho_new[0] = re[r];
         s.rho_new[1] = im[r];
+        // the first iteration's beta (later ones are formed by k_bicg_check)
+        const std::complex<double> b = (std::complex<double>(s.rho_new[0], s.rho_new[1]) /
+                                        std::complex<double>(s.rho[0], s.rho[1])) *
+                                       (std::complex<double>(s.alpha[0], s.alpha[1]) /
+                                        std::complex<double>(s.omega[0], s.omega[1]));
+        s.beta[0] = b.real();
+        s.beta[1] = b.imag();
       } else {
         if (full) s.rr = 1.0;
         s.rr_new = rn[r];
+        s.beta[0] = s.rr_new / s.rr;  // the first iteration's beta (p = 0 after a full restart)
+        s.beta[1] = 0.0;
       }
     }
     if (full && !S.bicg()) blas_zero(S.p, st);
