@@ -79,21 +79,26 @@ def run_dwf(args):
                      "hop_gbs": round(alg / ms / 1e6, 1), "hop_frac": round(alg / ms / 1e6 / _peak(), 4),
                      "mhat_ms": round(ms_m, 4)}
     res = {}
-    for inner in ("f16", "f32", "f64"):
+    # inner precision / outer precision of the mixed solves; "f64" is the plain FP64 CG
+    for name, inner, outer in (("f16", "f16", "f64"), ("f32", "f32", "f64"), ("f16_df", "f16", "df64"),
+                               ("f32_df", "f32", "df64"), ("f64", "f64", "f64")):
+        kw = dict(method=qcd.CG_NORMAL, tol=1e-10, inner=inner, use_graph=True, graph_chunk=32,
+                  delta=(args.delta or 0.0), outer=outer)
         x = torch.zeros_like(bd)
-        qcd.solve(g, f, bd, x, method=qcd.CG_NORMAL, tol=1e-10, inner=inner, use_graph=True, graph_chunk=32,
-                  delta=(args.delta or 0.0))  # warm-up (tuning, workspace)
+        qcd.solve(g, f, bd, x, **kw)  # warm-up (tuning, workspace)
         x.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        info, _ = qcd.solve(g, f, bd, x, method=qcd.CG_NORMAL, tol=1e-10, inner=inner, use_graph=True,
-                            graph_chunk=32, delta=(args.delta or 0.0))
+        info, _ = qcd.solve(g, f, bd, x, **kw)
         torch.cuda.synchronize()
-        res[inner] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "iters": info[0]["iters"],
-                      "updates": info[0]["outer_updates"], "true_resid": info[0]["true_resid"]}
+        res[name] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "iters": info[0]["iters"],
+                     "updates": info[0]["outer_updates"], "true_resid": info[0]["true_resid"]}
     out = {"workload": "dwf_16x16x16x32_Ls16_M5_1.8_mf0.02", "hop": hop, "cg": res,
+           "note": "cg keys: inner precision, _df = double-float outer steps (else IEEE FP64)",
            "speedup_f16_vs_f64": round(res["f64"]["ms"] / res["f16"]["ms"], 3),
-           "speedup_f32_vs_f64": round(res["f64"]["ms"] / res["f32"]["ms"], 3)}
+           "speedup_f32_vs_f64": round(res["f64"]["ms"] / res["f32"]["ms"], 3),
+           "speedup_f16_df_vs_f64": round(res["f64"]["ms"] / res["f16_df"]["ms"], 3),
+           "speedup_f32_df_vs_f64": round(res["f64"]["ms"] / res["f32_df"]["ms"], 3)}
     print(json.dumps(out), flush=True)
 
 

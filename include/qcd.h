@@ -79,8 +79,9 @@ typedef enum {
  * is a small fraction of FP32.  Converting a double gives hi = x rounded to
  * 24 significant bits and lo = fl32(x - hi): hi + lo is within 2^-48 |x| of x
  * for 2^-100 <= |x| < 2^100 (below that the low part may underflow).
- * QCD_DF64 is available for the Wilson operator (qcd_dslash, qcd_field_pack /
- * unpack, and as the outer precision of qcd_solve). */
+ * QCD_DF64 is available in qcd_field_pack / unpack, in qcd_dslash (every op
+ * for Wilson; D_EO, D_OE, MHAT, MHAT_DAG for domain-wall) and as the outer
+ * precision of qcd_solve. */
 typedef enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_DF64 = 3 } qcd_prec;
 
 typedef enum { QCD_WILSON = 0, QCD_DWF = 1 } qcd_fermion_type;
@@ -139,8 +140,8 @@ typedef struct {
  * outer: precision of the operator applications of the outer steps of a
  *   mixed solve (source preparation, reliable-update residuals b - Mhat x,
  *   reconstruction of the odd sites): QCD_F64 (IEEE double, the default when
- *   zero-initialised) or QCD_DF64 (double-float, Wilson only).  The solution
- *   is accumulated in FP64 and the final true_resid is computed with IEEE
+ *   zero-initialised) or QCD_DF64 (double-float; the solution is then also
+ *   accumulated in double-float).  The final true_resid is computed with IEEE
  *   FP64 operators either way; ignored when inner = QCD_F64. */
 typedef struct {
   int32_t method;

@@ -359,7 +359,8 @@ qcd_status qcd_dslash(const qcd_gauge* gc, const qcd_fermion* fermion, qcd_prec 
     cudaStream_t st = (cudaStream_t)stream;
     OpCtx c{g, *fermion, prec};
     const bool dwf = fermion->type == QCD_DWF;
-    if (dwf && prec == QCD_DF64) raise(QCD_ERR_UNSUPPORTED, "double-float is available for the Wilson operator");
+    if (dwf && prec == QCD_DF64 && (op == QCD_OP_FULL || op == QCD_OP_FULL_DAG))
+      raise(QCD_ERR_UNSUPPORTED, "the unpreconditioned domain-wall matrix is not available in double-float");
     if (layout == QCD_LAYOUT_INTERNAL) {
       if (op == QCD_OP_FULL || op == QCD_OP_FULL_DAG) raise(QCD_ERR_UNSUPPORTED, "FULL ops need the canonical layout");
       if (!is_device_ptr(in) || !is_device_ptr(out)) raise(QCD_ERR_ARG, "internal buffers must be device memory");
@@ -427,8 +428,6 @@ qcd_status qcd_solve(const qcd_gauge* gc, const qcd_fermion* fermion, const qcd_
       raise(QCD_ERR_ARG, "inner precision must be QCD_F64, QCD_F32 or QCD_F16 (got %d)", p.inner);
     if (p.outer != QCD_F64 && p.outer != QCD_DF64)
       raise(QCD_ERR_ARG, "outer precision must be QCD_F64 or QCD_DF64 (got %d)", p.outer);
-    if (p.outer == QCD_DF64 && fermion->type == QCD_DWF)
-      raise(QCD_ERR_UNSUPPORTED, "a double-float outer precision is available for Wilson fermions");
     if (p.maxiter < 0) raise(QCD_ERR_ARG, "maxiter must be >= 0");
     if (p.delta < 0 || p.delta >= 1) raise(QCD_ERR_ARG, "delta must be in [0, 1)");
     cudaStream_t user = (cudaStream_t)stream;

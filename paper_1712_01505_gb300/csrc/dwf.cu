@@ -175,6 +175,10 @@ dim3 grid_for(const Field& f, dim3 blk, int Ls) {
 
 void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double scale,
              const Field* x, cudaStream_t st, const int* stop) {
+  if (in.prec == QCD_DF64) {
+    dw_ainv_df(p, in, out, dagger, scale, x, st, stop);
+    return;
+  }
   if (p.Ls < 1 || p.Ls > kMaxLs) raise(QCD_ERR_ARG, "Ls must be in [1, %d]", kMaxLs);
   if (in.data == out.data || (x && x->data == out.data))
     raise(QCD_ERR_ARG, "dw_ainv: output aliases an input");
@@ -218,6 +222,8 @@ void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double 
 void dw_block(const DwParams& p, const Field& in, Field& out, int dagger, double c, const Field* y,
               cudaStream_t st) {
   if (in.data == out.data) raise(QCD_ERR_ARG, "dw_block: in and out alias");
+  if (in.prec == QCD_DF64 || out.prec == QCD_DF64 || (y && y->prec == QCD_DF64))
+    raise(QCD_ERR_UNSUPPORTED, "the domain-wall block A is not available in double-float");
   dim3 blk = block_for(p.Ls);
   dim3 grid = grid_for(in, blk, p.Ls);
   AnyView yv = y ? any_view(*y) : any_view(out);

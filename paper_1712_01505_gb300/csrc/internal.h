@@ -155,6 +155,9 @@ struct DwParams {
 // out = [x +] c * A^-1 in (A^-dag for dagger), per site over (s, spin)
 void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double c, const Field* x,
              cudaStream_t st, const int* stop = nullptr);
+// the same on double-float fields (dwf_df.cu; dw_ainv dispatches to it)
+void dw_ainv_df(const DwParams& p, const Field& in, Field& out, int dagger, double c, const Field* x,
+                cudaStream_t st, const int* stop = nullptr);
 // out = A in + c * y  (y may be null), A^dag for dagger
 void dw_block(const DwParams& p, const Field& in, Field& out, int dagger, double c, const Field* y,
               cudaStream_t st);

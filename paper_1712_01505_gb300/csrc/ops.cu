@@ -26,7 +26,6 @@ void apply_mhat(const OpCtx& c, const Field& in, Field& out, int dagger, cudaStr
     return;
   }
   if (red) raise(QCD_ERR_UNSUPPORTED, "fused reductions are for the Wilson operator");
-  if (c.prec == QCD_DF64) raise(QCD_ERR_UNSUPPORTED, "double-float is available for the Wilson operator");
   DwParams p{c.f.Ls, c.f.M5, c.f.mf};
   Field t1 = ws_field(c.g, t + ".mhat.t1", c.prec, in.ls, in.nrhs);
   Field t2 = ws_field(c.g, t + ".mhat.t2", c.prec, in.ls, in.nrhs);
@@ -52,7 +51,8 @@ void apply_full_parity(const OpCtx& c, const Field& in_same, const Field& in_oth
     hop(c.g, in_other, out, parity, dagger, -c.f.kappa, &in_same, st);
     return;
   }
-  if (c.prec == QCD_DF64) raise(QCD_ERR_UNSUPPORTED, "double-float is available for the Wilson operator");
+  if (c.prec == QCD_DF64)
+    raise(QCD_ERR_UNSUPPORTED, "the unpreconditioned domain-wall matrix is not available in double-float");
   DwParams p{c.f.Ls, c.f.M5, c.f.mf};
   Field t = ws_field(c.g, std::string(tag) + ".full.t", c.prec, in_same.ls, in_same.nrhs);
   hop(c.g, in_other, t, parity, dagger, 1.0, nullptr, st);

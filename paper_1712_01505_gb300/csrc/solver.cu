@@ -722,11 +722,12 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     if (g->ws.generation != gen) QCD_CK(cudaMemsetAsync(S.counters, 0, sizeof(int) * ngroups, st));
   }
   S.hsc.assign(nrhs, Scal{});
-  // Double-float outer steps (Wilson, mixed): the prepared source, the solution
+  // Double-float outer steps (mixed solves): the prepared source, the solution
   // and the outer residual live in FP32 pairs and the outer operator
-  // applications use the double-float stencil; the true residual reported at
-  // the end is recomputed with the IEEE-FP64 operator all the same.
-  const bool dfo = prm.outer == QCD_DF64 && !dwf && S.inner != QCD_F64;
+  // applications use the double-float stencil (and A^-1 for domain-wall); the
+  // true residual reported at the end is recomputed with the IEEE-FP64
+  // operator all the same.
+  const bool dfo = prm.outer == QCD_DF64 && S.inner != QCD_F64;
   const OpCtx opdf{g, f, QCD_DF64};
   Field be_d, bo_d, bh_d, x_d, t_d, u_d, r_d;
   if (dfo) {
@@ -751,7 +752,13 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   if (dfo) {
     blas_copy(S.b_e, be_d, st);
     blas_copy(S.b_o, bo_d, st);
-    hop_df(g, bo_d, bh_d, 0, dag, f.kappa, &be_d, nullptr, 0.0, st);
+    if (!dwf) {
+      hop_df(g, bo_d, bh_d, 0, dag, f.kappa, &be_d, nullptr, 0.0, st);
+    } else {
+      dw_ainv(dp, bo_d, t_d, 0, 1.0, nullptr, st);
+      hop(g, t_d, u_d, 0, 0, 0.5, &be_d, st);
+      dw_ainv(dp, u_d, bh_d, 0, 1.0, nullptr, st);
+    }
   } else if (!dwf) {
     // bhat = b_e + kappa H_eo b_o
     hop(g, S.b_o, S.bh, 0, dag, f.kappa, &S.b_e, st);
@@ -779,12 +786,21 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     if (dfo) {
       if (x_is_zero) {
         blas_copy(bh_d, t_d, st);
-      } else {
+      } else if (!dwf) {
         // rhat = bhat - x + kappa^2 H_eo H_oe x  (H -> H^dag for the adjoint system)
         hop_df(g, x_d, u_d, 1, dag, 1.0, nullptr, nullptr, 0.0, st);
         hop_df(g, u_d, t_d, 0, dag, f.kappa * f.kappa, &bh_d, &x_d, -1.0, st);
+      } else {
+        apply_mhat(opdf, x_d, t_d, dag, st, "odf");
+        blas_axpby(1.0, bh_d, -1.0, t_d, st);  // rhat = bhat - Mhat x
       }
-      blas_norm2(t_d, rfull.data(), st, g);
+      if (dwf) {  // |A rhat| (to FP64 for the block A; it decides no more than the stop)
+        blas_copy(t_d, S.t64, st);
+        dw_block(dp, S.t64, S.u64, 0, 0.0, nullptr, st);
+        blas_norm2(S.u64, rfull.data(), st, g);
+      } else {
+        blas_norm2(t_d, rfull.data(), st, g);
+      }
       for (int r = 0; r < nrhs; ++r) rfull[r] = std::sqrt(rfull[r]);
       if (!S.bicg()) apply_mhat(opdf, t_d, r_d, 1, st, "odf");
       blas_norm2(r_outer, rn.data(), st, g);
@@ -981,8 +997,15 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     blas_axpby(f.kappa, S.u64, 1.0, S.bh, st);
     blas_norm2(S.bh, ro_.data(), st, g);
   } else {
-    hop(g, S.x64, S.u64, 1, 0, 0.5, &S.b_o, st);  // x_o = A^-1 (b_o + 1/2 H_oe x_e)
-    dw_ainv(dp, S.u64, S.t64, 0, 1.0, nullptr, st);
+    if (dfo) {
+      hop(g, x_d, u_d, 1, 0, 0.5, &bo_d, st);  // x_o = A^-1 (b_o + 1/2 H_oe x_e)
+      dw_ainv(dp, u_d, t_d, 0, 1.0, nullptr, st);
+      blas_copy(x_d, S.x64, st);
+      blas_copy(t_d, S.t64, st);
+    } else {
+      hop(g, S.x64, S.u64, 1, 0, 0.5, &S.b_o, st);  // x_o = A^-1 (b_o + 1/2 H_oe x_e)
+      dw_ainv(dp, S.u64, S.t64, 0, 1.0, nullptr, st);
+    }
     unpack_field(lat, 0, S.x64, x, st);
     unpack_field(lat, 1, S.t64, x, st);
     // true residual on the full system, both parities

@@ -233,6 +233,4 @@ def test_argument_checks():
     xd = torch.zeros((4, V, 4, 3), dtype=torch.complex128, device=device())
     bd = to_dev(inputs.gaussian_source((4, V, 4, 3), 1))
     with pytest.raises(qcd.QCDError, match="ERR_UNSUPPORTED"):
-        qcd.solve(g, d, bd, xd, method=qcd.CG_NORMAL, inner="f32", outer="df64")
-    with pytest.raises(qcd.QCDError, match="ERR_UNSUPPORTED"):
-        qcd.dslash(g, d, "D_EO", bd, xd, prec="df64")
+        qcd.dslash(g, d, "FULL_DAG", bd, xd, prec="df64")

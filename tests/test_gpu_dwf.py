@@ -111,3 +111,65 @@ def test_dw_rejects_bicgstab():
     x = torch.zeros((Ls, V, 4, 3), dtype=torch.complex128, device=device())
     _, st = qcd.solve(g, f, to_dev(b), x, method=qcd.BICGSTAB, check=False)
     assert st == qcd.ERR_UNSUPPORTED
+
+
+# ----------------------------------------------------------------------------- double-float
+# hi + lo pairs of FP32 (see test_gpu_dfloat.py for the bound): element-wise 1e-12 of the
+# largest output for the hop; M_hat adds two A^-1 applications whose closed-form sums run over
+# Ls terms with weights below 1 / (5 - M5), the same bound holds.
+DF_TOL = 1e-12
+
+
+@pytest.mark.parametrize("L,Ls", [((4, 4, 4, 8), 8), ((6, 4, 2, 10), 5)])
+def test_dw_double_float_hop_on_every_slice(L, Ls):
+    device()
+    V, U, psi = _case(L, Ls, 31)
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    f = qcd.dwf(Ls, M5, MF)
+    out = torch.empty((Ls, V, 4, 3), dtype=torch.complex128, device=device())
+    qcd.dslash(g, f, "D_OE", to_dev(psi), out, prec="df64")
+    torch.cuda.synchronize()
+    par = ora.parity(L)
+    ref = np.empty_like(psi)
+    for s in range(Ls):
+        inp = psi[s].copy()
+        inp[par == 1] = 0
+        ref[s] = ora.hop(L, BC, U, inp, out_parity=1)
+    assert max_err(out, ref) < DF_TOL
+
+
+@pytest.mark.parametrize("dag", [False, True])
+@pytest.mark.parametrize("Ls", [8, 16])
+def test_dw_double_float_mhat(dag, Ls):
+    device()
+    L = (4, 4, 4, 8)
+    V, U, psi = _case(L, Ls, 41)
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    f = qcd.dwf(Ls, M5, MF)
+    par = ora.parity(L)
+    pe = psi.copy()
+    pe[:, par == 1] = 0
+    out = torch.empty((Ls, V, 4, 3), dtype=torch.complex128, device=device())
+    qcd.dslash(g, f, "MHAT_DAG" if dag else "MHAT", to_dev(psi), out, prec="df64")
+    torch.cuda.synchronize()
+    assert max_err(out, ora.dw_mhat(L, BC, Ls, M5, MF, U, pe, dagger=dag)) < DF_TOL
+    with pytest.raises(qcd.QCDError, match="ERR_UNSUPPORTED"):
+        qcd.dslash(g, f, "FULL", to_dev(psi), out, prec="df64")
+
+
+@pytest.mark.parametrize("inner", ["f32", "f16"])
+def test_dw_cg_solve_with_double_float_outer_steps(inner):
+    device()
+    L, Ls = (4, 4, 4, 8), 8
+    V, U, b = _case(L, Ls, 61)
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=12)
+    f = qcd.dwf(Ls, M5, MF)
+    x = torch.zeros((Ls, V, 4, 3), dtype=torch.complex128, device=device())
+    info, _ = qcd.solve(g, f, to_dev(b), x, method=qcd.CG_NORMAL, tol=1e-10, inner=inner,
+                        use_graph=True, graph_chunk=16, outer="df64")
+    assert info[0]["converged"], info
+    xr = x.cpu().numpy()
+    res = np.linalg.norm(b - ora.dw(L, BC, Ls, M5, MF, U, xr)) / np.linalg.norm(b)
+    assert res <= 1e-10
+    assert abs(res - info[0]["true_resid"]) <= 1e-6 * res
+    assert info[0]["outer_updates"] >= 2
