@@ -131,7 +131,7 @@ def run_batched(args):
                                             layout=qcd.INTERNAL))
     alg12 = Vh * (8 * 48 + 12 * 192)
     kw = dict(method=qcd.BICGSTAB, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32,
-              delta=(args.delta or 1e-4))
+              delta=(args.delta or 1e-4), outer=args.outer)
     x = torch.zeros_like(bd)
     qcd.solve(g, f, bd, x, nrhs=12, **kw)  # warm-up
     x.zero_()
@@ -155,7 +155,7 @@ def run_batched(args):
            "solve12_s": round(t_batch, 4), "solve_12x1_s": round(t_seq, 4),
            "speedup_batched": round(t_seq / t_batch, 3),
            "iters": [i["iters"] for i in info], "iters_seq": iters_seq,
-           "max_true_resid": max(i["true_resid"] for i in info)}
+           "max_true_resid": max(i["true_resid"] for i in info), "outer": args.outer}
     print(json.dumps(out), flush=True)
 
 
