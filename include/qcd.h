@@ -238,6 +238,43 @@ qcd_status qcd_solve(const qcd_gauge* g, const qcd_fermion* fermion,
 qcd_status qcd_force(const qcd_gauge* g, const qcd_fermion* fermion, const void* X,
                      const void* eta, void* dSdU, void* stream);
 
+/* Fermion force of the even-odd pseudofermion action S = phi_e^dag (Mhat^dag
+ * Mhat)^-1 phi_e (Wilson, Mhat = 1 - kappa^2 H_eo H_oe on the even sites; the
+ * consumer of repeated solves in ensemble generation, Sec. II A): given
+ * X = (Mhat^dag Mhat)^-1 phi_e and Y = Mhat X as canonical (V,4,3) complex128
+ * fields (device; their odd sites are ignored), write dS/dRe U_ab and
+ * dS/dIm U_ab into dSdU ((4, V, 3, 3, 2) float64, device):
+ *   dS = 2 kappa^2 Re(eta^dag dH xi),  xi = (X, H_oe X),  eta = (Y, (H^dag)_oe Y).
+ * X and Y can be had from two solves: z = the even part of the solution of
+ * M^dag z = (phi_e, 0) is (Mhat^dag)^-1 phi_e, so Y = z and X = the even part
+ * of the solution of M x = (z, 0); S = |z|^2.  Asynchronous. */
+qcd_status qcd_force_eo(const qcd_gauge* g, const qcd_fermion* fermion, const void* X,
+                        const void* Y, void* dSdU, void* stream);
+
+/* Project a link derivative onto su(3): F_mu(x) = P_TA(U_mu(x) G_mu(x)^dag) with
+ * G = dS/dRe U + i dS/dIm U (dSdU as written by qcd_force / qcd_force_eo) and
+ * P_TA(M) = (M - M^dag)/2 - tr(M - M^dag)/6, using the handle's links.  For a
+ * traceless Hermitian T, the derivative of S along U_mu(x) -> exp(i eps T) U_mu(x)
+ * is tr(i T F_mu(x)).  F: canonical (4, V, 3, 3) complex128, device.
+ * Asynchronous. */
+qcd_status qcd_force_project(const qcd_gauge* g, const void* dSdU, void* F, void* stream);
+
+/* Molecular-dynamics updates on canonical arrays of nlinks 3x3 complex128
+ * matrices (device; e.g. (4, V, 3, 3) gauge links and su(3) momenta):
+ *   qcd_link_update: U <- exp(eps P) U for every link (P traceless
+ *     anti-Hermitian; exp by scaling and squaring of a degree-13 Taylor
+ *     polynomial, accurate to rounding);
+ *   qcd_mom_update:  P <- P + c F;
+ *   qcd_mom_energy:  *out = sum over all entries of |P_ab|^2 (= sum tr(P^dag P)),
+ *     summed in FP64 in a fixed order; synchronises the stream.  Its partial
+ *     sums live in one fixed device array per GPU: calls whose GPU work
+ *     overlaps must be ordered by the caller.
+ * A gauge handle holds copies of the links: load a new one after updating U.
+ * QCD_ERR_ARG for NULL pointers, host pointers or nlinks < 0. */
+qcd_status qcd_link_update(void* U, const void* P, double eps, int64_t nlinks, void* stream);
+qcd_status qcd_mom_update(void* P, const void* F, double c, int64_t nlinks, void* stream);
+qcd_status qcd_mom_energy(const void* P, int64_t nlinks, double* out, void* stream);
+
 /* Squared norm |psi|^2 (sum over sites, spins, colours of |component|^2) of
  * each of the nrhs right-hand sides of a canonical complex128 field
  * (nrhs, [Ls,] V, 4, 3), summed in FP64; e.g. the action S = |eta|^2 with

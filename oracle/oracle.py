@@ -209,3 +209,87 @@ def wilson_action(L, bc, kappa, U, phi, tol=1e-13):
     eta, _, _ = wilson_solve(L, bc, kappa, U, phi, tol=tol, dagger=True)
     X, _, _ = wilson_solve(L, bc, kappa, U, eta, tol=tol, dagger=False)
     return float(np.vdot(eta, eta).real), eta, X
+
+
+# ----------------------------------------------------------------------------- molecular dynamics
+# Ensemble generation needs the solver many times (Sec. II A).  The pieces below
+# are the molecular-dynamics ingredients for the even-odd pseudofermion action,
+# written from their definitions: S_eo = phi_e^dag (Mhat^dag Mhat)^-1 phi_e with
+# Mhat = 1 - kappa^2 H_eo H_oe, momenta P in su(3), U(t) = exp(t P) U.
+
+def wilson_eo_action(L, bc, kappa, U, phi_e, tol=1e-13):
+    """S_eo = phi_e^dag (Mhat^dag Mhat)^-1 phi_e for the even sites of phi_e (odd sites ignored).
+
+    Uses the Schur complement of M = 1 - kappa H on the even sites: for b = (b_e, 0), the even
+    part of M^-1 b is Mhat^-1 b_e (and of M^-dag b, Mhat^-dag b_e).  Returns (S, X, Y) with
+    z = Mhat^-dag phi_e, X = Mhat^-1 z = (Mhat^dag Mhat)^-1 phi_e, Y = Mhat X = z, as canonical
+    fields that vanish on the odd sites.
+    """
+    par = parity(L)
+    b = _c(phi_e).copy()
+    b[par == 1] = 0
+    w, _, _ = wilson_solve(L, bc, kappa, U, b, tol=tol, dagger=True)
+    z = w.copy()
+    z[par == 1] = 0
+    v, _, _ = wilson_solve(L, bc, kappa, U, z, tol=tol, dagger=False)
+    X = v.copy()
+    X[par == 1] = 0
+    return float(np.vdot(z, z).real), X, z
+
+
+def wilson_eo_force(L, bc, kappa, U, X, Y):
+    """dS_eo/dU (4, V, 3, 3, 2) for X = (Mhat^dag Mhat)^-1 phi_e, Y = Mhat X.
+
+    dS_eo = -2 Re(Y^dag dMhat X) with dMhat = -kappa^2 (dH_eo H_oe + H_eo dH_oe), i.e.
+    2 kappa^2 Re(eta^dag dH xi) with xi = (X_e, H_oe X_e) and eta = (Y_e, (H^dag)_oe Y_e);
+    ``wilson_force`` gives 2 kappa Re(eta^dag dH xi).
+    """
+    par = parity(L)
+    Xe, Ye = _c(X).copy(), _c(Y).copy()
+    Xe[par == 1] = 0
+    Ye[par == 1] = 0
+    xi = Xe + hop(L, bc, U, Xe, out_parity=1)
+    eta = Ye + hop(L, bc, U, Ye, dagger=True, out_parity=1)
+    return kappa * wilson_force(L, bc, kappa, xi, eta)
+
+
+def su3_project(U, dSdU):
+    """F = P_TA(U G^dag), G = dS/dRe U + i dS/dIm U; P_TA(M) = (M - M^dag)/2 - tr(M - M^dag)/6."""
+    U = _c(U)
+    G = dSdU[..., 0] + 1j * dSdU[..., 1]
+    M = U @ np.conj(np.swapaxes(G, -1, -2))
+    A = 0.5 * (M - np.conj(np.swapaxes(M, -1, -2)))
+    tr = np.trace(A, axis1=-2, axis2=-1) / 3.0
+    return A - tr[..., None, None] * np.eye(3)
+
+
+def link_update(U, P, eps):
+    """U <- exp(eps P) U for every link (matrix exponential by scipy)."""
+    from scipy.linalg import expm
+
+    return expm(eps * _c(P)) @ _c(U)
+
+
+def kinetic(P):
+    """sum over links of tr(P^dag P) = sum |P_ab|^2."""
+    return float(np.sum(np.abs(P) ** 2))
+
+
+def leapfrog(L, bc, kappa, U, P, phi_e, eps, nsteps, tol=1e-13):
+    """Leapfrog for H = K/2 + S_eo with K = sum tr(P^dag P) and dU/dt = P U, so that dH/dt = 0
+    needs dP/dt = F = P_TA(U G^dag) (the derivative of S along P U is Re tr(P F)).
+    Returns (U, P, H_start, H_end)."""
+    def force(U):
+        _, X, Y = wilson_eo_action(L, bc, kappa, U, phi_e, tol=tol)
+        return su3_project(U, wilson_eo_force(L, bc, kappa, U, X, Y))
+
+    def ham(U, P):
+        return 0.5 * kinetic(P) + wilson_eo_action(L, bc, kappa, U, phi_e, tol=tol)[0]
+
+    U, P = _c(U).copy(), _c(P).copy()
+    h0 = ham(U, P)
+    P = P + 0.5 * eps * force(U)
+    for k in range(nsteps):
+        U = link_update(U, P, eps)
+        P = P + (eps if k < nsteps - 1 else 0.5 * eps) * force(U)
+    return U, P, h0, ham(U, P)

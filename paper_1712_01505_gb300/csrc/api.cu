@@ -15,6 +15,12 @@ namespace qcd {
 
 void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& prm, const double* b,
                   double* x, int nrhs, qcd_solve_info* info, cudaStream_t st);
+void force_eo_device(qcd_gauge* g, const qcd_fermion& f, const double* X, const double* Y, double* dSdU,
+                     cudaStream_t st);
+void force_project_device(const qcd_gauge* g, const double* dSdU, double* F, cudaStream_t st);
+void link_update_device(double* U, const double* P, double eps, long nlinks, cudaStream_t st);
+void mom_update_device(double* P, const double* F, double c, long nlinks, cudaStream_t st);
+double mom_energy_device(const double* P, long nlinks, cudaStream_t st);
 void force_device(const qcd_gauge* g, const qcd_fermion& f, const double* X, const double* eta,
                   double* dSdU, cudaStream_t st);
 void mhat_noalloc(const qcd_gauge* g, const qcd_fermion& f, int prec, int dagger, const void* in,
@@ -494,6 +500,59 @@ qcd_status qcd_force(const qcd_gauge* gc, const qcd_fermion* fermion, const void
     if (!is_device_ptr(X) || !is_device_ptr(eta) || !is_device_ptr(dSdU))
       raise(QCD_ERR_ARG, "qcd_force takes device buffers");
     force_device(gc, *fermion, (const double*)X, (const double*)eta, (double*)dSdU, (cudaStream_t)stream);
+  });
+}
+
+qcd_status qcd_force_eo(const qcd_gauge* gc, const qcd_fermion* fermion, const void* X, const void* Y,
+                        void* dSdU, void* stream) {
+  return guarded([&] {
+    check_gauge(gc);
+    check_fermion(fermion);
+    if (fermion->type != QCD_WILSON) raise(QCD_ERR_UNSUPPORTED, "the force is implemented for Wilson fermions");
+    if (!X || !Y || !dSdU) raise(QCD_ERR_ARG, "NULL argument");
+    if (!is_device_ptr(X) || !is_device_ptr(Y) || !is_device_ptr(dSdU))
+      raise(QCD_ERR_ARG, "qcd_force_eo takes device buffers");
+    force_eo_device(const_cast<qcd_gauge*>(gc), *fermion, (const double*)X, (const double*)Y, (double*)dSdU,
+                    (cudaStream_t)stream);
+  });
+}
+
+qcd_status qcd_force_project(const qcd_gauge* gc, const void* dSdU, void* F, void* stream) {
+  return guarded([&] {
+    check_gauge(gc);
+    if (!dSdU || !F) raise(QCD_ERR_ARG, "NULL argument");
+    if (dSdU == F) raise(QCD_ERR_ARG, "dSdU and F must not overlap");
+    if (!is_device_ptr(dSdU) || !is_device_ptr(F)) raise(QCD_ERR_ARG, "qcd_force_project takes device buffers");
+    force_project_device(gc, (const double*)dSdU, (double*)F, (cudaStream_t)stream);
+  });
+}
+
+qcd_status qcd_link_update(void* U, const void* P, double eps, int64_t nlinks, void* stream) {
+  return guarded([&] {
+    if (!U || !P) raise(QCD_ERR_ARG, "NULL argument");
+    if (nlinks < 0) raise(QCD_ERR_ARG, "nlinks must be >= 0");
+    if (U == P) raise(QCD_ERR_ARG, "U and P must not overlap");
+    if (!std::isfinite(eps)) raise(QCD_ERR_ARG, "eps must be finite");
+    if (!is_device_ptr(U) || !is_device_ptr(P)) raise(QCD_ERR_ARG, "qcd_link_update takes device buffers");
+    link_update_device((double*)U, (const double*)P, eps, (long)nlinks, (cudaStream_t)stream);
+  });
+}
+
+qcd_status qcd_mom_update(void* P, const void* F, double c, int64_t nlinks, void* stream) {
+  return guarded([&] {
+    if (!P || !F) raise(QCD_ERR_ARG, "NULL argument");
+    if (nlinks < 0) raise(QCD_ERR_ARG, "nlinks must be >= 0");
+    if (!is_device_ptr(P) || !is_device_ptr(F)) raise(QCD_ERR_ARG, "qcd_mom_update takes device buffers");
+    mom_update_device((double*)P, (const double*)F, c, (long)nlinks, (cudaStream_t)stream);
+  });
+}
+
+qcd_status qcd_mom_energy(const void* P, int64_t nlinks, double* out, void* stream) {
+  return guarded([&] {
+    if (!P || !out) raise(QCD_ERR_ARG, "NULL argument");
+    if (nlinks < 0) raise(QCD_ERR_ARG, "nlinks must be >= 0");
+    if (!is_device_ptr(P)) raise(QCD_ERR_ARG, "qcd_mom_energy takes a device buffer");
+    *out = mom_energy_device((const double*)P, (long)nlinks, (cudaStream_t)stream);
   });
 }
 

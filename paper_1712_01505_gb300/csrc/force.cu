@@ -84,10 +84,58 @@ __global__ void k_force(Geom g, const double2* __restrict__ X, const double2* __
   }
 }
 
-}  // namespace
+// F_mu(x) = P_TA(U_mu(x) G_mu(x)^dag), G = dS/dRe U + i dS/dIm U, P_TA(M) = (M - M^dag)/2
+// minus its trace / 3: the su(3) element whose pairing tr(i T F) with a generator T is the
+// derivative of S along U -> exp(i eps T) U.  One thread per link; the links are read from
+// the handle's even-odd FP64 copy.
+__global__ void k_force_project(Geom g, const double2* __restrict__ U64, const double* __restrict__ dSdU,
+                                double2* __restrict__ F) {
+  long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= 4L * g.V) return;
+  const int mu = (int)(idx / g.V);
+  const long i = idx - (long)mu * g.V;
+  long r = i;
+  int par = 0;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    par += (int)(r % g.L[m]);
+    r /= g.L[m];
+  }
+  par &= 1;
+  const long cb = i >> 1;
+  Cx<double> u[9], gg[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const double2 v = U64[((long)(par * 4 + mu) * 9 + k) * g.Vh + cb];
+    u[k] = {v.x, v.y};
+    const double* d = dSdU + (idx * 9 + k) * 2;
+    gg[k] = {d[0], d[1]};
+  }
+  Cx<double> m[9];  // M = U G^dag: M_ac = sum_b U_ab conj(G_cb)
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Cx<double> acc = {0.0, 0.0};
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc = cmadd(u[a * 3 + b], conjg(gg[c * 3 + b]), acc);
+      m[a * 3 + c] = acc;
+    }
+  const double tr = (m[0].im + m[4].im + m[8].im) / 3.0;  // Im tr(M) / 3; (M - M^dag)/2 has trace i Im tr M
+  double2* o = F + idx * 9;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const Cx<double> x = m[a * 3 + c], y = m[c * 3 + a];
+      // ((M - M^dag)/2)_ac = (M_ac - conj(M_ca)) / 2
+      double re = 0.5 * (x.re - y.re), im = 0.5 * (x.im + y.im);
+      if (a == c) im -= tr;
+      o[a * 3 + c] = make_double2(re, im);
+    }
+}
 
-void force_device(const qcd_gauge* gh, const qcd_fermion& f, const double* X, const double* eta,
-                  double* dSdU, cudaStream_t st) {
+Geom force_geom(const qcd_gauge* gh) {
   Geom g;
   for (int m = 0; m < 4; ++m) {
     g.L[m] = gh->lat.L[m];
@@ -95,9 +143,52 @@ void force_device(const qcd_gauge* gh, const qcd_fermion& f, const double* X, co
   }
   g.V = (int)gh->lat.V;
   g.Vh = (int)gh->lat.Vh;
-  long n = 4L * g.V;
-  k_force<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, (const double2*)X, (const double2*)eta, dSdU,
-                                                      2.0 * f.kappa);
+  return g;
+}
+
+void launch_force(const qcd_gauge* gh, const double* X, const double* eta, double* dSdU, double scale,
+                  cudaStream_t st) {
+  const Geom g = force_geom(gh);
+  const long n = 4L * g.V;
+  k_force<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, (const double2*)X, (const double2*)eta, dSdU, scale);
+  QCD_LAUNCH_CK();
+}
+
+}  // namespace
+
+void force_device(const qcd_gauge* gh, const qcd_fermion& f, const double* X, const double* eta,
+                  double* dSdU, cudaStream_t st) {
+  launch_force(gh, X, eta, dSdU, 2.0 * f.kappa, st);
+}
+
+// Even-odd pseudofermion action S = phi_e^dag (Mhat^dag Mhat)^-1 phi_e with Mhat = 1 - kappa^2
+// H_eo H_oe: for X = (Mhat^dag Mhat)^-1 phi_e and Y = Mhat X,
+//   dS = -2 Re(Y^dag dMhat X) = 2 kappa^2 Re(Y^dag dH_eo H_oe X + ((H^dag)_oe Y)^dag dH_oe X),
+// i.e. 2 kappa^2 Re(eta^dag dH xi) with the full fields xi = (X, H_oe X) and
+// eta = (Y, (H^dag)_oe Y): the kernel of the full action with 2 kappa^2 for 2 kappa.
+void force_eo_device(qcd_gauge* g, const qcd_fermion& f, const double* X, const double* Y, double* dSdU,
+                     cudaStream_t st) {
+  const Lattice& lat = g->lat;
+  Field xe = ws_field(g, "f.xe", QCD_F64, 1, 1), xo = ws_field(g, "f.xo", QCD_F64, 1, 1);
+  Field ye = ws_field(g, "f.ye", QCD_F64, 1, 1), yo = ws_field(g, "f.yo", QCD_F64, 1, 1);
+  pack_field(lat, 0, X, xe, st);
+  pack_field(lat, 0, Y, ye, st);
+  hop(g, xe, xo, 1, 0, 1.0, nullptr, st);
+  hop(g, ye, yo, 1, 1, 1.0, nullptr, st);
+  const size_t bytes = (size_t)lat.V * 12 * 2 * sizeof(double);
+  double* xi = (double*)g->ws.get("f.xi", bytes);
+  double* eta = (double*)g->ws.get("f.eta", bytes);
+  unpack_field(lat, 0, xe, xi, st);
+  unpack_field(lat, 1, xo, xi, st);
+  unpack_field(lat, 0, ye, eta, st);
+  unpack_field(lat, 1, yo, eta, st);
+  launch_force(g, xi, eta, dSdU, 2.0 * f.kappa * f.kappa, st);
+}
+
+void force_project_device(const qcd_gauge* gh, const double* dSdU, double* F, cudaStream_t st) {
+  const Geom g = force_geom(gh);
+  const long n = 4L * g.V;
+  k_force_project<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, (const double2*)gh->U64, dSdU, (double2*)F);
   QCD_LAUNCH_CK();
 }
 

@@ -117,3 +117,13 @@ def point_sources(L, seed: int):
     for k in range(12):
         b[k, x0, k // 3, k % 3] = 1.0
     return x0, b
+
+
+def su3_momenta(shape, seed: int) -> np.ndarray:
+    """Random su(3) elements (traceless anti-Hermitian 3x3), shape + (3, 3): i times the traceless
+    part of the Hermitian part of a complex Gaussian matrix."""
+    g = _rng(seed).standard_normal(tuple(shape) + (3, 3, 2))
+    a = g[..., 0] + 1j * g[..., 1]
+    h = 0.5 * (a + np.conj(np.swapaxes(a, -1, -2)))
+    tr = np.trace(h, axis1=-2, axis2=-1) / 3.0
+    return 1j * (h - tr[..., None, None] * np.eye(3))

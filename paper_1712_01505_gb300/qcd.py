@@ -42,7 +42,8 @@ BICGSTAB, CG_NORMAL = 0, 1
 # every symbol the header declares
 SYMBOLS = ["qcd_gauge_load", "qcd_gauge_free", "qcd_field_bytes", "qcd_field_pack", "qcd_field_unpack",
            "qcd_dslash", "qcd_solve", "qcd_force", "qcd_last_error", "qcd_set_tuning", "qcd_kernel_launches",
-           "qcd_mhat_noalloc", "qcd_norm2"]
+           "qcd_mhat_noalloc", "qcd_norm2", "qcd_force_eo", "qcd_force_project", "qcd_link_update",
+           "qcd_mom_update", "qcd_mom_energy"]
 
 
 class QCDError(RuntimeError):
@@ -107,9 +108,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qcd_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     lib.qcd_mhat_noalloc.argtypes = [vp, ctypes.POINTER(Fermion), i32, i32, vp, vp, i32, vp]
     lib.qcd_norm2.argtypes = [vp, ctypes.POINTER(Fermion), vp, i32, ctypes.POINTER(ctypes.c_double), vp]
+    lib.qcd_force_eo.argtypes = [vp, ctypes.POINTER(Fermion), vp, vp, vp, vp]
+    lib.qcd_force_project.argtypes = [vp, vp, vp, vp]
+    lib.qcd_link_update.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int64, vp]
+    lib.qcd_mom_update.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int64, vp]
+    lib.qcd_mom_energy.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp]
     for name in ("qcd_gauge_load", "qcd_gauge_free", "qcd_field_pack", "qcd_field_unpack", "qcd_dslash",
                  "qcd_solve", "qcd_force", "qcd_set_tuning", "qcd_kernel_launches", "qcd_mhat_noalloc",
-                 "qcd_norm2"):
+                 "qcd_norm2", "qcd_force_eo", "qcd_force_project", "qcd_link_update", "qcd_mom_update",
+                 "qcd_mom_energy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -263,3 +270,36 @@ def force(gauge, fermion, X, eta, out, stream=None):
     _check(load_library().qcd_force(gauge.handle, ctypes.byref(fermion), _ptr(X), _ptr(eta), _ptr(out),
                                     _stream(stream)))
     return out
+
+
+def force_eo(gauge, fermion, X, Y, out, stream=None):
+    """qcd_force_eo: dS/dU for S = phi_e^dag (Mhat^dag Mhat)^-1 phi_e given X = (Mhat^dag Mhat)^-1 phi_e and
+    Y = Mhat X (canonical full-lattice fields, odd sites ignored)."""
+    _check(load_library().qcd_force_eo(gauge.handle, ctypes.byref(fermion), _ptr(X), _ptr(Y), _ptr(out),
+                                       _stream(stream)))
+    return out
+
+
+def force_project(gauge, dSdU, out, stream=None):
+    """qcd_force_project: F = P_TA(U G^dag), G = dS/dRe U + i dS/dIm U, as (4, V, 3, 3) complex128."""
+    _check(load_library().qcd_force_project(gauge.handle, _ptr(dSdU), _ptr(out), _stream(stream)))
+    return out
+
+
+def link_update(U, P, eps, stream=None):
+    """qcd_link_update: U <- exp(eps P) U for every 3x3 matrix of U (device complex128 arrays)."""
+    _check(load_library().qcd_link_update(_ptr(U), _ptr(P), float(eps), U.numel() // 9, _stream(stream)))
+    return U
+
+
+def mom_update(P, F, c, stream=None):
+    """qcd_mom_update: P <- P + c F."""
+    _check(load_library().qcd_mom_update(_ptr(P), _ptr(F), float(c), P.numel() // 9, _stream(stream)))
+    return P
+
+
+def mom_energy(P, stream=None) -> float:
+    """qcd_mom_energy: sum over all entries of |P_ab|^2."""
+    out = ctypes.c_double()
+    _check(load_library().qcd_mom_energy(_ptr(P), P.numel() // 9, ctypes.byref(out), _stream(stream)))
+    return out.value
