@@ -192,9 +192,36 @@ def run_force(args):
         torch.cuda.profiler.stop()
         print("profile force done", flush=True)
         return
+    # molecular dynamics of the even-odd action: one force evaluation (two mixed solves to 1e-10,
+    # qcd_force_eo, qcd_force_project) and one leapfrog step (force + link and momentum updates)
+    from paper_1712_01505_gb300 import hmc
+
+    md = hmc.EOPseudofermionMD(L, kappa, pt, tol=1e-10)
+    P = torch.from_numpy(inputs.su3_momenta((4, V), 2)).to(dev)
+    Fm, _ = md.force(Ut)  # warm-up (tuning, workspace, graphs)
+    t_force = []
+    for rep in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        md.force(Ut, Fm)
+        torch.cuda.synchronize()
+        t_force.append(time.perf_counter() - t0)
+    Uc, Pc = Ut.clone(), P.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h0, h1 = md.leapfrog(Uc, Pc, 0.02, 1)
+    torch.cuda.synchronize()
+    t_step = time.perf_counter() - t0
+    ms_eo = _time_launches(lambda: qcd.force_eo(g, f, X, pt, out_t))
+    ms_proj = _time_launches(lambda: qcd.force_project(g, out_t, Fm))
+    ms_link = _time_launches(lambda: qcd.link_update(Uc, Pc, 0.02))
     out = {"workload": "force_wilson_16x16x16x16_kappa0.12", "backward_ms": round(min(times[1:]) * 1e3, 3),
            "force_kernel_ms": round(ms, 4),
-           "force_kernel_gbs": round(V * (2 * 192 + 4 * 144) / ms / 1e6, 1)}
+           "force_kernel_gbs": round(V * (2 * 192 + 4 * 144) / ms / 1e6, 1),
+           "md": {"force_eval_ms": round(min(t_force) * 1e3, 3),
+                  "leapfrog_step_ms": round(t_step * 1e3, 3),
+                  "force_eo_ms": round(ms_eo, 4), "force_project_ms": round(ms_proj, 4),
+                  "link_update_ms": round(ms_link, 4), "dH_one_step_0.02": h1 - h0}}
     print(json.dumps(out), flush=True)
 
 

@@ -119,3 +119,25 @@ def test_leapfrog_reversible_and_matches_the_oracle():
     md.leapfrog(Ud, Pd, 0.05, 4)
     assert max_err(Ud, U) < 1e-9
     assert max_err(-Pd, P) < 1e-8
+
+
+def test_eo_autograd_matches_the_oracle():
+    """torch.autograd through the even-odd action: dS/dU is the oracle's even-odd force, dS/dphi is
+    2 X on the even sites and 0 on the odd ones."""
+    device()
+    from paper_1712_01505_gb300.autograd import wilson_eo_action
+
+    L, kappa = (6, 4, 4, 8), 0.12
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.3, 34)
+    phi = inputs.gaussian_source((V, 4, 3), 35)
+    Ut = to_dev(U).requires_grad_(True)
+    pt = to_dev(phi).requires_grad_(True)
+    S = wilson_eo_action(Ut, pt, kappa, L, BC, tol=1e-12)
+    S.backward()
+    s_ref, X, Y = ora.wilson_eo_action(L, BC, kappa, U, phi)
+    assert abs(S.item() - s_ref) <= 1e-10 * s_ref
+    g_ref = ora.wilson_eo_force(L, BC, kappa, U, X, Y)
+    assert max_err(torch.view_as_real(Ut.grad), g_ref) < 1e-9
+    assert max_err(pt.grad, 2 * X) < 1e-9
+    assert not pt.grad.cpu().numpy()[ora.parity(L) == 1].any()
