@@ -82,6 +82,29 @@ __device__ __forceinline__ Cx<R> conjg(Cx<R> a) {
   return {a.re, -a.im};
 }
 
+// ----------------------------------------------------------------------------- division
+// n / d for 0 <= n < 2^31 by a multiply-high and a shift (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, Thm 4.2 with
+// N = 31): l = ceil(log2 d), m = ceil(2^(31+l) / d) < 2^32, n / d = (n m) >> (31 + l).
+// d = 1 is flagged by s = -1.  Replaces the ~20-instruction runtime division in
+// the index arithmetic of the stencils.
+struct FastDiv {
+  unsigned m;
+  int s;  // l - 1
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+  if (d <= 1) return {0u, -1};
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  const unsigned long long m = ((1ull << (31 + l)) + d - 1) / d;
+  return {(unsigned)m, l - 1};
+}
+
+__device__ __forceinline__ int fdiv(int n, FastDiv f) {
+  return f.s < 0 ? n : (int)(__umulhi((unsigned)n, f.m) >> f.s);
+}
+
 // ----------------------------------------------------------------------------- geometry
 // Lattice extents, boundary factors and the even-odd map.  Canonical site
 // index i = x + Lx*(y + Ly*(z + Lz*t)); parity (x+y+z+t) & 1; within a parity
@@ -90,7 +113,20 @@ struct Geom {
   int L[4];
   int apbc[4];  // 1 where the boundary factor is -1
   int V, Vh;
+  FastDiv dL[3];  // division by L[0], L[1], L[2]
 };
+
+inline Geom make_geom(const int L[4], const int bc[4], long V, long Vh) {
+  Geom g;
+  for (int m = 0; m < 4; ++m) {
+    g.L[m] = L[m];
+    g.apbc[m] = bc[m] < 0;
+  }
+  g.V = (int)V;
+  g.Vh = (int)Vh;
+  for (int m = 0; m < 3; ++m) g.dL[m] = make_fastdiv((unsigned)L[m]);
+  return g;
+}
 
 struct SiteCoords {
   int x[4];
@@ -100,12 +136,12 @@ struct SiteCoords {
 __device__ __forceinline__ SiteCoords cb_to_site(const Geom& g, int cb, int parity) {
   SiteCoords c;
   int i2 = 2 * cb;
-  int x0 = i2 % g.L[0];
-  int r = i2 / g.L[0];
-  c.x[1] = r % g.L[1];
-  r /= g.L[1];
-  c.x[2] = r % g.L[2];
-  c.x[3] = r / g.L[2];
+  int r = fdiv(i2, g.dL[0]);
+  int x0 = i2 - r * g.L[0];
+  int r2 = fdiv(r, g.dL[1]);
+  c.x[1] = r - r2 * g.L[1];
+  c.x[3] = fdiv(r2, g.dL[2]);
+  c.x[2] = r2 - c.x[3] * g.L[2];
   c.x[0] = x0 + ((parity + c.x[1] + c.x[2] + c.x[3]) & 1);
   c.i = c.x[0] + g.L[0] * (c.x[1] + g.L[1] * (c.x[2] + g.L[2] * c.x[3]));
   return c;

@@ -135,16 +135,7 @@ __global__ void k_force_project(Geom g, const double2* __restrict__ U64, const d
     }
 }
 
-Geom force_geom(const qcd_gauge* gh) {
-  Geom g;
-  for (int m = 0; m < 4; ++m) {
-    g.L[m] = gh->lat.L[m];
-    g.apbc[m] = gh->lat.bc[m] < 0;
-  }
-  g.V = (int)gh->lat.V;
-  g.Vh = (int)gh->lat.Vh;
-  return g;
-}
+Geom force_geom(const qcd_gauge* gh) { return make_geom(gh->lat.L, gh->lat.bc, gh->lat.V, gh->lat.Vh); }
 
 void launch_force(const qcd_gauge* gh, const double* X, const double* eta, double* dSdU, double scale,
                   cudaStream_t st) {

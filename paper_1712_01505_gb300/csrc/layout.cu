@@ -21,16 +21,7 @@ __device__ __forceinline__ void site_of(const Geom& g, long i, int* parity, long
   *cb = i >> 1;
 }
 
-Geom dev_geom(const Lattice& lat) {
-  Geom g;
-  for (int m = 0; m < 4; ++m) {
-    g.L[m] = lat.L[m];
-    g.apbc[m] = lat.bc[m] < 0;
-  }
-  g.V = (int)lat.V;
-  g.Vh = (int)lat.Vh;
-  return g;
-}
+Geom dev_geom(const Lattice& lat) { return make_geom(lat.L, lat.bc, lat.V, lat.Vh); }
 
 // one thread per (mu, site)
 __global__ void k_gauge_reorder(Geom g, const double2* __restrict__ U, double2* U64, void* U32,

@@ -87,6 +87,7 @@ struct HopArgs {
   int ls;        // slices per right-hand side
   int nslices;   // ls * nrhs
   int ntiles;    // ceil(nslices / TILE)
+  FastDiv d_ls, d_ntiles;  // division by ls and by ntiles
   int dagger;
   int xpay;
   double a;
@@ -122,7 +123,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCo
     for (int t = 0; t < TILE; ++t) {
       int q = q0 + t;
       if (TILE > 1 && q >= A.nslices) break;
-      int r = q / A.ls, s = q - r * A.ls;
+      int r = fdiv(q, A.d_ls), s = q - r * A.ls;
       Cx<R> psi[12], h[6], gg[6];
       A.in.offset_rhs(r).load((long)s * g.Vh + ncb, psi);
       project<MU>(psi, sg, h);
@@ -149,7 +150,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCo
     for (int t = 0; t < TILE; ++t) {
       int q = q0 + t;
       if (TILE > 1 && q >= A.nslices) break;
-      int r = q / A.ls, s = q - r * A.ls;
+      int r = fdiv(q, A.d_ls), s = q - r * A.ls;
       Cx<R> psi[12], h[6], gg[6];
       A.in.offset_rhs(r).load((long)s * g.Vh + ncb, psi);
       project<MU>(psi, -sg, h);
@@ -221,8 +222,8 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
   if (A.stop && *A.stop) return;
   // block -> (site block, slice tile), tiles of one site block adjacent in
   // launch order so that they read the same links at about the same time
-  int tile = blockIdx.x % A.ntiles;
-  int sblock = blockIdx.x / A.ntiles;
+  int sblock = fdiv(blockIdx.x, A.d_ntiles);
+  int tile = blockIdx.x - sblock * A.ntiles;
   int cb = sblock * blockDim.x + threadIdx.x;
   if (cb >= A.g.Vh) return;
   int q0 = tile * TILE;
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
   for (int t = 0; t < TILE; ++t) {
     int q = q0 + t;
     if (TILE > 1 && q >= A.nslices) break;
-    int r = q / A.ls, s = q - r * A.ls;
+    int r = fdiv(q, A.d_ls), s = q - r * A.ls;
     long site = (long)s * A.g.Vh + cb;
     Cx<R> o[12];
     if (A.xpay) {
@@ -366,10 +367,14 @@ __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
 // owns one site and TS slices, reads each link once from shared memory and
 // applies it to its TS slices.  Link traffic per block is 8 x 32 links
 // whatever the number of slices, and the per-site index arithmetic is done once.
+// The links are stored as pairs of complex numbers so that a thread reads a
+// link with five 16-byte shared-memory loads: element k is half (k & 1) of pair
+// k >> 1; pair 4 holds element 8 and padding.
 template <typename R>
 struct SmLinks {
-  Cx<R> U[8][9][32];      // [2 mu + backward][element][site]
-  int nb[8][32];          // neighbour checkerboard index
+  static_assert(sizeof(R) == 4, "shared-memory links are FP32");
+  float4 U[8][5][32];        // [2 mu + backward][element pair][site]
+  int nb[8][32];             // neighbour checkerboard index
   unsigned char neg[8][32];  // 1 if the hop carries the antiperiodic sign
 };
 
@@ -385,7 +390,11 @@ __device__ __forceinline__ void hop_link_sm(const HopArgs<P, RECON>& A, const Sm
   const bool neg = sm.neg[L][tx];
   Cx<R> U[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) U[k] = sm.U[L][k][tx];
+  for (int k = 0; k < 5; ++k) {
+    const float4 v = sm.U[L][k][tx];
+    U[2 * k] = {v.x, v.y};
+    if (k < 4) U[2 * k + 1] = {v.z, v.w};
+  }
   const R sgn = BACK ? -sg : sg;
 #pragma unroll
   for (int t = 0; t < TS; ++t) {
@@ -407,8 +416,8 @@ __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
   if (A.stop && *A.stop) return;
   __shared__ SmLinks<R> sm;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int stile = blockIdx.x % A.ntiles;
-  const int sblock = blockIdx.x / A.ntiles;
+  const int sblock = fdiv(blockIdx.x, A.d_ntiles);
+  const int stile = blockIdx.x - sblock * A.ntiles;
   const int cb = sblock * 32 + tx;
   const bool valid = cb < A.g.Vh;
   if (valid) {
@@ -427,7 +436,9 @@ __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
       else
         A.U.load(1 - A.out_parity, mu, j >> 1, U);  // U_mu(x - mu)
 #pragma unroll
-      for (int k = 0; k < 9; ++k) sm.U[l][k][tx] = U[k];
+      for (int k = 0; k < 5; ++k)
+        sm.U[l][k][tx] = make_float4(U[2 * k].re, U[2 * k].im, k < 4 ? U[2 * k + 1].re : 0.f,
+                                     k < 4 ? U[2 * k + 1].im : 0.f);
     }
   }
   __syncthreads();
@@ -439,7 +450,7 @@ __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
 #pragma unroll
   for (int t = 0; t < TS; ++t) {
     const int q = min(q0 + t, A.nslices - 1);
-    const int r = q / A.ls, s = q - r * A.ls;
+    const int r = fdiv(q, A.d_ls), s = q - r * A.ls;
     in[t] = A.in.offset_rhs(r);
     soff[t] = (long)s * A.g.Vh;
   }
@@ -462,7 +473,7 @@ __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
   for (int t = 0; t < TS; ++t) {
     if (TS > 1 && t >= nt) break;
     const int q = q0 + t;
-    const int r = q / A.ls;
+    const int r = fdiv(q, A.d_ls);
     const long site = soff[t] + cb;
     Cx<R> o[12];
     if (A.xpay) {
@@ -477,16 +488,7 @@ __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
   }
 }
 
-Geom dev_geom(const Lattice& lat) {
-  Geom g;
-  for (int m = 0; m < 4; ++m) {
-    g.L[m] = lat.L[m];
-    g.apbc[m] = lat.bc[m] < 0;
-  }
-  g.V = (int)lat.V;
-  g.Vh = (int)lat.Vh;
-  return g;
-}
+Geom dev_geom(const Lattice& lat) { return make_geom(lat.L, lat.bc, lat.V, lat.Vh); }
 
 template <int P>
 SpinorView<P> sview(const Field& f) {
@@ -508,6 +510,7 @@ template <int P, int RECON, int TILE, int PF = 0>
 void launch_tile(HopLaunch<P, RECON>* L, int block) {
   HopArgs<P, RECON> A = L->args;
   A.ntiles = (A.nslices + TILE - 1) / TILE;
+  A.d_ntiles = make_fastdiv((unsigned)A.ntiles);
   long sblocks = (A.g.Vh + block - 1) / block;
   if constexpr (TILE == 1 && P != P16) {
     if (A.red == 1) {
@@ -526,6 +529,7 @@ template <int P, int RECON, int BY, int TS>
 void launch_sm(HopLaunch<P, RECON>* L) {
   HopArgs<P, RECON> A = L->args;
   A.ntiles = (A.nslices + BY * TS - 1) / (BY * TS);
+  A.d_ntiles = make_fastdiv((unsigned)A.ntiles);
   long sblocks = (A.g.Vh + 31) / 32;
   k_hop_sm<P, RECON, BY, TS><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
 }
@@ -578,6 +582,7 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   A.g = dev_geom(gh->lat);
   A.out_parity = out_parity;
   A.ls = in.ls;
+  A.d_ls = make_fastdiv((unsigned)in.ls);
   A.nslices = in.ls * in.nrhs;
   A.dagger = dagger;
   A.xpay = x != nullptr;

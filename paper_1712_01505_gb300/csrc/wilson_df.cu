@@ -30,6 +30,7 @@ struct HopDfArgs {
   Geom g;
   int out_parity;
   int ls;
+  FastDiv d_ls;
   int x1, x2;  // epilogue terms present
   F2 a, c2;
   LinkViewDF U;
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(128, 3) k_hop_df(HopDfArgs A) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   if (cb >= A.g.Vh) return;
   const int q = blockIdx.y;
-  const int r = q / A.ls, s = q - r * A.ls;
+  const int r = fdiv(q, A.d_ls), s = q - r * A.ls;
   const long soff = (long)s * A.g.Vh;
   const SpinorView<PDF> in = A.in.offset_rhs(r);
   const SiteCoords c = cb_to_site(A.g, cb, A.out_parity);
@@ -224,16 +225,7 @@ __global__ void __launch_bounds__(128, 3) k_hop_df(HopDfArgs A) {
   A.out.offset_rhs(r).store_df(site, o);
 }
 
-Geom df_geom(const Lattice& lat) {
-  Geom g;
-  for (int m = 0; m < 4; ++m) {
-    g.L[m] = lat.L[m];
-    g.apbc[m] = lat.bc[m] < 0;
-  }
-  g.V = (int)lat.V;
-  g.Vh = (int)lat.Vh;
-  return g;
-}
+Geom df_geom(const Lattice& lat) { return make_geom(lat.L, lat.bc, lat.V, lat.Vh); }
 
 SpinorView<PDF> dfview(const Field& f) {
   SpinorView<PDF> v;
@@ -417,6 +409,7 @@ void hop_df(const qcd_gauge* gh, const Field& in, Field& out, int out_parity, in
   A.g = df_geom(gh->lat);
   A.out_parity = out_parity;
   A.ls = in.ls;
+  A.d_ls = make_fastdiv((unsigned)in.ls);
   A.x1 = x1 != nullptr;
   A.x2 = x2 != nullptr;
   A.a = df_scalar_host(a);

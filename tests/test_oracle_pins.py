@@ -372,3 +372,30 @@ def test_generator_su3_and_smoothness():
     assert means[0] > means[1]
     # reproducible from the seed
     assert np.array_equal(inputs.gauge_field((2, 2, 2, 2), 0.2, 7), inputs.gauge_field((2, 2, 2, 2), 0.2, 7))
+
+
+def test_spectra_explain_the_choice_of_solver():
+    """Sec. II C: BiCGStab is used for Wilson and CG on D^dag D for domain-wall because the
+    domain-wall spectrum reaches into the left half of the complex plane.  Dense spectra on 2^4
+    (Ls = 4, M5 = 1.8, mf = 0.02) of the benchmark-like smoothed fields: every eigenvalue of the
+    Wilson matrix at kappa = 0.125 has a positive real part, some of the domain-wall ones do not."""
+    L = (2, 2, 2, 2)
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.2, 3)
+    n4 = V * 12
+    W = np.empty((n4, n4), dtype=complex)
+    for j in range(n4):
+        e = np.zeros(n4, dtype=complex)
+        e[j] = 1.0
+        W[:, j] = ora.wilson(L, BC_T, 0.125, U, e.reshape(V, 4, 3)).reshape(n4)
+    ew = np.linalg.eigvals(W)
+    Ls = 4
+    n5 = Ls * n4
+    D = np.empty((n5, n5), dtype=complex)
+    for j in range(n5):
+        e = np.zeros(n5, dtype=complex)
+        e[j] = 1.0
+        D[:, j] = ora.dw(L, BC_T, Ls, 1.8, 0.02, U, e.reshape(Ls, V, 4, 3)).reshape(n5)
+    ed = np.linalg.eigvals(D)
+    assert ew.real.min() > 0
+    assert ed.real.min() < 0 < ed.real.max()
