@@ -283,6 +283,16 @@ qcd_status qcd_mom_energy(const void* P, int64_t nlinks, double* out, void* stre
 qcd_status qcd_norm2(const qcd_gauge* g, const qcd_fermion* fermion, const void* psi, int32_t nrhs,
                      double* out, void* stream);
 
+/* Diagnostics and test hooks (environment variables, read by the library):
+ *   QCD_TUNECACHE=<file>   the autotuner's persistent cache (see qcd_set_tuning);
+ *   QCD_TUNE_VERBOSE=1     print every timed launch shape to stderr;
+ *   QCD_FAULT=alloc        every device workspace allocation fails (QCD_ERR_OOM);
+ *   QCD_FAULT=nan          qcd_solve poisons its inner residual with NaN after the
+ *                          first restart, which the device reductions must report
+ *                          (QCD_ERR_NAN);
+ *   QCD_FAULT=noconv       qcd_solve stops after one inner iteration (QCD_ERR_NOCONV).
+ * The main entry points open an NVTX range named after themselves. */
+
 /* Message describing the last failing call on this thread ("" if none). */
 const char* qcd_last_error(void);
 

@@ -8,10 +8,19 @@
 #include <cstring>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace qcd {
+
+// An NVTX range around an ABI call (visible in Nsight Systems / Compute timelines; costs
+// nothing when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& prm, const double* b,
                   double* x, int nrhs, qcd_solve_info* info, cudaStream_t st);
@@ -233,6 +242,7 @@ qcd_status qcd_set_tuning(int32_t mode) {
 }
 
 qcd_status qcd_gauge_load(const qcd_geom* geom, const void* U, void* stream, qcd_gauge** out) {
+  NvtxRange nvtx_range("qcd_gauge_load");
   qcd_gauge* g = nullptr;
   qcd_status s = guarded([&] {
     check_geom(geom);
@@ -313,6 +323,7 @@ size_t qcd_field_bytes(const qcd_geom* geom, const qcd_fermion* fermion, qcd_pre
 
 qcd_status qcd_field_pack(const qcd_gauge* gc, const qcd_fermion* fermion, qcd_prec prec, int32_t parity,
                           const void* canon, void* internal, int32_t nrhs, void* stream) {
+  NvtxRange nvtx_range("qcd_field_pack");
   return guarded([&] {
     check_gauge(gc);
     qcd_gauge* g = const_cast<qcd_gauge*>(gc);
@@ -332,6 +343,7 @@ qcd_status qcd_field_pack(const qcd_gauge* gc, const qcd_fermion* fermion, qcd_p
 
 qcd_status qcd_field_unpack(const qcd_gauge* gc, const qcd_fermion* fermion, qcd_prec prec, int32_t parity,
                             const void* internal, void* canon, int32_t nrhs, void* stream) {
+  NvtxRange nvtx_range("qcd_field_unpack");
   return guarded([&] {
     check_gauge(gc);
     qcd_gauge* g = const_cast<qcd_gauge*>(gc);
@@ -352,6 +364,7 @@ qcd_status qcd_field_unpack(const qcd_gauge* gc, const qcd_fermion* fermion, qcd
 
 qcd_status qcd_dslash(const qcd_gauge* gc, const qcd_fermion* fermion, qcd_prec prec, int32_t op,
                       const void* in, void* out, int32_t nrhs, int32_t layout, void* stream) {
+  NvtxRange nvtx_range("qcd_dslash");
   return guarded([&] {
     check_gauge(gc);
     qcd_gauge* g = const_cast<qcd_gauge*>(gc);
@@ -418,6 +431,7 @@ qcd_status qcd_dslash(const qcd_gauge* gc, const qcd_fermion* fermion, qcd_prec 
 
 qcd_status qcd_solve(const qcd_gauge* gc, const qcd_fermion* fermion, const qcd_solver_params* params,
                      const void* b, void* x, int32_t nrhs, qcd_solve_info* info, void* stream) {
+  NvtxRange nvtx_range("qcd_solve");
   return guarded([&] {
     check_gauge(gc);
     qcd_gauge* g = const_cast<qcd_gauge*>(gc);
@@ -460,6 +474,7 @@ qcd_status qcd_solve(const qcd_gauge* gc, const qcd_fermion* fermion, const qcd_
 
 qcd_status qcd_norm2(const qcd_gauge* gc, const qcd_fermion* fermion, const void* psi, int32_t nrhs,
                      double* out, void* stream) {
+  NvtxRange nvtx_range("qcd_norm2");
   return guarded([&] {
     check_gauge(gc);
     qcd_gauge* g = const_cast<qcd_gauge*>(gc);
@@ -492,6 +507,7 @@ qcd_status qcd_mhat_noalloc(const qcd_gauge* gc, const qcd_fermion* fermion, qcd
 
 qcd_status qcd_force(const qcd_gauge* gc, const qcd_fermion* fermion, const void* X, const void* eta,
                      void* dSdU, void* stream) {
+  NvtxRange nvtx_range("qcd_force");
   return guarded([&] {
     check_gauge(gc);
     check_fermion(fermion);
@@ -505,6 +521,7 @@ qcd_status qcd_force(const qcd_gauge* gc, const qcd_fermion* fermion, const void
 
 qcd_status qcd_force_eo(const qcd_gauge* gc, const qcd_fermion* fermion, const void* X, const void* Y,
                         void* dSdU, void* stream) {
+  NvtxRange nvtx_range("qcd_force_eo");
   return guarded([&] {
     check_gauge(gc);
     check_fermion(fermion);
@@ -518,6 +535,7 @@ qcd_status qcd_force_eo(const qcd_gauge* gc, const qcd_fermion* fermion, const v
 }
 
 qcd_status qcd_force_project(const qcd_gauge* gc, const void* dSdU, void* F, void* stream) {
+  NvtxRange nvtx_range("qcd_force_project");
   return guarded([&] {
     check_gauge(gc);
     if (!dSdU || !F) raise(QCD_ERR_ARG, "NULL argument");
@@ -528,6 +546,7 @@ qcd_status qcd_force_project(const qcd_gauge* gc, const void* dSdU, void* F, voi
 }
 
 qcd_status qcd_link_update(void* U, const void* P, double eps, int64_t nlinks, void* stream) {
+  NvtxRange nvtx_range("qcd_link_update");
   return guarded([&] {
     if (!U || !P) raise(QCD_ERR_ARG, "NULL argument");
     if (nlinks < 0) raise(QCD_ERR_ARG, "nlinks must be >= 0");

@@ -27,6 +27,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <string>
@@ -897,7 +898,16 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   if (nactive > 0) restart_from_residual(true);
   S.upload();
 
-  const int maxiter = prm.maxiter > 0 ? prm.maxiter : 100000;
+  // host-side fault injection for tests (no device fault is ever provoked):
+  // QCD_FAULT=nan poisons the inner residual with a NaN bit pattern after the
+  // first restart, so the device reductions must report it; QCD_FAULT=noconv
+  // caps the iteration count at one.
+  const char* fault = getenv("QCD_FAULT");
+  if (fault && strcmp(fault, "nan") == 0 && nactive > 0) {
+    QCD_CK(cudaMemsetAsync(S.r.data, 0xFF, S.r.data_bytes(), st));
+    if (S.r.norm) QCD_CK(cudaMemsetAsync(S.r.norm, 0xFF, S.r.norm_bytes(), st));
+  }
+  const int maxiter = (fault && strcmp(fault, "noconv") == 0) ? 1 : (prm.maxiter > 0 ? prm.maxiter : 100000);
   const bool graph = prm.use_graph != 0;
   const int chunk = graph ? (prm.graph_chunk > 0 ? prm.graph_chunk : 32) : 16;
   bool first = true;

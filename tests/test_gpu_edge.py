@@ -142,3 +142,26 @@ def test_allocation_fault_injection_on_the_host(small):
         del os.environ["QCD_FAULT"]
     g = qcd.Gauge.load(to_dev(U), L, BC)  # and the library still works afterwards
     g.free()
+
+
+@pytest.mark.parametrize("fault,status", [("nan", "ERR_NAN"), ("noconv", "ERR_NOCONV")])
+@pytest.mark.parametrize("inner", ["f32", "f16"])
+def test_solver_fault_injection_on_the_host(small, fault, status, inner):
+    """QCD_FAULT=nan poisons the inner residual (the device reductions must flag it); QCD_FAULT=noconv
+    caps the iterations: the solve returns the matching status, and the next solve is clean."""
+    device()
+    L, V, U = small
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    f = qcd.wilson(0.12)
+    b = to_dev(inputs.gaussian_source((V, 4, 3), 3))
+    x = torch.zeros_like(b)
+    os.environ["QCD_FAULT"] = fault
+    try:
+        info, st = qcd.solve(g, f, b, x, tol=1e-10, inner=inner, use_graph=True, check=False)
+    finally:
+        del os.environ["QCD_FAULT"]
+    assert qcd.STATUS_NAMES[st] == status, (st, info)
+    assert not info[0]["converged"]
+    x.zero_()
+    info, st = qcd.solve(g, f, b, x, tol=1e-10, inner=inner, use_graph=True)
+    assert st == qcd.OK and info[0]["converged"]
