@@ -116,13 +116,17 @@ void zero_parity_canon(const Lattice& lat, int parity, double* canon, int nvec, 
 // with H -> H^dag for dagger; all slices (ls) and right-hand sides of `in`.
 // `stop` (device int, may be null): the kernel does nothing when *stop != 0
 // (used by the solver's captured iteration chunks).
-// `red` (may be null; single right-hand side, FP32/FP64, x given): an inner
-// product fused into the epilogue.  Every block writes an FP64 partial sum to
+// `red` (may be null; x given): an inner product fused into the epilogue.
+//   mode 1: (rt, out)          -> k = 0, 1 (re, im)
+//   mode 2: (out, x), |out|^2  -> k = 0, 1, 2
+// One right-hand side (FP32/FP64): every block writes an FP64 partial sum to
 // partial[block * 4 + k]; the last block of each group of 64 blocks to finish
 // (counted in counters[group], which start at 0 and are reset) sums its group
 // in order into gpartial[group * 4 + k]; *npartial receives the number of groups.
-//   mode 1: (rt, out)          -> k = 0, 1 (re, im)
-//   mode 2: (out, x), |out|^2  -> k = 0, 1, 2
+// Several right-hand sides (FP32): every warp (32 sites of one right-hand side)
+// writes partial[(q * ceil(Vh/32) + site block) * 4 + k] and a second kernel
+// sums each right-hand side q in order into gpartial[q * 4 + k] (counters and
+// npartial unused).
 struct RedSpec {
   int mode;
   const Field* rt;

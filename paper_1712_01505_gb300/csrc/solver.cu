@@ -520,8 +520,10 @@ struct Solver {
 
   bool bicg() const { return prm.method == QCD_BICGSTAB; }
   // BiCGStab inner products fused into the stencil epilogue: one Wilson
-  // right-hand side stored in FP32 or FP64
+  // right-hand side stored in FP32 or FP64 (group sums by the stencil's last
+  // blocks), or several stored in FP32 (per-warp partials summed per rhs)
   bool fused() const { return bicg() && f.type == QCD_WILSON && nrhs == 1 && inner != QCD_F16; }
+  bool fused_multi() const { return bicg() && f.type == QCD_WILSON && nrhs > 1 && inner == QCD_F32; }
   long n() const { return r.nsites(); }
 
   void body() {
@@ -550,6 +552,15 @@ struct Solver {
                                                npart);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl, &red2);
+      } else if (fused_multi()) {
+        // per-rhs sums land in partial[rhs * 4 + k]: one partial per right-hand side
+        RedSpec red1{1, &rt, bpartial, partial, nullptr, nullptr};
+        RedSpec red2{2, nullptr, bpartial, partial, nullptr, nullptr};
+        apply_mhat(opin, p, v, dag, st, "in", ctl, &red1);
+        k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, 1,
+                                               nullptr);
+        QCD_LAUNCH_CK();
+        apply_mhat(opin, s, t, dag, st, "in", ctl, &red2);
       } else {
         apply_mhat(opin, p, v, dag, st, "in", ctl);
         k_cdot<R><<<grid, kThreads, 0, st>>>(any_view(rt), any_view(v), nn, partial, sc, ctl);
@@ -562,8 +573,9 @@ struct Solver {
         QCD_LAUNCH_CK();
       }
       k_bicg_xr<R, RX><<<grid, kThreads, 0, st>>>(any_view(xin), any_view(p), any_view(s), any_view(t),
-                                                  any_view(r), any_view(rt), nn, partial, nblk,
-                                                  fused() ? ctl + 2 : nullptr, partial2, sc, ctl);
+                                                  any_view(r), any_view(rt), nn, partial,
+                                                  fused_multi() ? 1 : (int)nblk, fused() ? ctl + 2 : nullptr,
+                                                  partial2, sc, ctl);
       QCD_LAUNCH_CK();
       k_bicg_check<<<nrhs, kThreads, 0, st>>>(sc, partial2, nblk, ctl, nrhs == 1);
       QCD_LAUNCH_CK();
@@ -715,6 +727,8 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   const size_t npart = std::max<size_t>((size_t)S.nblk * nrhs, nstencil_blocks / 64 + 1);
   S.partial = (double*)g->ws.get("s.partial", sizeof(double) * npart * kMaxPartial);
   S.partial2 = (double*)g->ws.get("s.partial2", sizeof(double) * (size_t)S.nblk * nrhs * kMaxPartial);
+  if (S.fused_multi())  // per-warp partials of every right-hand side
+    S.bpartial = (double*)g->ws.get("s.bpartialN", sizeof(double) * (size_t)nrhs * ((lat.Vh + 31) / 32) * kMaxPartial);
   if (S.fused()) {
     S.bpartial = (double*)g->ws.get("s.bpartial", sizeof(double) * nstencil_blocks * kMaxPartial);
     const size_t ngroups = nstencil_blocks / 64 + 2;

@@ -410,8 +410,13 @@ __device__ __forceinline__ void hop_link_sm(const HopArgs<P, RECON>& A, const Sm
   }
 }
 
-template <int P, int RECON, int BY, int TS>
+// RED (with TS = 1, several right-hand sides): the BiCGStab inner products of
+// the k_hop_red kernel per right-hand side.  A warp is 32 sites of one slice, so
+// it reduces in registers and lane 0 writes partial[(q * nsb + site block) * 4
+// + k] (nsb = ceil(Vh / 32)); k_red_rows then sums each slice's partials in order.
+template <int P, int RECON, int BY, int TS, int RED = 0>
 __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
+  static_assert(RED == 0 || TS == 1, "fused reductions need one slice per thread");
   using R = typename MathType<P>::type;
   if (A.stop && *A.stop) return;
   __shared__ SmLinks<R> sm;
@@ -443,7 +448,8 @@ __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
   }
   __syncthreads();
   const int q0 = (stile * BY + ty) * TS;
-  if (!valid || q0 >= A.nslices) return;
+  if (q0 >= A.nslices) return;      // a whole warp (one row of slices)
+  if (!valid && RED == 0) return;  // sites past Vh: with RED they add zero to the warp's sum
   const int nt = min(TS, A.nslices - q0);
   SpinorView<P> in[TS];
   long soff[TS];
@@ -459,6 +465,8 @@ __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
   for (int t = 0; t < TS; ++t)
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[t][k] = {R(0), R(0)};
+  R red[3] = {R(0), R(0), R(0)};
+  if (valid) {
   const R sg = A.dagger ? R(1) : R(-1);
   hop_link_sm<P, RECON, TS, 0>(A, sm, tx, sg, in, soff, nt, acc);
   hop_link_sm<P, RECON, TS, 1>(A, sm, tx, sg, in, soff, nt, acc);
@@ -485,7 +493,52 @@ __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
       for (int k = 0; k < 12; ++k) o[k] = a * acc[t][k];
     }
     A.out.offset_rhs(r).store(site, o);
+    if constexpr (RED == 1) {  // (rt, out)
+      Cx<R> w[12], d = {R(0), R(0)};
+      A.rt.offset_rhs(r).load(site, w);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) d = cjmadd(w[k], o[k], d);
+      red[0] = d.re;
+      red[1] = d.im;
+    } else if constexpr (RED == 2) {  // (out, x), |out|^2
+      Cx<R> xs[12], d = {R(0), R(0)};
+      A.x.offset_rhs(r).load(site, xs);
+      R oo = R(0);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        d = cjmadd(o[k], xs[k], d);
+        oo = fma(o[k].re, o[k].re, fma(o[k].im, o[k].im, oo));
+      }
+      red[0] = d.re;
+      red[1] = d.im;
+      red[2] = oo;
+    }
   }
+  }  // valid
+  if constexpr (RED != 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      for (int o = 16; o > 0; o >>= 1) red[k] += __shfl_down_sync(0xffffffffu, red[k], o);
+    if (tx == 0) {
+      const long nsb = (A.g.Vh + 31) / 32;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) A.partial[((long)q0 * nsb + sblock) * 4 + k] = (double)red[k];
+    }
+  }
+}
+
+// per slice q: out[q * 4 + k] = sum over the nsb site blocks of partial[(q * nsb + b) * 4 + k]
+// in a fixed order (one block per slice)
+__global__ void k_red_rows(const double* __restrict__ partial, long nsb, double* __restrict__ out) {
+  const int q = blockIdx.x;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (long b = threadIdx.x; b < nsb; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] += partial[((long)q * nsb + b) * 4 + k];
+  block_sum<3>(v);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[(long)q * 4 + k] = v[k];
 }
 
 Geom dev_geom(const Lattice& lat) { return make_geom(lat.L, lat.bc, lat.V, lat.Vh); }
@@ -525,13 +578,13 @@ void launch_tile(HopLaunch<P, RECON>* L, int block) {
   k_hop<P, RECON, TILE, PF><<<(unsigned)(sblocks * A.ntiles), block, 0, L->st>>>(A);
 }
 
-template <int P, int RECON, int BY, int TS>
+template <int P, int RECON, int BY, int TS, int RED = 0>
 void launch_sm(HopLaunch<P, RECON>* L) {
   HopArgs<P, RECON> A = L->args;
   A.ntiles = (A.nslices + BY * TS - 1) / (BY * TS);
   A.d_ntiles = make_fastdiv((unsigned)A.ntiles);
   long sblocks = (A.g.Vh + 31) / 32;
-  k_hop_sm<P, RECON, BY, TS><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
+  k_hop_sm<P, RECON, BY, TS, RED><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
 }
 
 // cfg.tile > 0: register tile of that many slices per thread (k_hop), 101 /
@@ -543,6 +596,13 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
   auto* L = (HopLaunch<P, RECON>*)ctx;
   if constexpr (P == P64) {
     launch_tile<P, RECON, 1>(L, cfg.block);
+  } else if (L->args.red && L->args.nslices > 1) {  // fused reductions over several slices
+    const bool by8 = cfg.tile == -81;
+    if (L->args.red == 1) {
+      if (by8) launch_sm<P, RECON, 8, 1, 1>(L); else launch_sm<P, RECON, 4, 1, 1>(L);
+    } else {
+      if (by8) launch_sm<P, RECON, 8, 1, 2>(L); else launch_sm<P, RECON, 4, 1, 2>(L);
+    }
   } else {
     switch (cfg.tile) {
       case 1: launch_tile<P, RECON, 1>(L, cfg.block); break;
@@ -569,9 +629,10 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   A.gpartial = nullptr;
   A.counters = nullptr;
   A.npartial = nullptr;
+  const bool multi_red = red && red->mode && in.nrhs * in.ls > 1;
   if (red && red->mode) {
-    if (P == P16 || in.nrhs * in.ls != 1 || !x || (red->mode == 1 && !red->rt))
-      raise(QCD_ERR_ARG, "fused reduction needs one FP32/FP64 right-hand side and an x term");
+    if (P == P16 || !x || (red->mode == 1 && !red->rt) || (multi_red && P != P32))
+      raise(QCD_ERR_ARG, "fused reductions need FP32 (or, for one right-hand side, FP64) fields and an x term");
     A.red = red->mode;
     A.partial = red->partial;
     A.gpartial = red->gpartial;
@@ -613,12 +674,17 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64)  // one slice per thread with prefetches (memory-bound precisions)
     for (int pf : {101, 201})
       for (int b : blocks) cands.push_back({b, pf});
+  if (multi_red) cands = {{128, -41}, {256, -81}};  // shared-memory links, one slice per thread
   char key[160];
   snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d red%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay, A.red);
   LaunchCfg cfg = tune(key, cands, &run_cfg<P, RECON>, &L, st, allow_tuning);
   run_cfg<P, RECON>(&L, cfg);
   QCD_LAUNCH_CK();
+  if (multi_red) {  // per right-hand side sums of the per-warp partials
+    k_red_rows<<<(unsigned)A.nslices, 256, 0, st>>>(A.partial, (A.g.Vh + 31) / 32, A.gpartial);
+    QCD_LAUNCH_CK();
+  }
 }
 
 }  // namespace
