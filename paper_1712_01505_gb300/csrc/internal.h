@@ -123,10 +123,11 @@ void zero_parity_canon(const Lattice& lat, int parity, double* canon, int nvec, 
 // partial[block * 4 + k]; the last block of each group of 64 blocks to finish
 // (counted in counters[group], which start at 0 and are reset) sums its group
 // in order into gpartial[group * 4 + k]; *npartial receives the number of groups.
-// Several right-hand sides (FP32): every warp (32 sites of one right-hand side)
-// writes partial[(q * ceil(Vh/32) + site block) * 4 + k] and a second kernel
-// sums each right-hand side q in order into gpartial[q * 4 + k] (counters and
-// npartial unused).
+// Several slices (FP32: right-hand sides, domain-wall slices): every warp (32
+// sites of one slice q) writes partial[(q * ceil(Vh/32) + site block) * 4 + k]
+// and a second kernel sums each slice in order into gpartial[q * 4 + k]: the ls
+// slice sums of right-hand side r are gpartial[(r * ls + s) * 4 + k] (counters
+// and npartial unused).
 struct RedSpec {
   int mode;
   const Field* rt;
@@ -184,7 +185,8 @@ struct OpCtx {
   int prec;
 };
 // Schur operator on even sites: out = Mhat in (dagger: Mhat^dag); uses workspace temporaries
-// `red` (Wilson only) is forwarded to the final stencil, whose epilogue forms out.
+// `red` is forwarded to the final stencil, whose epilogue forms out (Wilson; for
+// domain-wall only with dagger, where the final step is the stencil).
 void apply_mhat(const OpCtx& c, const Field& in, Field& out, int dagger, cudaStream_t st,
                 const char* tag, const int* stop = nullptr, const RedSpec* red = nullptr);
 // out_p = in_p - kappa H in_other (Wilson) or A in_p - 1/2 H in_other (DWF), parity p

@@ -25,7 +25,7 @@ void apply_mhat(const OpCtx& c, const Field& in, Field& out, int dagger, cudaStr
     hop(c.g, tmp, out, 0, dagger, -k2, &in, st, stop, true, red);
     return;
   }
-  if (red) raise(QCD_ERR_UNSUPPORTED, "fused reductions are for the Wilson operator");
+  if (red && !dagger) raise(QCD_ERR_UNSUPPORTED, "domain-wall Mhat fuses reductions into Mhat^dag only");
   DwParams p{c.f.Ls, c.f.M5, c.f.mf};
   Field t1 = ws_field(c.g, t + ".mhat.t1", c.prec, in.ls, in.nrhs);
   Field t2 = ws_field(c.g, t + ".mhat.t2", c.prec, in.ls, in.nrhs);
@@ -38,7 +38,7 @@ void apply_mhat(const OpCtx& c, const Field& in, Field& out, int dagger, cudaStr
     dw_ainv(p, in, t1, 1, 1.0, nullptr, st, stop);        // A^-dag in
     hop(c.g, t1, t2, 1, 1, 1.0, nullptr, st, stop);       // (H^dag)_oe
     dw_ainv(p, t2, t1, 1, 1.0, nullptr, st, stop);        // A^-dag
-    hop(c.g, t1, out, 0, 1, -0.25, &in, st, stop);        // in - 1/4 (H^dag)_eo (...)
+    hop(c.g, t1, out, 0, 1, -0.25, &in, st, stop, true, red);  // in - 1/4 (H^dag)_eo (...)
   }
 }
 

@@ -390,13 +390,13 @@ __device__ __forceinline__ bool block_cg_alpha(Scal& s, const double* partial, i
 // into partial_out (not the array alpha is read from)
 template <typename R, typename RX>
 __global__ void k_cg_xr(AnyView x_, AnyView p_, AnyView q_, AnyView r_, long n, const double* partial_in,
-                        int nblk, double* partial_out, Scal* sc, int* ctl) {
+                        int nblk, const int* nb_dev, double* partial_out, Scal* sc, int* ctl) {
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
   Scal& s = sc[r];
   if (!s.active) return;
   double a;
-  if (!block_cg_alpha(s, partial_in, nblk, r, ctl, &a)) return;
+  if (!block_cg_alpha(s, partial_in, nb_dev ? *nb_dev : nblk, r, ctl, &a)) return;
   const R al = (R)a;
   const RX alx = (RX)a;
   double v[1] = {0.0};
@@ -524,6 +524,10 @@ struct Solver {
   // blocks), or several stored in FP32 (per-warp partials summed per rhs)
   bool fused() const { return bicg() && f.type == QCD_WILSON && nrhs == 1 && inner != QCD_F16; }
   bool fused_multi() const { return bicg() && f.type == QCD_WILSON && nrhs > 1 && inner == QCD_F32; }
+  // CG: Re(p, q) formed in the epilogue of the last stencil of Mhat^dag (FP32; per-warp
+  // partials summed per slice when there are several slices, else group sums)
+  bool fused_cg() const { return !bicg() && inner == QCD_F32; }
+  bool cg_single() const { return fused_cg() && nrhs * ls == 1; }
   long n() const { return r.nsites(); }
 
   void body() {
@@ -587,11 +591,23 @@ struct Solver {
       k_cg_p<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(p), nn, sc, ctl);
       QCD_LAUNCH_CK();
       apply_mhat(opin, p, w, 0, st, "in", ctl);
-      apply_mhat(opin, w, q, 1, st, "in", ctl);
-      k_rdot<R><<<grid, kThreads, 0, st>>>(any_view(p), any_view(q), nn, partial, sc, ctl);
-      QCD_LAUNCH_CK();
+      int nb = (int)nblk;
+      const int* nb_dev = nullptr;
+      if (fused_cg()) {  // (p, q) in the epilogue of q = Mhat^dag w
+        int* npart = ctl + 2;
+        RedSpec red{1, &p, bpartial, partial, counters, npart};
+        apply_mhat(opin, w, q, 1, st, "in", ctl, &red);
+        if (cg_single())
+          nb_dev = npart;
+        else
+          nb = ls;  // one sum per slice
+      } else {
+        apply_mhat(opin, w, q, 1, st, "in", ctl);
+        k_rdot<R><<<grid, kThreads, 0, st>>>(any_view(p), any_view(q), nn, partial, sc, ctl);
+        QCD_LAUNCH_CK();
+      }
       k_cg_xr<R, RX><<<grid, kThreads, 0, st>>>(any_view(xin), any_view(p), any_view(q), any_view(r),
-                                                nn, partial, nblk, partial2, sc, ctl);
+                                                nn, partial, nb, nb_dev, partial2, sc, ctl);
       QCD_LAUNCH_CK();
       k_cg_check<<<nrhs, kThreads, 0, st>>>(sc, partial2, nblk, ctl, nrhs == 1);
       QCD_LAUNCH_CK();
@@ -727,9 +743,10 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   const size_t npart = std::max<size_t>((size_t)S.nblk * nrhs, nstencil_blocks / 64 + 1);
   S.partial = (double*)g->ws.get("s.partial", sizeof(double) * npart * kMaxPartial);
   S.partial2 = (double*)g->ws.get("s.partial2", sizeof(double) * (size_t)S.nblk * nrhs * kMaxPartial);
-  if (S.fused_multi())  // per-warp partials of every right-hand side
-    S.bpartial = (double*)g->ws.get("s.bpartialN", sizeof(double) * (size_t)nrhs * ((lat.Vh + 31) / 32) * kMaxPartial);
-  if (S.fused()) {
+  if (S.fused_multi() || (S.fused_cg() && !S.cg_single()))  // per-warp partials of every slice
+    S.bpartial = (double*)g->ws.get("s.bpartialN",
+                                    sizeof(double) * (size_t)nrhs * ls * ((lat.Vh + 31) / 32) * kMaxPartial);
+  if (S.fused() || S.cg_single()) {
     S.bpartial = (double*)g->ws.get("s.bpartial", sizeof(double) * nstencil_blocks * kMaxPartial);
     const size_t ngroups = nstencil_blocks / 64 + 2;
     const long gen = g->ws.generation;

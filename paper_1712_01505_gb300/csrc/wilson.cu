@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
 }
 
 // per slice q: out[q * 4 + k] = sum over the nsb site blocks of partial[(q * nsb + b) * 4 + k]
-// in a fixed order (one block per slice)
+// in a fixed order (one block per slice); the consumer adds the ls slices of a right-hand side
 __global__ void k_red_rows(const double* __restrict__ partial, long nsb, double* __restrict__ out) {
   const int q = blockIdx.x;
   double v[3] = {0.0, 0.0, 0.0};

@@ -46,6 +46,15 @@ for case in json.loads(sys.argv[1]):
             a = o[r].cpu().numpy()
             err = max(err, float(np.linalg.norm(a - ref) / np.linalg.norm(ref)))
         res.append(err)
+    elif case["kind"] == "dwsolve":
+        Ls = case["Ls"]
+        f = qcd.dwf(Ls, 1.8, 0.02)
+        b = inputs.gaussian_source((Ls, V, 4, 3), 1)
+        x = torch.zeros((Ls, V, 4, 3), dtype=torch.complex128, device="cuda")
+        qcd.solve(g, f, torch.from_numpy(b).cuda(), x, method=qcd.CG_NORMAL, tol=1e-10, inner="f32",
+                  use_graph=True, graph_chunk=8)
+        xr = x.cpu().numpy()
+        res.append(float(np.linalg.norm(b - ora.dw(L, BC, Ls, 1.8, 0.02, U, xr)) / np.linalg.norm(b)))
     else:
         kappa = 0.124
         f = qcd.wilson(kappa)
@@ -95,6 +104,13 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
         cases.append({"kind": "solve", "L": L, "recon": 12, "nrhs": 4})
         for xp, red in ((1, 1), (1, 2)):
             lines.append(f"{_key(L, 'f32', 12, 4, xp, red)}\t{block}\t{tile}")
+        tol.append(1e-10)
+    # the fused-reduction shared-memory stencils of the domain-wall CG (Re(p, q) over all slices)
+    for tile, block in ((-41, 128), (-81, 256)):
+        L = (4, 4, 2, t)
+        t += 2
+        cases.append({"kind": "dwsolve", "L": L, "recon": 12, "Ls": 8})
+        lines.append(f"{_key(L, 'f32', 12, 8, 1, 1)}\t{block}\t{tile}")
         tol.append(1e-10)
     cache = tmp_path / "tune.txt"
     cache.write_text("\n".join(lines) + "\n")
