@@ -173,3 +173,35 @@ def test_dw_cg_solve_with_double_float_outer_steps(inner):
     assert res <= 1e-10
     assert abs(res - info[0]["true_resid"]) <= 1e-6 * res
     assert info[0]["outer_updates"] >= 2
+
+
+def test_full_size_dw_hop_on_sampled_sites():
+    """Domain-wall benchmark lattice (16^3 x 32, Ls = 16, eps = 0.2 links seed 3, Gaussian source
+    seed 0): the FP32 12-real hop on all slices in the benchmark's INTERNAL-layout launch, checked
+    on sampled (site, slice) outputs the oracle computes one by one."""
+    device()
+    L, Ls = (16, 16, 16, 32), 16
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.2, 3)
+    psi = inputs.gaussian_source((Ls, V, 4, 3), 0)
+    par = ora.parity(L)
+    even = np.flatnonzero(par == 0)
+    rng = np.random.default_rng(9)
+    sites = np.concatenate([even[:32], even[-32:], rng.choice(even, 128, replace=False)])
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=12)
+    f = qcd.dwf(Ls, M5, MF)
+    nb = qcd.field_bytes(g, f, "f32")
+    bi = torch.empty(nb, dtype=torch.uint8, device=device())
+    bo = torch.empty(nb, dtype=torch.uint8, device=device())
+    qcd.field_pack(g, f, "f32", 1, to_dev(psi), bi)
+    qcd.dslash(g, f, "D_EO", bi, bo, prec="f32", layout=qcd.INTERNAL)
+    out = torch.zeros((Ls, V, 4, 3), dtype=torch.complex128, device=device())
+    qcd.field_unpack(g, f, "f32", 0, bo, out)
+    torch.cuda.synchronize()
+    idx = torch.from_numpy(sites).to(device())
+    for s in (0, 7, Ls - 1):
+        inp = psi[s].copy()
+        inp[par == 0] = 0
+        ref = ora.hop_sites(L, BC, U, inp, sites)
+        assert rel_err(out[s][idx].cpu().numpy(), ref) < 1e-6
+    g.free()

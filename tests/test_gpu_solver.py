@@ -101,3 +101,35 @@ def test_solver_reports_noconv_with_best_iterate():
     assert not info[0]["converged"] and info[0]["iters"] <= 3
     r = oracle_resid_wilson(L, kappa, U, b, x.cpu().numpy())
     assert r < 1.0 and abs(r - info[0]["true_resid"]) < 1e-6 * max(r, 1e-30)
+
+
+def test_full_size_12rhs_hop_on_sampled_sites():
+    """Batched benchmark lattice (24^3 x 48, eps = 0.2 links seed 4, the 12 point sources plus
+    Gaussian noise so that every output is nonzero): the FP32 12-rhs D_eo in the benchmark's
+    INTERNAL-layout launch, checked on sampled outputs of every right-hand side."""
+    device()
+    L = (24, 24, 24, 48)
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.2, 4)
+    psi = inputs.gaussian_source((12, V, 4, 3), 5)
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=12)
+    f = qcd.wilson(0.124)
+    nb = qcd.field_bytes(g, f, "f32", 12)
+    bi = torch.empty(nb, dtype=torch.uint8, device=device())
+    bo = torch.empty(nb, dtype=torch.uint8, device=device())
+    qcd.field_pack(g, f, "f32", 1, to_dev(psi), bi, nrhs=12)
+    qcd.dslash(g, f, "D_EO", bi, bo, prec="f32", nrhs=12, layout=qcd.INTERNAL)
+    out = torch.zeros((12, V, 4, 3), dtype=torch.complex128, device=device())
+    qcd.field_unpack(g, f, "f32", 0, bo, out, nrhs=12)
+    torch.cuda.synchronize()
+    par = ora.parity(L)
+    even = np.flatnonzero(par == 0)
+    sites = np.random.default_rng(6).choice(even, 96, replace=False)
+    idx = torch.from_numpy(sites).to(device())
+    from tests.gpu_util import rel_err
+    for r in range(12):
+        inp = psi[r].copy()
+        inp[par == 0] = 0
+        ref = ora.hop_sites(L, BC, U, inp, sites)
+        assert rel_err(out[r][idx].cpu().numpy(), ref) < 1e-6
+    g.free()
