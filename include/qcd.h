@@ -128,8 +128,8 @@ typedef struct {
  * tol: target |b - A x| / |b| on the full, unpreconditioned system.
  * maxiter: cap on inner Krylov iterations (summed over restarts).
  * inner: precision of the inner iterations (QCD_F64: plain double solve;
- *   QCD_F32 / QCD_F16: mixed precision with double-precision reliable
- *   updates -- true residual recomputed and solution accumulated in FP64).
+ *   QCD_F32 / QCD_F16: mixed precision with reliable updates -- true residual
+ *   recomputed and solution accumulated in the outer precision, below).
  * delta: a reliable update is made when the iterated residual has dropped by
  *   this factor since the last one (0 < delta < 1; 0 selects 0.01 for an FP32
  *   and 0.1 for an FP16 inner solver).
