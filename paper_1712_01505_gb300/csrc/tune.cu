@@ -1,12 +1,14 @@
 // Launch-shape autotuner for the stencil kernels.
 //
 // On the first launch of a key (kernel, lattice, precision, right-hand sides)
-// every candidate shape is run a few times on the caller's stream and timed
-// with CUDA events; the fastest is cached for the life of the process and,
+// every candidate shape is timed with CUDA events on the caller's stream (about
+// 2 ms of launches per candidate, twice, interleaved); the fastest is cached for
+// the life of the process and,
 // when QCD_TUNECACHE names a file, appended to it and read back by later
 // processes.  Candidates must be idempotent (out-of-place stencils).  While a
 // stream is being captured into a CUDA graph nothing can be timed, so an
 // unknown key then falls back to the first candidate without caching it.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -96,12 +98,11 @@ LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
   cudaEvent_t e0, e1;
   QCD_CK(cudaEventCreate(&e0));
   QCD_CK(cudaEventCreate(&e1));
-  LaunchCfg best = cands[0];
-  float best_ms = 1e30f;
-  const int reps = 3;
-  for (const auto& c : cands) {
-    run(ctx, c);  // warm-up
-    QCD_LAUNCH_CK();
+  // every candidate: one warm-up launch, then two passes over all candidates
+  // (interleaved, so that clock or thermal drift does not favour one), each
+  // timing enough back-to-back launches to cover about 2 ms; a candidate's time
+  // is its smaller per-launch average
+  auto time_reps = [&](const LaunchCfg& c, int reps) {
     QCD_CK(cudaEventRecord(e0, st));
     for (int r = 0; r < reps; ++r) run(ctx, c);
     QCD_CK(cudaEventRecord(e1, st));
@@ -110,18 +111,34 @@ LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
     QCD_LAUNCH_CK();
     float ms = 0;
     QCD_CK(cudaEventElapsedTime(&ms, e0, e1));
+    return ms / reps;
+  };
+  std::vector<int> reps(cands.size());
+  std::vector<float> best_of(cands.size(), 1e30f);
+  for (size_t i = 0; i < cands.size(); ++i) {
+    run(ctx, cands[i]);  // warm-up
+    QCD_LAUNCH_CK();
+    const float once = time_reps(cands[i], 1);
+    reps[i] = once > 0.f ? (int)std::min(50.f, std::max(3.f, 2.0f / once)) : 50;
+  }
+  for (int pass = 0; pass < 2; ++pass)
+    for (size_t i = 0; i < cands.size(); ++i) best_of[i] = std::min(best_of[i], time_reps(cands[i], reps[i]));
+  LaunchCfg best = cands[0];
+  float best_ms = 1e30f;
+  for (size_t i = 0; i < cands.size(); ++i) {
     if (getenv("QCD_TUNE_VERBOSE"))
-      fprintf(stderr, "[qcd tune]   %s block %d tile %d: %.4f ms\n", key.c_str(), c.block, c.tile, ms / reps);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = c;
+      fprintf(stderr, "[qcd tune]   %s block %d tile %d: %.4f ms\n", key.c_str(), cands[i].block, cands[i].tile,
+              best_of[i]);
+    if (best_of[i] < best_ms) {
+      best_ms = best_of[i];
+      best = cands[i];
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (getenv("QCD_TUNE_VERBOSE"))
     fprintf(stderr, "[qcd tune] %s -> block %d tile %d (%.4f ms per launch)\n", key.c_str(), best.block,
-            best.tile, best_ms / reps);
+            best.tile, best_ms);
   std::lock_guard<std::mutex> lk(g_mu);
   g_cache[key] = best;
   append_cache(key, best);

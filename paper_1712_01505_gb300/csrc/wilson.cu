@@ -414,8 +414,8 @@ __device__ __forceinline__ void hop_link_sm(const HopArgs<P, RECON>& A, const Sm
 // the k_hop_red kernel per right-hand side.  A warp is 32 sites of one slice, so
 // it reduces in registers and lane 0 writes partial[(q * nsb + site block) * 4
 // + k] (nsb = ceil(Vh / 32)); k_red_rows then sums each slice's partials in order.
-template <int P, int RECON, int BY, int TS, int RED = 0>
-__global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
+template <int P, int RECON, int BY, int TS, int RED>
+__device__ __forceinline__ void hop_sm(const HopArgs<P, RECON>& A) {
   static_assert(RED == 0 || TS == 1, "fused reductions need one slice per thread");
   using R = typename MathType<P>::type;
   if (A.stop && *A.stop) return;
@@ -527,6 +527,17 @@ __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
   }
 }
 
+template <int P, int RECON, int BY, int TS, int RED>
+__global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
+  hop_sm<P, RECON, BY, TS, RED>(A);
+}
+
+// the same with the registers bounded so that 1024 threads (32 warps) fit on an SM
+template <int P, int RECON, int BY, int TS, int RED>
+__global__ void __launch_bounds__(32 * BY, 32 / BY) k_hop_sm_occ(HopArgs<P, RECON> A) {
+  hop_sm<P, RECON, BY, TS, RED>(A);
+}
+
 // per slice q: out[q * 4 + k] = sum over the nsb site blocks of partial[(q * nsb + b) * 4 + k]
 // in a fixed order (one block per slice); the consumer adds the ls slices of a right-hand side
 __global__ void k_red_rows(const double* __restrict__ partial, long nsb, double* __restrict__ out) {
@@ -578,30 +589,34 @@ void launch_tile(HopLaunch<P, RECON>* L, int block) {
   k_hop<P, RECON, TILE, PF><<<(unsigned)(sblocks * A.ntiles), block, 0, L->st>>>(A);
 }
 
-template <int P, int RECON, int BY, int TS, int RED = 0>
+template <int P, int RECON, int BY, int TS, int RED = 0, int OCC = 0>
 void launch_sm(HopLaunch<P, RECON>* L) {
   HopArgs<P, RECON> A = L->args;
   A.ntiles = (A.nslices + BY * TS - 1) / (BY * TS);
   A.d_ntiles = make_fastdiv((unsigned)A.ntiles);
   long sblocks = (A.g.Vh + 31) / 32;
-  k_hop_sm<P, RECON, BY, TS, RED><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
+  if constexpr (OCC)
+    k_hop_sm_occ<P, RECON, BY, TS, RED><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
+  else
+    k_hop_sm<P, RECON, BY, TS, RED><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
 }
 
 // cfg.tile > 0: register tile of that many slices per thread (k_hop), 101 /
 // 201: one slice per thread with prefetch mode 1 / 2;
 // cfg.tile < 0: shared-memory links (k_hop_sm), -tile = 10 * BY + TS for
-// BY thread rows of TS slices each
+// BY thread rows of TS slices each; -tile = 200 + 10 * BY + TS: the same with at most
+// 64 registers per thread (32 resident warps per SM)
 template <int P, int RECON>
 void run_cfg(void* ctx, const LaunchCfg& cfg) {
   auto* L = (HopLaunch<P, RECON>*)ctx;
   if constexpr (P == P64) {
     launch_tile<P, RECON, 1>(L, cfg.block);
   } else if (L->args.red && L->args.nslices > 1) {  // fused reductions over several slices
-    const bool by8 = cfg.tile == -81;
-    if (L->args.red == 1) {
-      if (by8) launch_sm<P, RECON, 8, 1, 1>(L); else launch_sm<P, RECON, 4, 1, 1>(L);
-    } else {
-      if (by8) launch_sm<P, RECON, 8, 1, 2>(L); else launch_sm<P, RECON, 4, 1, 2>(L);
+    switch (cfg.tile) {
+      case -81: L->args.red == 1 ? launch_sm<P, RECON, 8, 1, 1>(L) : launch_sm<P, RECON, 8, 1, 2>(L); break;
+      case -241: L->args.red == 1 ? launch_sm<P, RECON, 4, 1, 1, 1>(L) : launch_sm<P, RECON, 4, 1, 2, 1>(L); break;
+      case -281: L->args.red == 1 ? launch_sm<P, RECON, 8, 1, 1, 1>(L) : launch_sm<P, RECON, 8, 1, 2, 1>(L); break;
+      default: L->args.red == 1 ? launch_sm<P, RECON, 4, 1, 1>(L) : launch_sm<P, RECON, 4, 1, 2>(L);
     }
   } else {
     switch (cfg.tile) {
@@ -613,6 +628,8 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case -41: launch_sm<P, RECON, 4, 1>(L); break;
       case -42: launch_sm<P, RECON, 4, 2>(L); break;
       case -81: launch_sm<P, RECON, 8, 1>(L); break;
+      case -241: launch_sm<P, RECON, 4, 1, 0, 1>(L); break;
+      case -281: launch_sm<P, RECON, 8, 1, 0, 1>(L); break;
       default: launch_sm<P, RECON, 8, 2>(L); break;
     }
   }
@@ -667,6 +684,8 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64 && A.nslices >= 8) cands.push_back({128, -42});
   if (P != P64 && A.nslices >= 8) cands.push_back({256, -81});
   if (P != P64 && A.nslices >= 16) cands.push_back({256, -82});
+  if (P == P32 && A.nslices >= 4) cands.push_back({128, -241});
+  if (P == P32 && A.nslices >= 8) cands.push_back({256, -281});
   if (A.red) {  // the fused reduction exists for one slice per thread only
     cands.clear();
     for (int b : blocks) cands.push_back({b, 1});
@@ -674,7 +693,7 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64)  // one slice per thread with prefetches (memory-bound precisions)
     for (int pf : {101, 201})
       for (int b : blocks) cands.push_back({b, pf});
-  if (multi_red) cands = {{128, -41}, {256, -81}};  // shared-memory links, one slice per thread
+  if (multi_red) cands = {{128, -41}, {256, -81}, {128, -241}, {256, -281}};  // shared-memory links, one slice per thread
   char key[160];
   snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d red%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay, A.red);

@@ -79,11 +79,14 @@ def _key(L, prec, recon, ns, xp, red):
 def test_every_stencil_candidate_matches_the_oracle(tmp_path):
     device()
     # (tile code, block) of every candidate family; the shared-memory kernels fix their block
-    shapes = [(1, 128), (2, 64), (4, 256), (101, 64), (201, 128), (-41, 128), (-42, 128), (-81, 256), (-82, 256)]
+    shapes = [(1, 128), (2, 64), (4, 256), (101, 64), (201, 128), (-41, 128), (-42, 128), (-81, 256), (-82, 256),
+              (-241, 128), (-281, 256)]
     cases, lines, tol = [], [], []
     t = 4
     for prec, recon in (("f32", 12), ("f32", 18), ("f16", 12)):
         for tile, block in shapes:
+            if tile < -200 and prec != "f32":
+                continue  # the register-bounded shapes are FP32 only
             L = (4, 4, 4, t)
             t += 2
             cases.append({"kind": "hop", "L": L, "prec": prec, "recon": recon, "nrhs": 16})
@@ -98,7 +101,7 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
             lines.append(f"{_key(L, 'f32', 12, 1, xp, red)}\t{block}\t{tile}")
         tol.append(1e-10)
     # the fused-reduction shared-memory stencils of the batched (several rhs) iteration
-    for tile, block in ((-41, 128), (-81, 256)):
+    for tile, block in ((-41, 128), (-81, 256), (-241, 128), (-281, 256)):
         L = (4, 4, 8, t)
         t += 2
         cases.append({"kind": "solve", "L": L, "recon": 12, "nrhs": 4})
