@@ -293,3 +293,70 @@ def leapfrog(L, bc, kappa, U, P, phi_e, eps, nsteps, tol=1e-13):
         U = link_update(U, P, eps)
         P = P + (eps if k < nsteps - 1 else 0.5 * eps) * force(U)
     return U, P, h0, ham(U, P)
+
+
+# ----------------------------------------------------------------------------- Mobius domain-wall
+# The Mobius generalisation of Eq. (2) (Brower, Neff and Orginos): with the fifth-dimension
+# shift (S psi)_s = P_- psi_{s+1} + P_+ psi_{s-1} (factor -mf across the wall) and
+# D_W = (4 - M5) - H/2 the 4D Wilson matrix of mass -M5,
+#   D_M psi_s = (b5 D_W + 1) psi_s - (1 - c5 D_W) (S psi)_s = A psi - 1/2 H (B psi),
+#   B = b5 + c5 S,   A = (4 - M5) B + 1 - S.
+# b5 = 1, c5 = 0 is Eq. (2).  A and B act on (s, spin) at every site and colour.
+
+def mobius_blocks(Ls, M5, mf, b5, c5):
+    """A and B as (Ls, 4, Ls, 4) real arrays [s, spin, s', spin']."""
+    Pp = np.diag([1.0, 1.0, 0.0, 0.0])  # (1 + gamma5)/2, gamma5 = diag(1, 1, -1, -1)
+    Pm = np.diag([0.0, 0.0, 1.0, 1.0])
+    S = np.zeros((Ls, 4, Ls, 4))
+    for s in range(Ls):
+        S[s, :, (s + 1) % Ls, :] += Pm * (-mf if s == Ls - 1 else 1.0)
+        S[s, :, (s - 1) % Ls, :] += Pp * (-mf if s == 0 else 1.0)
+    eye = np.eye(4 * Ls).reshape(Ls, 4, Ls, 4)
+    B = b5 * eye + c5 * S
+    A = (4.0 - M5) * B + eye - S
+    return A, B
+
+
+def _block_apply(M, psi, dagger=False):
+    """(M psi) on a (Ls, V, 4, 3) field, M an (Ls, 4, Ls, 4) real block (M^T for dagger)."""
+    if dagger:
+        M = np.transpose(M, (2, 3, 0, 1))
+    return np.einsum("satb,tvbc->svac", M, _c(psi))
+
+
+def _hop5(L, bc, U, psi, dagger=False, out_parity=-1):
+    return np.stack([hop(L, bc, U, p, dagger=dagger, out_parity=out_parity) for p in _c(psi)])
+
+
+def mobius(L, bc, Ls, M5, mf, b5, c5, U, psi, dagger=False):
+    """D_M psi = A psi - 1/2 H B psi (adjoint: A^T psi - 1/2 B^T H^dag psi) on (Ls, V, 4, 3)."""
+    A, B = mobius_blocks(Ls, M5, mf, b5, c5)
+    if not dagger:
+        return _block_apply(A, psi) - 0.5 * _hop5(L, bc, U, _block_apply(B, psi))
+    return _block_apply(A, psi, True) - 0.5 * _block_apply(B, _hop5(L, bc, U, psi, dagger=True), True)
+
+
+def _block_inv(M):
+    n = M.shape[0] * M.shape[1]
+    return np.linalg.inv(M.reshape(n, n)).reshape(M.shape)
+
+
+def mobius_mhat(L, bc, Ls, M5, mf, b5, c5, U, psi_even, dagger=False):
+    """Schur operator on the even sites, preconditioned by A^-1:
+    Mhat = 1 - 1/4 A^-1 H_eo B A^-1 H_oe B;  Mhat^dag = 1 - 1/4 B^T H^dag_eo A^-T B^T H^dag_oe A^-T.
+    Returns the even sites (odd sites zero)."""
+    A, B = mobius_blocks(Ls, M5, mf, b5, c5)
+    Ai = _block_inv(A)
+    par = parity(L)
+    pe = _c(psi_even).copy()
+    pe[:, par == 1] = 0
+    if not dagger:
+        t = _hop5(L, bc, U, _block_apply(B, pe), out_parity=1)
+        t = _hop5(L, bc, U, _block_apply(B, _block_apply(Ai, t)), out_parity=0)
+        out = pe - 0.25 * _block_apply(Ai, t)
+    else:
+        t = _hop5(L, bc, U, _block_apply(Ai, pe, True), dagger=True, out_parity=1)
+        t = _hop5(L, bc, U, _block_apply(Ai, _block_apply(B, t, True), True), dagger=True, out_parity=0)
+        out = pe - 0.25 * _block_apply(B, t, True)
+    out[:, par == 1] = 0
+    return out
