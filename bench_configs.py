@@ -2,7 +2,8 @@
 
 * dwf:     domain-wall 16^3 x 32 x Ls=16, M5 = 1.8, mf = 0.02, eps = 0.2 (seed 3), Gaussian
            source (seed 0): the fifth-dimension hop in FP32 and FP16, and CG on Mhat^dag Mhat
-           with FP16 inner iterations + FP64 outer steps against the plain FP64 CG, to 1e-10.
+           with FP16 / FP32 inner iterations + FP64 or double-float outer steps against the
+           plain FP64 CG, to 1e-10; the same for the Mobius operator with b5 = 1.5, c5 = 0.5.
 * batched: Wilson 24^3 x 48, kappa = 0.124, eps = 0.2 (seed 4), the 12 spin-colour point
            sources at one random site (seed 0): one 12-rhs solve (shared link loads, graph
            chunks, tuned tiles) against 12 single-rhs solves, FP32 inner + FP64, to 1e-10.
@@ -93,7 +94,29 @@ def run_dwf(args):
         torch.cuda.synchronize()
         res[name] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "iters": info[0]["iters"],
                      "updates": info[0]["outer_updates"], "true_resid": info[0]["true_resid"]}
+    # Mobius (b5 = 1.5, c5 = 0.5: the Shamir kernel scaled by b5 + c5 = 2) on the same lattice
+    fm = qcd.mobius(Ls, M5, mf, 1.5, 0.5)
+    nb = qcd.field_bytes(g, fm, "f32")
+    a_ = torch.empty(nb, dtype=torch.uint8, device=dev)
+    o_ = torch.empty(nb, dtype=torch.uint8, device=dev)
+    qcd.field_pack(g, fm, "f32", 0, bd, a_)
+    mob = {"mhat_ms_f32": round(_time_launches(lambda: qcd.dslash(g, fm, "MHAT", a_, o_, prec="f32",
+                                                                  layout=qcd.INTERNAL), n=10), 4)}
+    for name, inner, outer in (("f32_df", "f32", "df64"), ("f64", "f64", "f64")):
+        kw = dict(method=qcd.CG_NORMAL, tol=1e-10, inner=inner, use_graph=True, graph_chunk=32,
+                  delta=(args.delta or 0.0), outer=outer)
+        x = torch.zeros_like(bd)
+        qcd.solve(g, fm, bd, x, **kw)  # warm-up (tuning, workspace)
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info, _ = qcd.solve(g, fm, bd, x, **kw)
+        torch.cuda.synchronize()
+        mob[name] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "iters": info[0]["iters"],
+                     "updates": info[0]["outer_updates"], "true_resid": info[0]["true_resid"]}
+    mob["speedup_f32_df_vs_f64"] = round(mob["f64"]["ms"] / mob["f32_df"]["ms"], 3)
     out = {"workload": "dwf_16x16x16x32_Ls16_M5_1.8_mf0.02", "hop": hop, "cg": res,
+           "mobius_b5_1.5_c5_0.5": mob,
            "note": "cg keys: inner precision, _df = double-float outer steps (else IEEE FP64)",
            "speedup_f16_vs_f64": round(res["f64"]["ms"] / res["f16"]["ms"], 3),
            "speedup_f32_vs_f64": round(res["f64"]["ms"] / res["f32"]["ms"], 3),

@@ -84,7 +84,7 @@ typedef enum {
  * precision of qcd_solve. */
 typedef enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_DF64 = 3 } qcd_prec;
 
-typedef enum { QCD_WILSON = 0, QCD_DWF = 1 } qcd_fermion_type;
+typedef enum { QCD_WILSON = 0, QCD_DWF = 1, QCD_MOBIUS = 2 } qcd_fermion_type;
 
 typedef enum {
   QCD_OP_D_EO = 0,     /* out_even = H_eo in_odd  (hopping term only, no kappa)    */
@@ -114,13 +114,22 @@ typedef struct {
 
 /* type = QCD_WILSON: kappa = 1/(2(m0+4)) of Eq. (1).
  * type = QCD_DWF: Ls = N_s >= 2 (fifth-dimension size), M5 (m0 = -M5 in the
- * D_W blocks of Eq. (2)), mf = m of Eq. (2); kappa is ignored. */
+ * D_W blocks of Eq. (2)), mf = m of Eq. (2); kappa, b5 and c5 are ignored.
+ * type = QCD_MOBIUS: the Mobius generalisation of Eq. (2) (Brower, Neff and
+ * Orginos), D = (b5 D_W + 1) - (1 - c5 D_W) S, with D_W = 4 - M5 - H/2 the 4D
+ * Wilson matrix of mass -M5 and (S psi)_s = P_- psi_{s+1} + P_+ psi_{s-1}
+ * (factor -mf across the wall); b5 = 1, c5 = 0 is Eq. (2).  Needs b5 != 0,
+ * alpha = (4 - M5) b5 + 1 != 0 and nonsingular fifth-dimension blocks
+ * A = alpha - beta S, B = b5 + c5 S (beta = 1 - (4 - M5) c5).
+ * b5 and c5 are appended after the Shamir fields. */
 typedef struct {
   int32_t type;
   double kappa;
   int32_t Ls;
   double M5;
   double mf;
+  double b5;
+  double c5;
 } qcd_fermion;
 
 /* method: QCD_BICGSTAB (Wilson) or QCD_CG_NORMAL (CG on Mhat^dag Mhat; the
@@ -205,10 +214,15 @@ qcd_status qcd_field_unpack(const qcd_gauge* g, const qcd_fermion* fermion, qcd_
  *   Wilson:      D_EO = H_eo,  D_OE = H_oe,  MHAT = 1 - kappa^2 H_eo H_oe,
  *                MHAT_DAG = 1 - kappa^2 (H^dag)_eo (H^dag)_oe, FULL = 1 - kappa H.
  *   Domain-wall: D_EO / D_OE = the 4D hop H on every s slice;
- *                MHAT = 1 - 1/4 A^-1 H_eo A^-1 H_oe with A the site-local part
- *                of Eq. (2) (diagonal 5 - M5 plus the s couplings);
- *                MHAT_DAG = 1 - 1/4 (H^dag)_eo A^-dag (H^dag)_oe A^-dag;
- *                FULL = D_DW of Eq. (2).
+ *                MHAT = 1 - 1/4 W H_eo W H_oe with W = B A^-1 the inverse of
+ *                the site-local part A B^-1 of D B^-1 (Shamir: B = 1, W = A^-1
+ *                with A = 5 - M5 plus the s couplings of Eq. (2); Mobius:
+ *                D = A - 1/2 H B, see qcd_fermion);
+ *                MHAT_DAG = 1 - 1/4 (H^dag)_eo W^dag (H^dag)_oe W^dag;
+ *                FULL = D (Eq. (2) for Shamir).
+ *                MHAT is the Schur complement of D B^-1 on the even sites,
+ *                left-multiplied by the inverse of its even-even block; the
+ *                solver works with x' = B x.
  * layout CANON: in/out are full-lattice canonical complex128 fields (device or
  *   host); for D_EO the odd sites of `in` are read and out is written on the
  *   even sites and zeroed on the odd ones (D_OE: the reverse; MHAT: even to
@@ -222,7 +236,8 @@ qcd_status qcd_dslash(const qcd_gauge* g, const qcd_fermion* fermion, qcd_prec p
 /* Solve A x = b for nrhs right-hand sides (A = M for Wilson, D_DW for
  * domain-wall; A^dag with params->dagger), by even-odd preconditioned
  * BiCGStab (Wilson) or CG on Mhat^dag Mhat, then reconstruction of the odd
- * sites.  b, x: canonical complex128, device or host.  info: host array of
+ * sites (domain-wall: of x' = B x, then x = B^-1 x').  b, x: canonical
+ * complex128, device or host.  info: host array of
  * nrhs entries.  Returns QCD_OK when every right-hand side reached tol,
  * QCD_ERR_NOCONV / QCD_ERR_BREAKDOWN / QCD_ERR_NAN otherwise (x then holds the
  * last double-precision iterate). */

@@ -342,21 +342,29 @@ def _block_inv(M):
 
 
 def mobius_mhat(L, bc, Ls, M5, mf, b5, c5, U, psi_even, dagger=False):
-    """Schur operator on the even sites, preconditioned by A^-1:
-    Mhat = 1 - 1/4 A^-1 H_eo B A^-1 H_oe B;  Mhat^dag = 1 - 1/4 B^T H^dag_eo A^-T B^T H^dag_oe A^-T.
+    """Even-odd operator of the Mobius matrix in the variable x' = B x: D B^-1 = A B^-1 - 1/2 H
+    has the form of Eq. (2) with the site-local block A B^-1, whose inverse is W = B A^-1, and
+      Mhat = 1 - 1/4 W H_eo W H_oe,   Mhat^dag = 1 - 1/4 H^dag_eo W^T H^dag_oe W^T
+    (the Schur complement of D B^-1 on the even sites, times the inverse of its even block).
     Returns the even sites (odd sites zero)."""
     A, B = mobius_blocks(Ls, M5, mf, b5, c5)
-    Ai = _block_inv(A)
+    W = np.einsum("satb,tbuc->sauc", B, _block_inv(A))
     par = parity(L)
     pe = _c(psi_even).copy()
     pe[:, par == 1] = 0
     if not dagger:
-        t = _hop5(L, bc, U, _block_apply(B, pe), out_parity=1)
-        t = _hop5(L, bc, U, _block_apply(B, _block_apply(Ai, t)), out_parity=0)
-        out = pe - 0.25 * _block_apply(Ai, t)
+        t = _block_apply(W, _hop5(L, bc, U, pe, out_parity=1))
+        out = pe - 0.25 * _block_apply(W, _hop5(L, bc, U, t, out_parity=0))
     else:
-        t = _hop5(L, bc, U, _block_apply(Ai, pe, True), dagger=True, out_parity=1)
-        t = _hop5(L, bc, U, _block_apply(Ai, _block_apply(B, t, True), True), dagger=True, out_parity=0)
-        out = pe - 0.25 * _block_apply(B, t, True)
+        t = _hop5(L, bc, U, _block_apply(W, pe, True), dagger=True, out_parity=1)
+        out = pe - 0.25 * _hop5(L, bc, U, _block_apply(W, t, True), dagger=True, out_parity=0)
     out[:, par == 1] = 0
     return out
+
+
+def mobius_block(Ls, M5, mf, b5, c5, which, psi, dagger=False):
+    """A, B, B^-1 or W = B A^-1 (which = "A", "B", "Binv", "W") applied to a (Ls, V, 4, 3) field."""
+    A, B = mobius_blocks(Ls, M5, mf, b5, c5)
+    M = {"A": A, "B": B, "Binv": _block_inv(B) if which == "Binv" else None,
+         "W": np.einsum("satb,tbuc->sauc", B, _block_inv(A)) if which == "W" else None}[which]
+    return _block_apply(M, psi, dagger)

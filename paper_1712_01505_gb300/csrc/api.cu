@@ -150,12 +150,21 @@ int check_fermion(const qcd_fermion* f) {
     if (!std::isfinite(f->kappa) || f->kappa <= 0) raise(QCD_ERR_ARG, "kappa must be finite and > 0");
     return 1;
   }
-  if (f->type == QCD_DWF) {
+  if (f->type == QCD_DWF || f->type == QCD_MOBIUS) {
     if (f->Ls < 2 || f->Ls > 64) raise(QCD_ERR_ARG, "Ls = %d must be in [2, 64]", f->Ls);
     if (!std::isfinite(f->M5) || !std::isfinite(f->mf)) raise(QCD_ERR_ARG, "M5 and mf must be finite");
-    if (std::fabs(5.0 - f->M5) < 1e-12) raise(QCD_ERR_ARG, "5 - M5 must be nonzero");
-    double a = 5.0 - f->M5;
-    if (std::fabs(1.0 + f->mf * std::pow(a, -f->Ls)) < 1e-300) raise(QCD_ERR_ARG, "singular fifth-dimension block");
+    if (f->type == QCD_MOBIUS && (!std::isfinite(f->b5) || !std::isfinite(f->c5)))
+      raise(QCD_ERR_ARG, "b5 and c5 must be finite");
+    const DwParams p = dw_params(*f);
+    // A = alpha - beta S and B = b5 + c5 S are inverted in closed form:
+    // (d - e S)^-1 needs d != 0 and 1 + mf (e / d)^Ls != 0
+    auto check_block = [&](double d, double e, const char* what) {
+      if (std::fabs(d) < 1e-12) raise(QCD_ERR_ARG, "singular fifth-dimension block %s (diagonal %g)", what, d);
+      if (std::fabs(1.0 + f->mf * std::pow(e / d, f->Ls)) < 1e-12)
+        raise(QCD_ERR_ARG, "singular fifth-dimension block %s", what);
+    };
+    check_block(p.alpha(), p.beta(), "A");
+    check_block(p.b5, -p.c5, "B");
     return f->Ls;
   }
   raise(QCD_ERR_ARG, "unknown fermion type %d", f->type);
@@ -377,7 +386,7 @@ qcd_status qcd_dslash(const qcd_gauge* gc, const qcd_fermion* fermion, qcd_prec 
     if (nrhs < 1 || nrhs > 64) raise(QCD_ERR_ARG, "nrhs = %d must be in [1, 64]", nrhs);
     cudaStream_t st = (cudaStream_t)stream;
     OpCtx c{g, *fermion, prec};
-    const bool dwf = fermion->type == QCD_DWF;
+    const bool dwf = is_dw(*fermion);
     if (dwf && prec == QCD_DF64 && (op == QCD_OP_FULL || op == QCD_OP_FULL_DAG))
       raise(QCD_ERR_UNSUPPORTED, "the unpreconditioned domain-wall matrix is not available in double-float");
     if (layout == QCD_LAYOUT_INTERNAL) {
@@ -440,9 +449,9 @@ qcd_status qcd_solve(const qcd_gauge* gc, const qcd_fermion* fermion, const qcd_
     if (nrhs < 1 || nrhs > 64) raise(QCD_ERR_ARG, "nrhs = %d must be in [1, 64]", nrhs);
     const qcd_solver_params& p = *params;
     if (p.method != QCD_BICGSTAB && p.method != QCD_CG_NORMAL) raise(QCD_ERR_ARG, "unknown method %d", p.method);
-    if (fermion->type == QCD_DWF && p.method == QCD_BICGSTAB)
+    if (is_dw(*fermion) && p.method == QCD_BICGSTAB)
       raise(QCD_ERR_UNSUPPORTED, "domain-wall needs CG on the normal equations (BiCGStab fails on its spectrum)");
-    if (fermion->type == QCD_DWF && p.dagger) raise(QCD_ERR_UNSUPPORTED, "dagger solves are Wilson only");
+    if (is_dw(*fermion) && p.dagger) raise(QCD_ERR_UNSUPPORTED, "dagger solves are Wilson only");
     if (!(p.tol > 0) || !std::isfinite(p.tol)) raise(QCD_ERR_ARG, "tol must be finite and > 0");
     if (p.inner != QCD_F64 && p.inner != QCD_F32 && p.inner != QCD_F16)
       raise(QCD_ERR_ARG, "inner precision must be QCD_F64, QCD_F32 or QCD_F16 (got %d)", p.inner);

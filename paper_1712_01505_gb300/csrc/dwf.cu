@@ -1,17 +1,18 @@
-// Site-local part of the domain-wall matrix (Eq. (2)) and its inverse.
+// Site-local parts of the domain-wall matrix: Eq. (2) (Shamir) and its Mobius
+// generalisation D = A - 1/2 H B.
 //
-// Writing D_DW = A - H/2 with H the 4D Wilson hop acting identically on every
-// slice s, the block A couples (s, spin) at one 4D site:
-//   (A psi)_s = (5 - M5) psi_s - P_- psi_{s+1} - P_+ psi_{s-1}
-//             + m P_+ psi_{Ls-1} [s = 0] + m P_- psi_0 [s = Ls-1]
+// S is the fifth-dimension chiral shift, (S psi)_s = P_- psi_{s+1} + P_+ psi_{s-1},
+// with factor -m on the terms that cross the wall (s = Ls-1 -> 0 and 0 -> Ls-1);
+// B = b5 + c5 S and A = (4 - M5) B + 1 - S = alpha - beta S with
+// alpha = (4 - M5) b5 + 1, beta = 1 - (4 - M5) c5 (Shamir: B = 1, A = 5 - M5 - S).
 // With gamma_5 = diag(1,1,-1,-1) the projectors P_+- select spins {0,1} and
-// {2,3}.  On the P_+ spins A = a - (lower shift with wrap factor -m), on the
-// P_- spins A = a - (upper shift with the same wrap), a = 5 - M5.  The
-// inverse of a I - (twisted lower shift) has the closed form
-//   (A_+^-1)_{s,s'} = a^(-1-k) * (s >= s' ? 1 : -m) / (1 + m a^-Ls),
-//   k = (s - s') mod Ls,
-// and A_-^-1 is its transpose (as is A_+^-dag; A is real).  Both are applied
-// at every site, colour and spin with Ls real coefficients per output.
+// {2,3}, so every one of these blocks acts on a column (site, colour, spin) of
+// Ls values: on the P_+ spins S is the lower shift T_lo (psi_{s-1}, wrap -m),
+// on the P_- spins the upper shift T_up (psi_{s+1}, wrap -m); S^T = S^dag
+// exchanges the two.  The inverse of alpha - beta T_lo has the closed form
+//   (alpha - beta T_lo)^-1_{s,s'} = beta^k alpha^(-1-k) (s >= s' ? 1 : -m) / den,
+//   k = (s - s') mod Ls,   den = 1 + m (beta / alpha)^Ls,
+// (T_lo^Ls = -m), and that of alpha - beta T_up is its transpose.
 #include <cmath>
 
 #include "common.cuh"
@@ -19,35 +20,107 @@
 
 namespace qcd {
 
+DwParams dw_params(const qcd_fermion& f) {
+  DwParams p{f.Ls, f.M5, f.mf};
+  if (f.type == QCD_MOBIUS) {
+    p.b5 = f.b5;
+    p.c5 = f.c5;
+  }
+  return p;
+}
+
+bool is_dw(const qcd_fermion& f) { return f.type == QCD_DWF || f.type == QCD_MOBIUS; }
+
 namespace {
 
 constexpr int kMaxLs = 64;
 
-// coefficients in the kernel's arithmetic type (no FP64 in the FP32 kernels)
+// A column operator out = post . inv . pre (in) on the (s, spin) columns, every
+// factor optional: pre and post are d + e S, inv is (alpha - beta S)^-1.  The
+// adjoint applies post^T, inv^T, pre^T in that order.  Coefficients in the
+// kernel's arithmetic type (no FP64 in the FP32 kernels).
+enum { kPre = 1, kInv = 2, kPost = 4 };
+
 template <typename R>
-struct AinvCoef {
-  int Ls;
-  R apow[kMaxLs];  // a^(-1-k) / (1 + m a^-Ls)
+struct ColCoef {
+  int Ls, flags;
   R mf;
-  R ainv;  // 1 / a
+  R pre_d, pre_e, post_d, post_e;
+  R ainv, ratio;   // 1 / alpha, beta / alpha
+  R apow[kMaxLs];  // beta^k alpha^(-1-k) / den
 };
 
-// A^-1 per column (site, colour, spin) in O(Ls): on the P_+ spins A is
-// a - (lower shift, wrap -m), so with the first slice from the closed form,
-//   psi_0 = a^-1 chi_0 / den - m sum_{s'>0} a^(-1-(Ls-s')) chi_s' / den,
-// the rest follows by forward substitution psi_s = (chi_s + psi_{s-1}) / a;
-// on the P_- spins (upper shift) the last slice comes from the closed form,
-//   psi_{Ls-1} = a^-1 chi_{Ls-1} / den - m sum_{s'<Ls-1} a^(-2-s') chi_s' / den,
-// and backward substitution psi_s = (chi_s + psi_{s+1}) / a gives the rest.
-// A^dag = A^T exchanges the two recurrences between the chiralities.
+// (d + e T) in place on one column of Ls complex values (stride cs), T = T_lo or T_up
+template <typename R>
+__device__ __forceinline__ void col_mul(R* re, R* im, int cs, int Ls, bool lower, R d, R e, R mf) {
+  const R ew = -mf * e;
+  if (lower) {
+    const R lr = re[(Ls - 1) * cs], li = im[(Ls - 1) * cs];
+    for (int s = Ls - 1; s >= 1; --s) {
+      re[s * cs] = fma(e, re[(s - 1) * cs], d * re[s * cs]);
+      im[s * cs] = fma(e, im[(s - 1) * cs], d * im[s * cs]);
+    }
+    re[0] = fma(ew, lr, d * re[0]);
+    im[0] = fma(ew, li, d * im[0]);
+  } else {
+    const R fr = re[0], fi = im[0];
+    for (int s = 0; s < Ls - 1; ++s) {
+      re[s * cs] = fma(e, re[(s + 1) * cs], d * re[s * cs]);
+      im[s * cs] = fma(e, im[(s + 1) * cs], d * im[s * cs]);
+    }
+    re[(Ls - 1) * cs] = fma(ew, fr, d * re[(Ls - 1) * cs]);
+    im[(Ls - 1) * cs] = fma(ew, fi, d * im[(Ls - 1) * cs]);
+  }
+}
+
+// (alpha - beta T)^-1 in place on one column: the end slice from the closed form,
+// the others by substitution psi_s = chi_s / alpha + (beta / alpha) psi_{s-+1}
+template <typename R>
+__device__ __forceinline__ void col_inv(R* re, R* im, int cs, const ColCoef<R>& c, bool lower) {
+  const int Ls = c.Ls;
+  if (lower) {
+    R pr = c.apow[0] * re[0], pi = c.apow[0] * im[0];
+    for (int sp = 1; sp < Ls; ++sp) {
+      const R w = -c.mf * c.apow[Ls - sp];
+      pr = fma(w, re[sp * cs], pr);
+      pi = fma(w, im[sp * cs], pi);
+    }
+    re[0] = pr;
+    im[0] = pi;
+    for (int s = 1; s < Ls; ++s) {
+      pr = fma(c.ratio, pr, c.ainv * re[s * cs]);
+      pi = fma(c.ratio, pi, c.ainv * im[s * cs]);
+      re[s * cs] = pr;
+      im[s * cs] = pi;
+    }
+  } else {
+    const int l = Ls - 1;
+    R pr = c.apow[0] * re[l * cs], pi = c.apow[0] * im[l * cs];
+    for (int sp = 0; sp < l; ++sp) {
+      const R w = -c.mf * c.apow[sp + 1];
+      pr = fma(w, re[sp * cs], pr);
+      pi = fma(w, im[sp * cs], pi);
+    }
+    re[l * cs] = pr;
+    im[l * cs] = pi;
+    for (int s = l - 1; s >= 0; --s) {
+      pr = fma(c.ratio, pr, c.ainv * re[s * cs]);
+      pi = fma(c.ratio, pi, c.ainv * im[s * cs]);
+      re[s * cs] = pr;
+      im[s * cs] = pi;
+    }
+  }
+}
+
+// out = [x +] scale * (column operator) in.
 // The block stages its SB sites for all Ls slices in shared memory (one HBM
-// read per 5D site), runs the recurrences in place (thread (site, k) owns the
+// read per 5D site), runs the column passes in place (thread (site, k) owns the
 // complex components k, k + blockDim.y, ...), then writes (site, slice) units.
 // block: (SB sites) x (256 / SB); grid: (ceil(Vh/SB), nrhs); dynamic shared
 // memory Ls * 24 * SB reals laid out [s][real][site].
 template <typename R>
-__global__ void __launch_bounds__(256) k_ainv(AinvCoef<R> c, AnyView in, AnyView out, long Vh, int dagger, R scale,
-                       AnyView x, int has_x, const int* stop) {
+__global__ void __launch_bounds__(256) k_col(ColCoef<R> c, AnyView in, AnyView out, long Vh, int dagger, R scale,
+                                             AnyView x, int has_x, const int* stop) {
   if (stop && *stop) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
@@ -76,38 +149,11 @@ __global__ void __launch_bounds__(256) k_ainv(AinvCoef<R> c, AnyView in, AnyView
     R* re = sm + (2 * k) * SB + tx;
     R* im = sm + (2 * k + 1) * SB + tx;
     const bool lower = (k < 6) != (dagger != 0);
-    if (lower) {
-      R pr = c.apow[0] * re[0], pi = c.apow[0] * im[0];
-      for (int sp = 1; sp < Ls; ++sp) {
-        const R w = -c.mf * c.apow[Ls - sp];
-        pr = fma(w, re[sp * cs], pr);
-        pi = fma(w, im[sp * cs], pi);
-      }
-      re[0] = pr;
-      im[0] = pi;
-      for (int s = 1; s < Ls; ++s) {
-        pr = (re[s * cs] + pr) * c.ainv;
-        pi = (im[s * cs] + pi) * c.ainv;
-        re[s * cs] = pr;
-        im[s * cs] = pi;
-      }
-    } else {
-      const int l = Ls - 1;
-      R pr = c.apow[0] * re[l * cs], pi = c.apow[0] * im[l * cs];
-      for (int sp = 0; sp < l; ++sp) {
-        const R w = -c.mf * c.apow[sp + 1];
-        pr = fma(w, re[sp * cs], pr);
-        pi = fma(w, im[sp * cs], pi);
-      }
-      re[l * cs] = pr;
-      im[l * cs] = pi;
-      for (int s = l - 1; s >= 0; --s) {
-        pr = (re[s * cs] + pr) * c.ainv;
-        pi = (im[s * cs] + pi) * c.ainv;
-        re[s * cs] = pr;
-        im[s * cs] = pi;
-      }
-    }
+    const bool first = dagger ? (c.flags & kPost) : (c.flags & kPre);
+    const bool last = dagger ? (c.flags & kPre) : (c.flags & kPost);
+    if (first) col_mul(re, im, cs, Ls, lower, dagger ? c.post_d : c.pre_d, dagger ? c.post_e : c.pre_e, c.mf);
+    if (c.flags & kInv) col_inv(re, im, cs, c, lower);
+    if (last) col_mul(re, im, cs, Ls, lower, dagger ? c.pre_d : c.post_d, dagger ? c.pre_e : c.post_e, c.mf);
   }
   __syncthreads();
   if (cb >= Vh) return;
@@ -128,39 +174,53 @@ __global__ void __launch_bounds__(256) k_ainv(AinvCoef<R> c, AnyView in, AnyView
   }
 }
 
-// out = A in + c * y  (A^dag for dagger)
+// out = (xd + xe S) in + cy (yd + ye S) y, S^T for dagger; one thread per 5D site
 template <typename R>
-__global__ void __launch_bounds__(256) k_ablock(int Ls, R a, R mf, AnyView in, AnyView out, R cy, AnyView y, int has_y,
-                         long Vh, int dagger) {
+__global__ void __launch_bounds__(256) k_ablock(int Ls, R mf, R xd, R xe, AnyView in, AnyView out, R yd, R ye,
+                                                AnyView y, int has_y, long Vh, int dagger) {
   int r = blockIdx.y;
   long cb = blockIdx.x * (long)blockDim.x + threadIdx.x;
   int s = blockIdx.z * blockDim.y + threadIdx.y;
   if (cb >= Vh || s >= Ls) return;
-  Cx<R> v[12], lo[12], up[12];
-  any_load<R>(in, r, (long)s * Vh + cb, v);
-  int sm = s == 0 ? Ls - 1 : s - 1;
-  int spl = s == Ls - 1 ? 0 : s + 1;
-  any_load<R>(in, r, (long)sm * Vh + cb, lo);   // psi_{s-1}
-  any_load<R>(in, r, (long)spl * Vh + cb, up);  // psi_{s+1}
-  // coefficient of psi_{s-1} (lower shift) and psi_{s+1} (upper shift)
-  R flo = (s == 0) ? mf : R(-1);
-  R fup = (s == Ls - 1) ? mf : R(-1);
-  // A: P_+ spins use the lower shift, P_- spins the upper; A^dag swaps them
-  R cp_lo = dagger ? R(0) : flo, cp_up = dagger ? fup : R(0);
-  R cm_lo = dagger ? flo : R(0), cm_up = dagger ? R(0) : fup;
+  const int sm = s == 0 ? Ls - 1 : s - 1;
+  const int spl = s == Ls - 1 ? 0 : s + 1;
+  // S: P_+ spins take psi_{s-1} (factor -m at s = 0), P_- spins psi_{s+1}
+  // (factor -m at s = Ls-1); S^T exchanges the shifts between the chiralities
+  const R flo = (s == 0) ? -mf : R(1);
+  const R fup = (s == Ls - 1) ? -mf : R(1);
+  const R p_lo = dagger ? R(0) : flo, p_up = dagger ? fup : R(0);
+  const R m_lo = dagger ? flo : R(0), m_up = dagger ? R(0) : fup;
   Cx<R> o[12];
+  {
+    Cx<R> v[12], lo[12], up[12];
+    any_load<R>(in, r, (long)s * Vh + cb, v);
+    any_load<R>(in, r, (long)sm * Vh + cb, lo);
+    any_load<R>(in, r, (long)spl * Vh + cb, up);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    R clo = k < 6 ? cp_lo : cm_lo;
-    R cup = k < 6 ? cp_up : cm_up;
-    o[k].re = a * v[k].re + clo * lo[k].re + cup * up[k].re;
-    o[k].im = a * v[k].im + clo * lo[k].im + cup * up[k].im;
+    for (int k = 0; k < 12; ++k) {
+      const R clo = xe * (k < 6 ? p_lo : m_lo);
+      const R cup = xe * (k < 6 ? p_up : m_up);
+      o[k].re = xd * v[k].re + clo * lo[k].re + cup * up[k].re;
+      o[k].im = xd * v[k].im + clo * lo[k].im + cup * up[k].im;
+    }
   }
   if (has_y) {
-    Cx<R> w[12];
-    any_load<R>(y, r, (long)s * Vh + cb, w);
+    Cx<R> v[12], lo[12], up[12];
+    any_load<R>(y, r, (long)s * Vh + cb, v);
+    if (ye != R(0)) {
+      any_load<R>(y, r, (long)sm * Vh + cb, lo);
+      any_load<R>(y, r, (long)spl * Vh + cb, up);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) o[k] = {fma(cy, w[k].re, o[k].re), fma(cy, w[k].im, o[k].im)};
+      for (int k = 0; k < 12; ++k) lo[k] = up[k] = {R(0), R(0)};
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const R clo = ye * (k < 6 ? p_lo : m_lo);
+      const R cup = ye * (k < 6 ? p_up : m_up);
+      o[k].re += yd * v[k].re + clo * lo[k].re + cup * up[k].re;
+      o[k].im += yd * v[k].im + clo * lo[k].im + cup * up[k].im;
+    }
   }
   any_store<R>(out, r, (long)s * Vh + cb, o);
 }
@@ -171,31 +231,44 @@ dim3 grid_for(const Field& f, dim3 blk, int Ls) {
   return dim3((unsigned)((f.Vh + blk.x - 1) / blk.x), f.nrhs, (unsigned)((Ls + blk.y - 1) / blk.y));
 }
 
-}  // namespace
+// host description of a column operator
+struct ColSpec {
+  int flags = 0;
+  double pre_d = 1, pre_e = 0, post_d = 1, post_e = 0;
+  double alpha = 1, beta = 0;  // inverse of alpha - beta S
+};
 
-void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double scale,
-             const Field* x, cudaStream_t st, const int* stop) {
-  if (in.prec == QCD_DF64) {
-    dw_ainv_df(p, in, out, dagger, scale, x, st, stop);
-    return;
+template <typename R>
+ColCoef<R> make_coef(const DwParams& p, const ColSpec& cs) {
+  ColCoef<R> c;
+  c.Ls = p.Ls;
+  c.flags = cs.flags;
+  c.mf = (R)p.mf;
+  c.pre_d = (R)cs.pre_d;
+  c.pre_e = (R)cs.pre_e;
+  c.post_d = (R)cs.post_d;
+  c.post_e = (R)cs.post_e;
+  const double ratio = cs.beta / cs.alpha;
+  const double den = 1.0 + p.mf * std::pow(ratio, p.Ls);
+  c.ainv = (R)(1.0 / cs.alpha);
+  c.ratio = (R)ratio;
+  double w = 1.0 / (cs.alpha * den);
+  for (int k = 0; k < p.Ls; ++k) {
+    c.apow[k] = (R)w;
+    w *= ratio;
   }
+  return c;
+}
+
+void run_col(const DwParams& p, const ColSpec& spec, const Field& in, Field& out, int dagger, double scale,
+             const Field* x, cudaStream_t st, const int* stop) {
   if (p.Ls < 1 || p.Ls > kMaxLs) raise(QCD_ERR_ARG, "Ls must be in [1, %d]", kMaxLs);
   if (in.data == out.data || (x && x->data == out.data))
-    raise(QCD_ERR_ARG, "dw_ainv: output aliases an input");
+    raise(QCD_ERR_ARG, "domain-wall block: output aliases an input");
+  if (in.prec == QCD_DF64 || out.prec == QCD_DF64 || (x && x->prec == QCD_DF64))
+    raise(QCD_ERR_UNSUPPORTED, "this domain-wall block is not available in double-float");
+  if (in.nsites() == 0 || in.nrhs == 0) return;
   AnyView xv = x ? any_view(*x) : any_view(out);
-  AinvCoef<double> c;
-  AinvCoef<float> cf;
-  c.Ls = cf.Ls = p.Ls;
-  c.mf = p.mf;
-  cf.mf = (float)p.mf;
-  double a = 5.0 - p.M5;
-  double den = 1.0 + p.mf * std::pow(a, -p.Ls);
-  for (int k = 0; k < p.Ls; ++k) {
-    c.apow[k] = std::pow(a, -1.0 - k) / den;
-    cf.apow[k] = (float)c.apow[k];
-  }
-  c.ainv = 1.0 / a;
-  cf.ainv = (float)c.ainv;
   const bool dbl = in.prec == QCD_F64 || out.prec == QCD_F64;
   const size_t rb = dbl ? sizeof(double) : sizeof(float);
   // sites per block: as many as fit 96 KB of staging (at least 8)
@@ -206,34 +279,82 @@ void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double 
   dim3 grid((unsigned)((in.Vh + SB - 1) / SB), in.nrhs);
   static bool attr_set = false;
   if (!attr_set) {
-    QCD_CK(cudaFuncSetAttribute(k_ainv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-    QCD_CK(cudaFuncSetAttribute(k_ainv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    QCD_CK(cudaFuncSetAttribute(k_col<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    QCD_CK(cudaFuncSetAttribute(k_col<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
     attr_set = true;
   }
   if (dbl)
-    k_ainv<double><<<grid, blk, smem, st>>>(c, any_view(in), any_view(out), in.Vh, dagger, scale, xv,
-                                            x != nullptr, stop);
+    k_col<double><<<grid, blk, smem, st>>>(make_coef<double>(p, spec), any_view(in), any_view(out), in.Vh, dagger,
+                                           scale, xv, x != nullptr, stop);
   else
-    k_ainv<float><<<grid, blk, smem, st>>>(cf, any_view(in), any_view(out), in.Vh, dagger, (float)scale,
-                                           xv, x != nullptr, stop);
+    k_col<float><<<grid, blk, smem, st>>>(make_coef<float>(p, spec), any_view(in), any_view(out), in.Vh, dagger,
+                                          (float)scale, xv, x != nullptr, stop);
   QCD_LAUNCH_CK();
 }
 
+void blk_coef(const DwParams& p, Blk5 b, double& d, double& e) {
+  switch (b) {
+    case BLK_A: d = p.alpha(); e = -p.beta(); return;
+    case BLK_B: d = p.b5; e = p.c5; return;
+    default: d = 1.0; e = 0.0; return;
+  }
+}
+
+}  // namespace
+
+void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double scale,
+             const Field* x, cudaStream_t st, const int* stop) {
+  if (in.prec == QCD_DF64) {
+    dw_ainv_df(p, in, out, dagger, scale, x, st, stop);
+    return;
+  }
+  ColSpec cs;
+  cs.flags = kInv | (p.mobius() ? kPost : 0);
+  cs.alpha = p.alpha();
+  cs.beta = p.beta();
+  cs.post_d = p.b5;
+  cs.post_e = p.c5;
+  run_col(p, cs, in, out, dagger, scale, x, st, stop);
+}
+
+void dw_binv(const DwParams& p, const Field& in, Field& out, cudaStream_t st) {
+  ColSpec cs;
+  cs.flags = kInv;
+  cs.alpha = p.b5;
+  cs.beta = -p.c5;
+  run_col(p, cs, in, out, 0, 1.0, nullptr, st, nullptr);
+}
+
+void dw_a_binv(const DwParams& p, const Field& in, Field& out, cudaStream_t st) {
+  ColSpec cs;
+  cs.flags = kPost | (p.mobius() ? kInv : 0);
+  cs.alpha = p.b5;
+  cs.beta = -p.c5;
+  cs.post_d = p.alpha();
+  cs.post_e = -p.beta();
+  run_col(p, cs, in, out, 0, 1.0, nullptr, st, nullptr);
+}
+
 void dw_block(const DwParams& p, const Field& in, Field& out, int dagger, double c, const Field* y,
-              cudaStream_t st) {
-  if (in.data == out.data) raise(QCD_ERR_ARG, "dw_block: in and out alias");
+              cudaStream_t st, Blk5 X, Blk5 Y) {
+  if (in.data == out.data || (y && y->data == out.data)) raise(QCD_ERR_ARG, "dw_block: output aliases an input");
   if (in.prec == QCD_DF64 || out.prec == QCD_DF64 || (y && y->prec == QCD_DF64))
-    raise(QCD_ERR_UNSUPPORTED, "the domain-wall block A is not available in double-float");
+    raise(QCD_ERR_UNSUPPORTED, "the domain-wall blocks A and B are not available in double-float");
+  if (in.nsites() == 0 || in.nrhs == 0) return;
+  double xd, xe, yd, ye;
+  blk_coef(p, X, xd, xe);
+  blk_coef(p, Y, yd, ye);
+  yd *= c;
+  ye *= c;
   dim3 blk = block_for(p.Ls);
   dim3 grid = grid_for(in, blk, p.Ls);
   AnyView yv = y ? any_view(*y) : any_view(out);
-  double a = 5.0 - p.M5;
   if (in.prec == QCD_F64 || out.prec == QCD_F64)
-    k_ablock<double><<<grid, blk, 0, st>>>(p.Ls, a, p.mf, any_view(in), any_view(out), c, yv,
+    k_ablock<double><<<grid, blk, 0, st>>>(p.Ls, p.mf, xd, xe, any_view(in), any_view(out), yd, ye, yv,
                                            y != nullptr, in.Vh, dagger);
   else
-    k_ablock<float><<<grid, blk, 0, st>>>(p.Ls, (float)a, (float)p.mf, any_view(in), any_view(out),
-                                          (float)c, yv, y != nullptr, in.Vh, dagger);
+    k_ablock<float><<<grid, blk, 0, st>>>(p.Ls, (float)p.mf, (float)xd, (float)xe, any_view(in), any_view(out),
+                                          (float)yd, (float)ye, yv, y != nullptr, in.Vh, dagger);
   QCD_LAUNCH_CK();
 }
 

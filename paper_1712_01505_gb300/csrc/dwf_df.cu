@@ -1,16 +1,18 @@
-// Double-float inverse of the site-local domain-wall block A (Eq. (2)) for the
-// outer steps of the mixed-precision CG (see wilson_df.cu for the stencil and
-// dfloat.cuh for the arithmetic).
+// Double-float site-local inverse of the domain-wall matrix for the outer steps
+// of the mixed-precision CG (see wilson_df.cu for the stencil and dfloat.cuh for
+// the arithmetic): W = B A^-1 (Shamir, Eq. (2): A^-1), and W^T for the adjoint.
 //
-// Same recurrences as the FP32 / FP64 kernel in dwf.cu: on the P_+ spins
-// A = a - (lower shift, wrap -m), so the first slice comes from the closed form
-//   psi_0 = sum_s' w_s' chi_s',  w_0 = a^-1 / den,  w_s' = -m a^(-1-(Ls-s')) / den,
-// and psi_s = (chi_s + psi_{s-1}) / a for s > 0; on the P_- spins the last slice
-// comes from the closed form with w_s' = -m a^(-2-s') / den (s' < Ls-1),
-// w_{Ls-1} = a^-1 / den, and psi_s = (chi_s + psi_{s+1}) / a downwards; the
-// adjoint exchanges the two chiralities.  den = 1 + m a^-Ls.  The closed-form
-// sums are Dot2 sums of Ls products; every recurrence step is a double-float
-// addition and a double-float product.
+// Same column passes as the FP32 / FP64 kernel in dwf.cu, with A = alpha - beta S,
+// B = b5 + c5 S: on the columns where S is the lower shift (P_+ spins; P_- for
+// the adjoint) the first slice of (A^-1 chi) comes from the closed form
+//   psi_0 = sum_s' w_s' chi_s',  w_0 = 1 / (alpha den),
+//   w_s' = -m beta^(Ls-s') alpha^(-1-(Ls-s')) / den,
+// and psi_s = chi_s / alpha + (beta / alpha) psi_{s-1} for s > 0; on the others
+// the last slice comes from w_{Ls-1} = 1 / (alpha den),
+// w_s' = -m beta^(s'+1) alpha^(-2-s') / den, and the substitution runs
+// downwards; den = 1 + m (beta / alpha)^Ls.  B (before A^-T for the adjoint,
+// after A^-1 otherwise) is d psi_s + e psi_{s-+1}.  The closed-form sums are
+// Dot2 sums of Ls products; every other step is a Dot2 sum of two products.
 #include <cmath>
 
 #include "dfloat.cuh"
@@ -23,15 +25,41 @@ namespace {
 constexpr int kMaxLsDf = 64;
 
 struct AinvDf {
-  int Ls;
+  int Ls, post;      // post: apply B after A^-1 (Mobius)
   F2 wlo[kMaxLsDf];  // closed-form weights of the first slice (lower-shift chirality)
   F2 wup[kMaxLsDf];  // closed-form weights of the last slice (upper-shift chirality)
-  F2 ainv;           // 1 / a
+  F2 ainv, ratio;    // 1 / alpha, beta / alpha
+  F2 bd, be, bew;    // B = bd + be S; bew = -m be (the term across the wall)
 };
 
 F2 split_host(double x) {
   const float h = (float)x;
   return {h, (float)(x - (double)h)};
+}
+
+// (bd + be T) in place on one column of Ls pairs (stride cs)
+__device__ __forceinline__ void col_mul_df(F2* col, int cs, int Ls, bool lower, const AinvDf& c) {
+  if (lower) {
+    const F2 last = col[(Ls - 1) * cs];
+    for (int s = Ls - 1; s >= 1; --s) {
+      Dot d = dot_first(c.bd, col[s * cs]);
+      dot_add(d, c.be, col[(s - 1) * cs]);
+      col[s * cs] = dot_value(d);
+    }
+    Dot d = dot_first(c.bd, col[0]);
+    dot_add(d, c.bew, last);
+    col[0] = dot_value(d);
+  } else {
+    const F2 first = col[0];
+    for (int s = 0; s < Ls - 1; ++s) {
+      Dot d = dot_first(c.bd, col[s * cs]);
+      dot_add(d, c.be, col[(s + 1) * cs]);
+      col[s * cs] = dot_value(d);
+    }
+    Dot d = dot_first(c.bd, col[(Ls - 1) * cs]);
+    dot_add(d, c.bew, first);
+    col[(Ls - 1) * cs] = dot_value(d);
+  }
 }
 
 // block: (SB sites) x (256 / SB); grid (ceil(Vh / SB), nrhs); dynamic shared memory
@@ -68,13 +96,16 @@ __global__ void __launch_bounds__(256) k_ainv_df(AinvDf c, SpinorView<PDF> in, S
   for (int k = threadIdx.y; k < 24; k += blockDim.y) {
     F2* col = sm + k * SB + tx;
     const bool lower = (k < 12) != (dagger != 0);  // spins 0, 1 are reals 0 .. 11
+    if (c.post && dagger) col_mul_df(col, cs, Ls, lower, c);
     if (lower) {
       Dot d = dot_first(c.wlo[0], col[0]);
       for (int sp = 1; sp < Ls; ++sp) dot_add(d, c.wlo[sp], col[sp * cs]);
       F2 p = dot_value(d);
       col[0] = p;
       for (int s = 1; s < Ls; ++s) {
-        p = dot_value(dot_first(c.ainv, df_add(col[s * cs], p)));
+        Dot e = dot_first(c.ainv, col[s * cs]);
+        dot_add(e, c.ratio, p);
+        p = dot_value(e);
         col[s * cs] = p;
       }
     } else {
@@ -84,10 +115,13 @@ __global__ void __launch_bounds__(256) k_ainv_df(AinvDf c, SpinorView<PDF> in, S
       F2 p = dot_value(d);
       col[l * cs] = p;
       for (int s = l - 1; s >= 0; --s) {
-        p = dot_value(dot_first(c.ainv, df_add(col[s * cs], p)));
+        Dot e = dot_first(c.ainv, col[s * cs]);
+        dot_add(e, c.ratio, p);
+        p = dot_value(e);
         col[s * cs] = p;
       }
     }
+    if (c.post && !dagger) col_mul_df(col, cs, Ls, lower, c);
   }
   __syncthreads();
   if (cb >= Vh) return;
@@ -134,16 +168,23 @@ void dw_ainv_df(const DwParams& p, const Field& in, Field& out, int dagger, doub
   if (in.nsites() == 0 || in.nrhs == 0) return;
   AinvDf c;
   c.Ls = p.Ls;
-  const double a = 5.0 - p.M5;
-  const double den = 1.0 + p.mf * std::pow(a, -p.Ls);
+  c.post = p.mobius();
+  const double alpha = p.alpha(), ratio = p.beta() / alpha;
+  const double den = 1.0 + p.mf * std::pow(ratio, p.Ls);
   const int Ls = p.Ls;
+  // apow[k] = beta^k alpha^(-1-k) / den
+  auto apow = [&](int k) { return std::pow(ratio, k) / (alpha * den); };
   for (int s = 0; s < Ls; ++s) {
-    // lower shift: w_0 = a^-1 / den, w_s' = -m a^(-1-(Ls-s')) / den
-    c.wlo[s] = split_host(s == 0 ? 1.0 / (a * den) : -p.mf * std::pow(a, -1.0 - (Ls - s)) / den);
-    // upper shift: w_{Ls-1} = a^-1 / den, w_s' = -m a^(-2-s') / den
-    c.wup[s] = split_host(s == Ls - 1 ? 1.0 / (a * den) : -p.mf * std::pow(a, -2.0 - s) / den);
+    // lower shift: w_0 = apow(0), w_s' = -m apow(Ls - s')
+    c.wlo[s] = split_host(s == 0 ? apow(0) : -p.mf * apow(Ls - s));
+    // upper shift: w_{Ls-1} = apow(0), w_s' = -m apow(s' + 1)
+    c.wup[s] = split_host(s == Ls - 1 ? apow(0) : -p.mf * apow(s + 1));
   }
-  c.ainv = split_host(1.0 / a);
+  c.ainv = split_host(1.0 / alpha);
+  c.ratio = split_host(ratio);
+  c.bd = split_host(p.b5);
+  c.be = split_host(p.c5);
+  c.bew = split_host(-p.mf * p.c5);
   int SB = 32;
   while (SB > 8 && (size_t)Ls * 24 * SB * sizeof(F2) > 96 * 1024) SB /= 2;
   const size_t smem = (size_t)Ls * 24 * SB * sizeof(F2);

@@ -153,19 +153,37 @@ unsigned df_norm2_blocks(long n);
 void df_norm2_partials(const Field& x, double* partial, unsigned nb, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- domain wall (dwf.cu)
+// Shamir (Eq. (2)) and Mobius domain-wall: D = A - 1/2 H B with the site-local
+// blocks B = b5 + c5 S and A = (4 - M5) B + 1 - S = alpha - beta S, S the
+// fifth-dimension chiral shift (P_- from s+1, P_+ from s-1, -mf across the wall).
+// Shamir is b5 = 1, c5 = 0 (B = 1, A = 5 - M5 - S).  The solver works with
+// x' = B x, for which D B^-1 = A B^-1 - 1/2 H has the Shamir structure with the
+// site-local inverse W = B A^-1.
 struct DwParams {
   int Ls;
   double M5, mf;
+  double b5 = 1.0, c5 = 0.0;
+  bool mobius() const { return !(b5 == 1.0 && c5 == 0.0); }
+  double alpha() const { return (4.0 - M5) * b5 + 1.0; }
+  double beta() const { return 1.0 - (4.0 - M5) * c5; }
 };
-// out = [x +] c * A^-1 in (A^-dag for dagger), per site over (s, spin)
+DwParams dw_params(const qcd_fermion& f);
+bool is_dw(const qcd_fermion& f);  // QCD_DWF or QCD_MOBIUS
+// out = [x +] c * W in, W = B A^-1 (dagger: W^T = A^-T B^T); A^-1 for Shamir
 void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double c, const Field* x,
              cudaStream_t st, const int* stop = nullptr);
 // the same on double-float fields (dwf_df.cu; dw_ainv dispatches to it)
 void dw_ainv_df(const DwParams& p, const Field& in, Field& out, int dagger, double c, const Field* x,
                 cudaStream_t st, const int* stop = nullptr);
-// out = A in + c * y  (y may be null), A^dag for dagger
+// out = B^-1 in (the physical solution from x'); FP32 / FP64
+void dw_binv(const DwParams& p, const Field& in, Field& out, cudaStream_t st);
+// out = A B^-1 in (the full residual from the even-odd one); A for Shamir
+void dw_a_binv(const DwParams& p, const Field& in, Field& out, cudaStream_t st);
+// site-local blocks of dw_block
+enum Blk5 { BLK_ONE = 0, BLK_A = 1, BLK_B = 2 };
+// out = X in + c * Y y (y may be null), X, Y in {1, A, B}; X^T, Y^T for dagger
 void dw_block(const DwParams& p, const Field& in, Field& out, int dagger, double c, const Field* y,
-              cudaStream_t st);
+              cudaStream_t st, Blk5 X = BLK_A, Blk5 Y = BLK_ONE);
 
 // ----------------------------------------------------------------------------- BLAS (blas.cu)
 void blas_zero(Field& f, cudaStream_t st);

@@ -627,6 +627,8 @@ struct Solver {
              prm.method, inner, nrhs, ls, prm.dagger, f.type, f.kappa, f.M5, f.mf, f.Ls, g->ws.generation, k,
              (void*)sc, (void*)ctl, (void*)partial, (void*)partial2, r.data, p.data, v.data, s.data, t.data, q.data,
              w.data, rt.data);
+    const DwParams dp = dw_params(f);  // b5, c5 of a Mobius operator (1, 0 otherwise)
+    snprintf(buf + strlen(buf), sizeof buf - strlen(buf), " b%a c%a", dp.b5, dp.c5);
     return std::string(buf) + " x" + std::to_string((uintptr_t)xin.data);
   }
 
@@ -701,14 +703,14 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   S.f = f;
   S.prm = prm;
   S.nrhs = nrhs;
-  S.ls = f.type == QCD_DWF ? f.Ls : 1;
+  S.ls = is_dw(f) ? f.Ls : 1;
   S.inner = prm.inner;
   S.xprec = prm.inner == QCD_F64 ? QCD_F64 : QCD_F32;
   S.st = st;
   S.op64 = {g, f, QCD_F64};
   S.opin = {g, f, prm.inner};
   const int ls = S.ls;
-  const bool dwf = f.type == QCD_DWF;
+  const bool dwf = is_dw(f);
   const int dag = prm.dagger;
   // default reliable-update factor: the FP32 recursion stays accurate over two decades,
   // the FP16 one over one
@@ -780,7 +782,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   blas_norm2(S.b_e, bn_e.data(), st, g);
   blas_norm2(S.b_o, bn_o.data(), st, g);
   for (int r = 0; r < nrhs; ++r) bnorm[r] = std::sqrt(bn_e[r] + bn_o[r]);
-  DwParams dp{f.Ls, f.M5, f.mf};
+  const DwParams dp = dw_params(f);
   if (dfo) {
     blas_copy(S.b_e, be_d, st);
     blas_copy(S.b_o, bo_d, st);
@@ -795,15 +797,19 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     // bhat = b_e + kappa H_eo b_o
     hop(g, S.b_o, S.bh, 0, dag, f.kappa, &S.b_e, st);
   } else {
-    // bhat = A^-1 (b_e + 1/2 H_eo A^-1 b_o)
+    // bhat = W (b_e + 1/2 H_eo W b_o), W = B A^-1 (A^-1 for Shamir)
     dw_ainv(dp, S.b_o, S.t64, 0, 1.0, nullptr, st);
     hop(g, S.t64, S.u64, 0, 0, 0.5, &S.b_e, st);
     dw_ainv(dp, S.u64, S.bh, 0, 1.0, nullptr, st);
   }
-  if (prm.x0_given)
+  if (prm.x0_given && dwf && dp.mobius()) {
+    pack_field(lat, 0, x, S.t64, st);
+    dw_block(dp, S.t64, S.x64, 0, 0.0, nullptr, st, BLK_B);  // x' = B x
+  } else if (prm.x0_given) {
     pack_field(lat, 0, x, S.x64, st);
-  else
+  } else {
     blas_zero(S.x64, st);
+  }
   if (dfo) {
     if (prm.x0_given)
       blas_copy(S.x64, x_d, st);
@@ -812,7 +818,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   }
 
   // |b - A x| on the full system from the even-odd residual rhat = bhat - Mhat x_e:
-  // Wilson: (rhat, 0);  DWF: (A rhat, 0)  (exact reconstruction of x_o)
+  // Wilson: (rhat, 0);  DWF: (A B^-1 rhat, 0)  (exact reconstruction of x_o)
   std::vector<double> rn(nrhs), rfull(nrhs);
   auto true_residual = [&](bool x_is_zero) {
     if (dfo) {
@@ -828,7 +834,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
       }
       if (dwf) {  // |A rhat| (to FP64 for the block A; it decides no more than the stop)
         blas_copy(t_d, S.t64, st);
-        dw_block(dp, S.t64, S.u64, 0, 0.0, nullptr, st);
+        dw_a_binv(dp, S.t64, S.u64, st);
         blas_norm2(S.u64, rfull.data(), st, g);
       } else {
         blas_norm2(t_d, rfull.data(), st, g);
@@ -845,7 +851,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
       blas_axpby(1.0, S.bh, -1.0, S.t64, st);  // t64 = bhat - Mhat x
     }
     if (dwf) {
-      dw_block(dp, S.t64, S.u64, 0, 0.0, nullptr, st);
+      dw_a_binv(dp, S.t64, S.u64, st);
       blas_norm2(S.u64, rfull.data(), st, g);
     } else {
       blas_norm2(S.t64, rfull.data(), st, g);
@@ -1039,16 +1045,22 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     blas_norm2(S.bh, ro_.data(), st, g);
   } else {
     if (dfo) {
-      hop(g, x_d, u_d, 1, 0, 0.5, &bo_d, st);  // x_o = A^-1 (b_o + 1/2 H_oe x_e)
+      hop(g, x_d, u_d, 1, 0, 0.5, &bo_d, st);  // x'_o = W (b_o + 1/2 H_oe x'_e)
       dw_ainv(dp, u_d, t_d, 0, 1.0, nullptr, st);
       blas_copy(x_d, S.x64, st);
       blas_copy(t_d, S.t64, st);
     } else {
-      hop(g, S.x64, S.u64, 1, 0, 0.5, &S.b_o, st);  // x_o = A^-1 (b_o + 1/2 H_oe x_e)
+      hop(g, S.x64, S.u64, 1, 0, 0.5, &S.b_o, st);  // x'_o = W (b_o + 1/2 H_oe x'_e)
       dw_ainv(dp, S.u64, S.t64, 0, 1.0, nullptr, st);
     }
-    unpack_field(lat, 0, S.x64, x, st);
-    unpack_field(lat, 1, S.t64, x, st);
+    if (dp.mobius()) {  // x = B^-1 x'
+      dw_binv(dp, S.x64, S.r64, st);
+      dw_binv(dp, S.t64, S.bh, st);
+      xe = S.r64;
+      xo = S.bh;
+    }
+    unpack_field(lat, 0, xe, x, st);
+    unpack_field(lat, 1, xo, x, st);
     // true residual on the full system, both parities
     apply_full_parity(S.op64, xe, xo, S.u64, 0, dag, st, "res");
     blas_axpby(1.0, S.b_e, -1.0, S.u64, st);

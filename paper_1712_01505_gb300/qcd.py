@@ -30,7 +30,7 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_OOM", "ERR_NOCONV", "ERR_BREAK
 F64, F32, F16, DF64 = 0, 1, 2, 3
 PREC = {"f64": F64, "f32": F32, "f16": F16, "df64": DF64, F64: F64, F32: F32, F16: F16, DF64: DF64}
 # qcd_fermion_type
-WILSON, DWF = 0, 1
+WILSON, DWF, MOBIUS = 0, 1, 2
 # qcd_op
 D_EO, D_OE, MHAT, MHAT_DAG, FULL, FULL_DAG = range(6)
 OPS = {"D_EO": D_EO, "D_OE": D_OE, "MHAT": MHAT, "MHAT_DAG": MHAT_DAG, "FULL": FULL, "FULL_DAG": FULL_DAG}
@@ -59,7 +59,8 @@ class Geom(ctypes.Structure):
 
 class Fermion(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int32), ("kappa", ctypes.c_double), ("Ls", ctypes.c_int32),
-                ("M5", ctypes.c_double), ("mf", ctypes.c_double)]
+                ("M5", ctypes.c_double), ("mf", ctypes.c_double), ("b5", ctypes.c_double),
+                ("c5", ctypes.c_double)]
 
 
 class SolverParams(ctypes.Structure):
@@ -152,12 +153,17 @@ def _stream(stream):
 
 def wilson(kappa: float) -> Fermion:
     """Wilson fermion, Eq. (1), hopping parameter kappa = 1/(2(m0+4))."""
-    return Fermion(WILSON, float(kappa), 0, 0.0, 0.0)
+    return Fermion(WILSON, float(kappa), 0, 0.0, 0.0, 0.0, 0.0)
 
 
 def dwf(Ls: int, M5: float, mf: float) -> Fermion:
     """Domain-wall fermion, Eq. (2): N_s = Ls, m0 = -M5, quark mass mf."""
-    return Fermion(DWF, 0.0, int(Ls), float(M5), float(mf))
+    return Fermion(DWF, 0.0, int(Ls), float(M5), float(mf), 1.0, 0.0)
+
+
+def mobius(Ls: int, M5: float, mf: float, b5: float, c5: float) -> Fermion:
+    """Mobius domain-wall fermion: D = (b5 D_W + 1) - (1 - c5 D_W) S, Eq. (2) at b5 = 1, c5 = 0."""
+    return Fermion(MOBIUS, 0.0, int(Ls), float(M5), float(mf), float(b5), float(c5))
 
 
 def kernel_launches() -> int:

@@ -39,6 +39,7 @@ def test_struct_layouts_match_header():
     # field order and C types of the ABI structs (offsets as a C compiler lays them out)
     assert ctypes.sizeof(qcd.Geom) == 36
     assert qcd.Fermion.kappa.offset == 8 and qcd.Fermion.Ls.offset == 16 and qcd.Fermion.mf.offset == 32
+    assert qcd.Fermion.c5.offset == 48 and ctypes.sizeof(qcd.Fermion) == 56
     assert qcd.SolverParams.tol.offset == 8 and qcd.SolverParams.delta.offset == 24
     assert qcd.SolverParams.outer.offset == 48 and ctypes.sizeof(qcd.SolverParams) == 56
     assert ctypes.sizeof(qcd.SolveInfo) == 32

@@ -1,7 +1,7 @@
 """Pins of the oracle's Mobius domain-wall operator D = D_W B + 1 - S (B = b5 + c5 S):
 Eq. (2) at b5 = 1, c5 = 0; the adjoint and gamma5 R5 hermiticity (c5 = 0); the free spectrum in
 momentum space; the induced 4D overlap operator (polar sign approximation), which fixes the order
-of D_W and the s-hop; the even-odd operator against the dense Schur complement; a dense solve."""
+of D_W and the s-hop; the even-odd operator against the dense Schur complement of D B^-1; the blocks; a dense solve."""
 import numpy as np
 
 from oracle import oracle as ora
@@ -128,6 +128,8 @@ def test_effective_4d_operator_is_the_polar_sign_approximation():
 
 
 def test_even_odd_operator_is_the_schur_complement():
+    """Mhat is the Schur complement of D' = D B^-1 on the even sites, times (D'_ee)^-1; and
+    B_e^-1 Mhat B_e is the Schur complement of D itself, times (D_ee)^-1 (the two are similar)."""
     L, Ls, b5, c5 = (2, 2, 2, 4), 4, 1.5, 0.5
     V = int(np.prod(L))
     U = inputs.gauge_field(L, 0.3, 4)
@@ -135,15 +137,35 @@ def test_even_odd_operator_is_the_schur_complement():
     shape = (Ls, V, 4, 3)
     n = Ls * V * 12
     D = _dense(lambda e: ora.mobius(L, BC, Ls, M5, MF, b5, c5, U, e.reshape(shape)).reshape(n), n)
+    B = _dense(lambda e: ora.mobius_block(Ls, M5, MF, b5, c5, "B", e.reshape(shape)).reshape(n), n)
     mask = np.broadcast_to(par[None, :, None, None], shape).reshape(n)
     e, o = np.flatnonzero(mask == 0), np.flatnonzero(mask == 1)
-    Dee, Deo, Doe, Doo = D[np.ix_(e, e)], D[np.ix_(e, o)], D[np.ix_(o, e)], D[np.ix_(o, o)]
-    schur = np.linalg.solve(Dee, Dee - Deo @ np.linalg.solve(Doo, Doe))  # A^-1 (D_ee - D_eo D_oo^-1 D_oe)
+
+    def schur(M):
+        Mee, Meo, Moe, Moo = M[np.ix_(e, e)], M[np.ix_(e, o)], M[np.ix_(o, e)], M[np.ix_(o, o)]
+        return np.linalg.solve(Mee, Mee - Meo @ np.linalg.solve(Moo, Moe))
+
+    mhat = schur(D @ np.linalg.inv(B))
+    Be = B[np.ix_(e, e)]
+    assert np.abs(np.linalg.solve(Be, mhat @ Be) - schur(D)).max() < 1e-11
     psi = inputs.gaussian_source(shape, 5)
     for dag in (False, True):
         got = ora.mobius_mhat(L, BC, Ls, M5, MF, b5, c5, U, psi, dagger=dag).reshape(n)[e]
-        want = (schur.conj().T if dag else schur) @ psi.reshape(n)[e]
+        want = (mhat.conj().T if dag else mhat) @ psi.reshape(n)[e]
         assert np.allclose(got, want, atol=1e-12)
+
+
+def test_blocks():
+    """B^-1 B = 1, W A = B, and A, B are the site-local parts of D (D = A - 1/2 H B)."""
+    L, Ls, b5, c5 = (2, 2, 2, 2), 6, 1.5, 0.5
+    V = int(np.prod(L))
+    psi = inputs.gaussian_source((Ls, V, 4, 3), 9)
+    blk = lambda w, v, dag=False: ora.mobius_block(Ls, M5, MF, b5, c5, w, v, dag)
+    for dag in (False, True):
+        assert np.abs(blk("Binv", blk("B", psi, dag), dag) - psi).max() < 1e-13
+    assert np.abs(blk("W", blk("A", psi)) - blk("B", psi)).max() < 1e-13
+    zero = np.zeros((4, V, 3, 3), dtype=complex)  # H = 0 without links
+    assert np.abs(ora.mobius(L, BC, Ls, M5, MF, b5, c5, zero, psi) - blk("A", psi)).max() < 1e-14
 
 
 def test_dense_solve():
