@@ -3,7 +3,8 @@
 * dwf:     domain-wall 16^3 x 32 x Ls=16, M5 = 1.8, mf = 0.02, eps = 0.2 (seed 3), Gaussian
            source (seed 0): the fifth-dimension hop in FP32 and FP16, and CG on Mhat^dag Mhat
            with FP16 / FP32 inner iterations + FP64 or double-float outer steps against the
-           plain FP64 CG, to 1e-10; the same for the Mobius operator with b5 = 1.5, c5 = 0.5.
+           plain FP64 CG, to 1e-10; the same for the Mobius operator with b5 = 1.5, c5 = 0.5;
+           BiCGStab on the domain-wall system; the hop as Ls launches of the 4D hop.
 * batched: Wilson 24^3 x 48, kappa = 0.124, eps = 0.2 (seed 4), the 12 spin-colour point
            sources at one random site (seed 0): one 12-rhs solve (shared link loads, graph
            chunks, tuned tiles) against 12 single-rhs solves, FP32 inner + FP64, to 1e-10.
@@ -79,6 +80,23 @@ def run_dwf(args):
         hop[prec] = {"hop_ms": round(ms, 4), "hop_gflops": round(metrics.HOP_FLOP_SITE * Vh * Ls / ms / 1e6, 1),
                      "hop_gbs": round(alg / ms / 1e6, 1), "hop_frac": round(alg / ms / 1e6 / _peak(), 4),
                      "mhat_ms": round(ms_m, 4)}
+    # repeated-4D comparison (Sec. II B 2, the first option): the fifth-dimension hop as Ls launches
+    # of the 4D Wilson hop, each on one slice (links re-read per slice) against one launch over
+    # all slices (links loaded once per site for every slice)
+    fw = qcd.wilson(0.125)
+    nb1 = qcd.field_bytes(g, fw, "f32")
+    a1 = [torch.empty(nb1, dtype=torch.uint8, device=dev) for _ in range(Ls)]
+    o1 = [torch.empty(nb1, dtype=torch.uint8, device=dev) for _ in range(Ls)]
+    for s_ in range(Ls):
+        qcd.field_pack(g, fw, "f32", 1, bd[s_], a1[s_])
+
+    def rep4d():
+        for s_ in range(Ls):
+            qcd.dslash(g, fw, "D_EO", a1[s_], o1[s_], prec="f32", layout=qcd.INTERNAL)
+
+    hop["f32"]["repeated_4d_ms"] = round(_time_launches(rep4d, n=10), 4)
+    hop["f32"]["fused_5d_speedup"] = round(hop["f32"]["repeated_4d_ms"] / hop["f32"]["hop_ms"], 3)
+    del a1, o1
     res = {}
     # inner precision / outer precision of the mixed solves; "f64" is the plain FP64 CG
     for name, inner, outer in (("f16", "f16", "f64"), ("f32", "f32", "f64"), ("f16_df", "f16", "df64"),
@@ -94,6 +112,18 @@ def run_dwf(args):
         torch.cuda.synchronize()
         res[name] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "iters": info[0]["iters"],
                      "updates": info[0]["outer_updates"], "true_resid": info[0]["true_resid"]}
+    # BiCGStab on the same system (Sec. II C: the paper's reason for CG here), capped at 4x CG's
+    # iteration count
+    kw = dict(method=qcd.BICGSTAB, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32, outer="df64",
+              maxiter=4 * res["f32_df"]["iters"])
+    x = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info, st = qcd.solve(g, f, bd, x, check=False, **kw)
+    torch.cuda.synchronize()
+    bicg = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "iters": info[0]["iters"],
+            "maxiter": kw["maxiter"], "converged": bool(info[0]["converged"]),
+            "status": qcd.STATUS_NAMES[st], "true_resid": info[0]["true_resid"]}
     # Mobius (b5 = 1.5, c5 = 0.5: the Shamir kernel scaled by b5 + c5 = 2) on the same lattice
     fm = qcd.mobius(Ls, M5, mf, 1.5, 0.5)
     nb = qcd.field_bytes(g, fm, "f32")
@@ -116,7 +146,7 @@ def run_dwf(args):
                      "updates": info[0]["outer_updates"], "true_resid": info[0]["true_resid"]}
     mob["speedup_f32_df_vs_f64"] = round(mob["f64"]["ms"] / mob["f32_df"]["ms"], 3)
     out = {"workload": "dwf_16x16x16x32_Ls16_M5_1.8_mf0.02", "hop": hop, "cg": res,
-           "mobius_b5_1.5_c5_0.5": mob,
+           "bicgstab_f32_df": bicg, "mobius_b5_1.5_c5_0.5": mob,
            "note": "cg keys: inner precision, _df = double-float outer steps (else IEEE FP64)",
            "speedup_f16_vs_f64": round(res["f64"]["ms"] / res["f16"]["ms"], 3),
            "speedup_f32_vs_f64": round(res["f64"]["ms"] / res["f32"]["ms"], 3),

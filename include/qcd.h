@@ -132,8 +132,10 @@ typedef struct {
   double c5;
 } qcd_fermion;
 
-/* method: QCD_BICGSTAB (Wilson) or QCD_CG_NORMAL (CG on Mhat^dag Mhat; the
- *   only choice for domain-wall, whose spectrum defeats BiCGStab, Sec. II C).
+/* method: QCD_BICGSTAB (the paper's choice for Wilson) or QCD_CG_NORMAL (CG on
+ *   Mhat^dag Mhat; its choice for domain-wall, whose spectrum reaches into the
+ *   left half plane, Sec. II C).  BiCGStab on domain-wall runs, and reports
+ *   QCD_ERR_NOCONV / QCD_ERR_BREAKDOWN when it does not reach tol.
  * tol: target |b - A x| / |b| on the full, unpreconditioned system.
  * maxiter: cap on inner Krylov iterations (summed over restarts).
  * inner: precision of the inner iterations (QCD_F64: plain double solve;

@@ -449,8 +449,6 @@ qcd_status qcd_solve(const qcd_gauge* gc, const qcd_fermion* fermion, const qcd_
     if (nrhs < 1 || nrhs > 64) raise(QCD_ERR_ARG, "nrhs = %d must be in [1, 64]", nrhs);
     const qcd_solver_params& p = *params;
     if (p.method != QCD_BICGSTAB && p.method != QCD_CG_NORMAL) raise(QCD_ERR_ARG, "unknown method %d", p.method);
-    if (is_dw(*fermion) && p.method == QCD_BICGSTAB)
-      raise(QCD_ERR_UNSUPPORTED, "domain-wall needs CG on the normal equations (BiCGStab fails on its spectrum)");
     if (is_dw(*fermion) && p.dagger) raise(QCD_ERR_UNSUPPORTED, "dagger solves are Wilson only");
     if (!(p.tol > 0) || !std::isfinite(p.tol)) raise(QCD_ERR_ARG, "tol must be finite and > 0");
     if (p.inner != QCD_F64 && p.inner != QCD_F32 && p.inner != QCD_F16)
