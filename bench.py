@@ -52,7 +52,8 @@ BYTES_SITE_FP32 = {r: int(metrics.hop_compulsory_bytes("f32", r)) for r in (12, 
 BYTES_SITE_FP64 = int(metrics.hop_compulsory_bytes("f64", 18))
 WORKLOAD = "wilson_32x32x32x64_kappa0.125_eps0.2_z2"
 PROFILE = os.path.join(ROOT, "profiles", "wilson_dslash_fp32_32x32x32x64.md")
-KERNEL_SOURCES = ["paper_1712_01505_gb300/csrc/wilson.cu", "paper_1712_01505_gb300/csrc/common.cuh"]
+KERNEL_SOURCES = ["paper_1712_01505_gb300/csrc/wilson.cu", "paper_1712_01505_gb300/csrc/stencil.cuh",
+                  "paper_1712_01505_gb300/csrc/common.cuh"]
 
 
 def peaks():

@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "dwf_col.cuh"
 #include "internal.h"
 
 namespace qcd {
@@ -33,84 +34,7 @@ bool is_dw(const qcd_fermion& f) { return f.type == QCD_DWF || f.type == QCD_MOB
 
 namespace {
 
-constexpr int kMaxLs = 64;
-
-// A column operator out = post . inv . pre (in) on the (s, spin) columns, every
-// factor optional: pre and post are d + e S, inv is (alpha - beta S)^-1.  The
-// adjoint applies post^T, inv^T, pre^T in that order.  Coefficients in the
-// kernel's arithmetic type (no FP64 in the FP32 kernels).
-enum { kPre = 1, kInv = 2, kPost = 4 };
-
-template <typename R>
-struct ColCoef {
-  int Ls, flags;
-  R mf;
-  R pre_d, pre_e, post_d, post_e;
-  R ainv, ratio;   // 1 / alpha, beta / alpha
-  R apow[kMaxLs];  // beta^k alpha^(-1-k) / den
-};
-
-// (d + e T) in place on one column of Ls complex values (stride cs), T = T_lo or T_up
-template <typename R>
-__device__ __forceinline__ void col_mul(R* re, R* im, int cs, int Ls, bool lower, R d, R e, R mf) {
-  const R ew = -mf * e;
-  if (lower) {
-    const R lr = re[(Ls - 1) * cs], li = im[(Ls - 1) * cs];
-    for (int s = Ls - 1; s >= 1; --s) {
-      re[s * cs] = fma(e, re[(s - 1) * cs], d * re[s * cs]);
-      im[s * cs] = fma(e, im[(s - 1) * cs], d * im[s * cs]);
-    }
-    re[0] = fma(ew, lr, d * re[0]);
-    im[0] = fma(ew, li, d * im[0]);
-  } else {
-    const R fr = re[0], fi = im[0];
-    for (int s = 0; s < Ls - 1; ++s) {
-      re[s * cs] = fma(e, re[(s + 1) * cs], d * re[s * cs]);
-      im[s * cs] = fma(e, im[(s + 1) * cs], d * im[s * cs]);
-    }
-    re[(Ls - 1) * cs] = fma(ew, fr, d * re[(Ls - 1) * cs]);
-    im[(Ls - 1) * cs] = fma(ew, fi, d * im[(Ls - 1) * cs]);
-  }
-}
-
-// (alpha - beta T)^-1 in place on one column: the end slice from the closed form,
-// the others by substitution psi_s = chi_s / alpha + (beta / alpha) psi_{s-+1}
-template <typename R>
-__device__ __forceinline__ void col_inv(R* re, R* im, int cs, const ColCoef<R>& c, bool lower) {
-  const int Ls = c.Ls;
-  if (lower) {
-    R pr = c.apow[0] * re[0], pi = c.apow[0] * im[0];
-    for (int sp = 1; sp < Ls; ++sp) {
-      const R w = -c.mf * c.apow[Ls - sp];
-      pr = fma(w, re[sp * cs], pr);
-      pi = fma(w, im[sp * cs], pi);
-    }
-    re[0] = pr;
-    im[0] = pi;
-    for (int s = 1; s < Ls; ++s) {
-      pr = fma(c.ratio, pr, c.ainv * re[s * cs]);
-      pi = fma(c.ratio, pi, c.ainv * im[s * cs]);
-      re[s * cs] = pr;
-      im[s * cs] = pi;
-    }
-  } else {
-    const int l = Ls - 1;
-    R pr = c.apow[0] * re[l * cs], pi = c.apow[0] * im[l * cs];
-    for (int sp = 0; sp < l; ++sp) {
-      const R w = -c.mf * c.apow[sp + 1];
-      pr = fma(w, re[sp * cs], pr);
-      pi = fma(w, im[sp * cs], pi);
-    }
-    re[l * cs] = pr;
-    im[l * cs] = pi;
-    for (int s = l - 1; s >= 0; --s) {
-      pr = fma(c.ratio, pr, c.ainv * re[s * cs]);
-      pi = fma(c.ratio, pi, c.ainv * im[s * cs]);
-      re[s * cs] = pr;
-      im[s * cs] = pi;
-    }
-  }
-}
+using namespace dwcol;
 
 // out = [x +] scale * (column operator) in.
 // The block stages its SB sites for all Ls slices in shared memory (one HBM
@@ -148,12 +72,7 @@ __global__ void __launch_bounds__(256) k_col(ColCoef<R> c, AnyView in, AnyView o
   for (int k = threadIdx.y; k < 12; k += blockDim.y) {
     R* re = sm + (2 * k) * SB + tx;
     R* im = sm + (2 * k + 1) * SB + tx;
-    const bool lower = (k < 6) != (dagger != 0);
-    const bool first = dagger ? (c.flags & kPost) : (c.flags & kPre);
-    const bool last = dagger ? (c.flags & kPre) : (c.flags & kPost);
-    if (first) col_mul(re, im, cs, Ls, lower, dagger ? c.post_d : c.pre_d, dagger ? c.post_e : c.pre_e, c.mf);
-    if (c.flags & kInv) col_inv(re, im, cs, c, lower);
-    if (last) col_mul(re, im, cs, Ls, lower, dagger ? c.pre_d : c.post_d, dagger ? c.pre_e : c.post_e, c.mf);
+    col_apply(re, im, cs, c, (k < 6) != (dagger != 0), dagger);
   }
   __syncthreads();
   if (cb >= Vh) return;
@@ -231,35 +150,6 @@ dim3 grid_for(const Field& f, dim3 blk, int Ls) {
   return dim3((unsigned)((f.Vh + blk.x - 1) / blk.x), f.nrhs, (unsigned)((Ls + blk.y - 1) / blk.y));
 }
 
-// host description of a column operator
-struct ColSpec {
-  int flags = 0;
-  double pre_d = 1, pre_e = 0, post_d = 1, post_e = 0;
-  double alpha = 1, beta = 0;  // inverse of alpha - beta S
-};
-
-template <typename R>
-ColCoef<R> make_coef(const DwParams& p, const ColSpec& cs) {
-  ColCoef<R> c;
-  c.Ls = p.Ls;
-  c.flags = cs.flags;
-  c.mf = (R)p.mf;
-  c.pre_d = (R)cs.pre_d;
-  c.pre_e = (R)cs.pre_e;
-  c.post_d = (R)cs.post_d;
-  c.post_e = (R)cs.post_e;
-  const double ratio = cs.beta / cs.alpha;
-  const double den = 1.0 + p.mf * std::pow(ratio, p.Ls);
-  c.ainv = (R)(1.0 / cs.alpha);
-  c.ratio = (R)ratio;
-  double w = 1.0 / (cs.alpha * den);
-  for (int k = 0; k < p.Ls; ++k) {
-    c.apow[k] = (R)w;
-    w *= ratio;
-  }
-  return c;
-}
-
 void run_col(const DwParams& p, const ColSpec& spec, const Field& in, Field& out, int dagger, double scale,
              const Field* x, cudaStream_t st, const int* stop) {
   if (p.Ls < 1 || p.Ls > kMaxLs) raise(QCD_ERR_ARG, "Ls must be in [1, %d]", kMaxLs);
@@ -308,13 +198,7 @@ void dw_ainv(const DwParams& p, const Field& in, Field& out, int dagger, double 
     dw_ainv_df(p, in, out, dagger, scale, x, st, stop);
     return;
   }
-  ColSpec cs;
-  cs.flags = kInv | (p.mobius() ? kPost : 0);
-  cs.alpha = p.alpha();
-  cs.beta = p.beta();
-  cs.post_d = p.b5;
-  cs.post_e = p.c5;
-  run_col(p, cs, in, out, dagger, scale, x, st, stop);
+  run_col(p, w_spec(p), in, out, dagger, scale, x, st, stop);
 }
 
 void dw_binv(const DwParams& p, const Field& in, Field& out, cudaStream_t st) {

@@ -179,6 +179,11 @@ void dw_ainv_df(const DwParams& p, const Field& in, Field& out, int dagger, doub
 void dw_binv(const DwParams& p, const Field& in, Field& out, cudaStream_t st);
 // out = A B^-1 in (the full residual from the even-odd one); A for Shamir
 void dw_a_binv(const DwParams& p, const Field& in, Field& out, cudaStream_t st);
+// fused stencil (dwf_hop.cu): out = [x +] a * W H_{p,1-p} in (dagger: W^T (H^dag)_{p,1-p} in),
+// one launch; FP32 / FP16 fields with Ls <= 32 (dw_hop_w_fusable)
+bool dw_hop_w_fusable(const DwParams& p, int prec);
+void dw_hop_w(const qcd_gauge* g, const DwParams& p, const Field& in, Field& out, int out_parity, int dagger,
+              double a, const Field* x, cudaStream_t st, const int* stop = nullptr);
 // site-local blocks of dw_block
 enum Blk5 { BLK_ONE = 0, BLK_A = 1, BLK_B = 2 };
 // out = X in + c * Y y (y may be null), X, Y in {1, A, B}; X^T, Y^T for dagger

@@ -30,6 +30,17 @@ void apply_mhat(const OpCtx& c, const Field& in, Field& out, int dagger, cudaStr
   const DwParams p = dw_params(c.f);
   Field t1 = ws_field(c.g, t + ".mhat.t1", c.prec, in.ls, in.nrhs);
   Field t2 = ws_field(c.g, t + ".mhat.t2", c.prec, in.ls, in.nrhs);
+  if (dw_hop_w_fusable(p, c.prec) && in.ls == p.Ls) {  // W fused into the stencil's epilogue
+    if (!dagger) {
+      dw_hop_w(c.g, p, in, t2, 1, 0, 1.0, nullptr, st, stop);    // W H_oe in
+      dw_hop_w(c.g, p, t2, out, 0, 0, -0.25, &in, st, stop);     // in - 1/4 W H_eo (...)
+    } else {
+      dw_ainv(p, in, t1, 1, 1.0, nullptr, st, stop);             // W^dag in
+      dw_hop_w(c.g, p, t1, t2, 1, 1, 1.0, nullptr, st, stop);    // W^dag (H^dag)_oe (...)
+      hop(c.g, t2, out, 0, 1, -0.25, &in, st, stop, true, red);  // in - 1/4 (H^dag)_eo (...)
+    }
+    return;
+  }
   if (!dagger) {
     hop(c.g, in, t1, 1, 0, 1.0, nullptr, st, stop);       // H_oe in
     dw_ainv(p, t1, t2, 0, 1.0, nullptr, st, stop);        // W H_oe in

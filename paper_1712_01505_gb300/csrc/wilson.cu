@@ -23,84 +23,13 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "stencil.cuh"
 
 namespace qcd {
 
 namespace {
 
-template <typename R>
-__device__ __forceinline__ Cx<R> fmac(R s, Cx<R> a, Cx<R> b) {  // b + s*a
-  return {fma(s, a.re, b.re), fma(s, a.im, b.im)};
-}
-
-// h = u + sg * B l  (2 spins x 3 colours)
-template <int MU, typename R>
-__device__ __forceinline__ void project(const Cx<R> psi[12], R sg, Cx<R> h[6]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    Cx<R> b0, b1;
-    apply_B<MU>(psi[6 + c], psi[9 + c], b0, b1);
-    h[c] = fmac(sg, b0, psi[c]);
-    h[3 + c] = fmac(sg, b1, psi[3 + c]);
-  }
-}
-
-// acc += f (g, sg B^dag g), f = +-1 the boundary factor of the hop (folded into
-// the accumulating FMAs instead of negating the half spinor)
-template <int MU, typename R>
-__device__ __forceinline__ void reconstruct_add(const Cx<R> g[6], R sg, R f, Cx<R> acc[12]) {
-  const R fs = f * sg;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    Cx<R> b0, b1;
-    apply_Bdag<MU>(g[c], g[3 + c], b0, b1);
-    acc[c] = fmac(f, g[c], acc[c]);
-    acc[3 + c] = fmac(f, g[3 + c], acc[3 + c]);
-    acc[6 + c] = fmac(fs, b0, acc[6 + c]);
-    acc[9 + c] = fmac(fs, b1, acc[9 + c]);
-  }
-}
-
-// g = U h (dag = false) or U^dag h (dag = true), for both spins of h
-template <bool DAG, typename R>
-__device__ __forceinline__ void link_mul(const Cx<R> U[9], const Cx<R> h[6], Cx<R> g[6]) {
-#pragma unroll
-  for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      Cx<R> acc = {R(0), R(0)};
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        if (DAG)
-          acc = cjmadd(U[b * 3 + a], h[sp * 3 + b], acc);
-        else
-          acc = cmadd(U[a * 3 + b], h[sp * 3 + b], acc);
-      }
-      g[sp * 3 + a] = acc;
-    }
-}
-
-template <int P, int RECON>
-struct HopArgs {
-  Geom g;
-  int out_parity;
-  int ls;        // slices per right-hand side
-  int nslices;   // ls * nrhs
-  int ntiles;    // ceil(nslices / TILE)
-  FastDiv d_ls, d_ntiles;  // division by ls and by ntiles
-  int dagger;
-  int xpay;
-  double a;
-  LinkView<P, RECON> U;
-  SpinorView<P> in, out, x;
-  const int* stop;
-  int red;             // 0: none; 1: (rt, out); 2: (out, x) and |out|^2
-  SpinorView<P> rt;
-  double* partial;     // [block][4]
-  double* gpartial;    // [group of 64 blocks][4]
-  int* counters;       // [group]
-  int* npartial;
-};
+using namespace stencil;
 
 template <int P, int RECON, int TILE, int MU>
 __device__ __forceinline__ void hop_dir(const HopArgs<P, RECON>& A, const SiteCoords& c, int cb,
@@ -359,57 +288,6 @@ __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
   }
 }
 
-// ----------------------------------------------------------------------------- shared-memory links
-// Many slices per site (domain-wall fifth dimension, several right-hand sides):
-// a block of 32 sites x BY thread rows loads the 8 links of each of its sites
-// once, rebuilds them (12-real) and keeps them in shared memory together with
-// the 8 neighbour indices and boundary signs of each site; every thread then
-// owns one site and TS slices, reads each link once from shared memory and
-// applies it to its TS slices.  Link traffic per block is 8 x 32 links
-// whatever the number of slices, and the per-site index arithmetic is done once.
-// The links are stored as pairs of complex numbers so that a thread reads a
-// link with five 16-byte shared-memory loads: element k is half (k & 1) of pair
-// k >> 1; pair 4 holds element 8 and padding.
-template <typename R>
-struct SmLinks {
-  static_assert(sizeof(R) == 4, "shared-memory links are FP32");
-  float4 U[8][5][32];        // [2 mu + backward][element pair][site]
-  int nb[8][32];             // neighbour checkerboard index
-  unsigned char neg[8][32];  // 1 if the hop carries the antiperiodic sign
-};
-
-template <int P, int RECON, int TS, int L>
-__device__ __forceinline__ void hop_link_sm(const HopArgs<P, RECON>& A, const SmLinks<typename MathType<P>::type>& sm,
-                                            int tx, typename MathType<P>::type sg, const SpinorView<P> (&in)[TS],
-                                            const long (&soff)[TS], int nt,
-                                            Cx<typename MathType<P>::type> (&acc)[TS][12]) {
-  using R = typename MathType<P>::type;
-  constexpr int MU = L >> 1;
-  constexpr bool BACK = (L & 1) != 0;
-  const long ncb = sm.nb[L][tx];
-  const bool neg = sm.neg[L][tx];
-  Cx<R> U[9];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const float4 v = sm.U[L][k][tx];
-    U[2 * k] = {v.x, v.y};
-    if (k < 4) U[2 * k + 1] = {v.z, v.w};
-  }
-  const R sgn = BACK ? -sg : sg;
-#pragma unroll
-  for (int t = 0; t < TS; ++t) {
-    if (TS > 1 && t >= nt) break;
-    Cx<R> psi[12], h[6], gg[6];
-    in[t].load(soff[t] + ncb, psi);
-    project<MU>(psi, sgn, h);
-    if (neg)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) h[k] = -h[k];
-    link_mul<BACK>(U, h, gg);
-    reconstruct_add<MU>(gg, sgn, R(1), acc[t]);
-  }
-}
-
 // RED (with TS = 1, several right-hand sides): the BiCGStab inner products of
 // the k_hop_red kernel per right-hand side.  A warp is 32 sites of one slice, so
 // it reduces in registers and lane 0 writes partial[(q * nsb + site block) * 4
@@ -425,27 +303,7 @@ __device__ __forceinline__ void hop_sm(const HopArgs<P, RECON>& A) {
   const int stile = blockIdx.x - sblock * A.ntiles;
   const int cb = sblock * 32 + tx;
   const bool valid = cb < A.g.Vh;
-  if (valid) {
-    SiteCoords c = cb_to_site(A.g, cb, A.out_parity);
-#pragma unroll
-    for (int l = 0; l < 8; ++l) {
-      if (l % BY != ty) continue;
-      const int mu = l >> 1;
-      int wrap;
-      int j = neighbour_index(A.g, c, mu, (l & 1) ? -1 : +1, &wrap);
-      sm.nb[l][tx] = j >> 1;
-      sm.neg[l][tx] = (unsigned char)(wrap && A.g.apbc[mu]);
-      Cx<R> U[9];
-      if ((l & 1) == 0)
-        A.U.load(A.out_parity, mu, cb, U);  // U_mu(x)
-      else
-        A.U.load(1 - A.out_parity, mu, j >> 1, U);  // U_mu(x - mu)
-#pragma unroll
-      for (int k = 0; k < 5; ++k)
-        sm.U[l][k][tx] = make_float4(U[2 * k].re, U[2 * k].im, k < 4 ? U[2 * k + 1].re : 0.f,
-                                     k < 4 ? U[2 * k + 1].im : 0.f);
-    }
-  }
+  stage_links_sm<P, RECON, BY>(A, sm, tx, ty, cb, valid);
   __syncthreads();
   const int q0 = (stile * BY + ty) * TS;
   if (q0 >= A.nslices) return;      // a whole warp (one row of slices)

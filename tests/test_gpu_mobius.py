@@ -156,3 +156,25 @@ def test_mobius_rejects_singular_blocks(b5, c5, M5_):
     out = torch.empty((Ls, V, 4, 3), dtype=torch.complex128, device=device())
     with pytest.raises(qcd.QCDError, match="ERR_ARG"):
         qcd.dslash(g, qcd.mobius(Ls, M5_, MF, b5, c5), "MHAT", to_dev(psi), out, prec="f32")
+
+
+@pytest.mark.parametrize("Ls", [32, 36])
+@pytest.mark.parametrize("mobius", [False, True])
+def test_mhat_at_the_fused_limit_and_beyond(Ls, mobius):
+    """Ls <= 32 runs the stencil with W in its epilogue (one launch per hop), larger Ls the hop and
+    the column kernel as two launches: both against the oracle, FP32 and FP16, both adjoints."""
+    device()
+    L = (2, 2, 2, 4)
+    V, U, psi = _case(L, Ls, 95)
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    b5, c5 = (B5, C5) if mobius else (1.0, 0.0)
+    f = qcd.mobius(Ls, M5, MF, b5, c5)
+    par = ora.parity(L)
+    pe = psi.copy()
+    pe[:, par == 1] = 0
+    out = torch.empty((Ls, V, 4, 3), dtype=torch.complex128, device=device())
+    for prec in ("f32", "f16"):
+        for dag in (False, True):
+            qcd.dslash(g, f, "MHAT_DAG" if dag else "MHAT", to_dev(psi), out, prec=prec)
+            torch.cuda.synchronize()
+            _check(out, ora.mobius_mhat(L, BC, Ls, M5, MF, b5, c5, U, pe, dagger=dag), prec)
