@@ -208,6 +208,16 @@ struct SpinorView<P64> {
   }
 };
 
+// FP32 and FP16 storage interleaves the two spins of each chiral half: spin
+// pair q (q = 0, 1, 2: spins 0 and 1 of colour q; q = 3, 4, 5: spins 2 and 3 of
+// colour q - 3) is one 16-byte unit (re_a, re_b, im_a, im_b).  load / store
+// give the canonical order [spin * 3 + colour] (a renaming of registers);
+// load_p / store_p give the pairs as two FP32 lanes, the operands of the packed
+// FP32x2 arithmetic of the stencil.
+struct P2 {
+  float2 re, im;  // (spin a, spin b)
+};
+
 template <>
 struct SpinorView<P32> {
   using R = float;
@@ -216,16 +226,30 @@ struct SpinorView<P32> {
   long stride;
   __device__ __forceinline__ void load(long site, Cx<R> v[12]) const {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      float4 d = __ldg(p + k * stride + site);
-      v[2 * k] = {d.x, d.y};
-      v[2 * k + 1] = {d.z, d.w};
+    for (int q = 0; q < 6; ++q) {
+      const int b = q < 3 ? q : q + 3;  // canonical index of spin a
+      float4 d = __ldg(p + q * stride + site);
+      v[b] = {d.x, d.z};
+      v[b + 3] = {d.y, d.w};
     }
   }
   __device__ __forceinline__ void store(long site, const Cx<R> v[12]) const {
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
-      p[k * stride + site] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+    for (int q = 0; q < 6; ++q) {
+      const int b = q < 3 ? q : q + 3;
+      p[q * stride + site] = make_float4(v[b].re, v[b + 3].re, v[b].im, v[b + 3].im);
+    }
+  }
+  __device__ __forceinline__ void load_p(long site, P2 w[6]) const {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      float4 d = __ldg(p + q * stride + site);
+      w[q] = {make_float2(d.x, d.y), make_float2(d.z, d.w)};
+    }
+  }
+  __device__ __forceinline__ void store_p(long site, const P2 w[6]) const {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) p[q * stride + site] = make_float4(w[q].re.x, w[q].re.y, w[q].im.x, w[q].im.y);
   }
   __device__ __forceinline__ SpinorView offset_rhs(int r) const {
     SpinorView o = *this;
@@ -235,7 +259,8 @@ struct SpinorView<P32> {
 };
 
 // binary16 storage of psi/s with s = max |component| of the site (FP32),
-// round-to-nearest-even on store; arithmetic is FP32.
+// round-to-nearest-even on store; arithmetic is FP32.  uint4 k holds spin pairs
+// q = 2k, 2k + 1 as half2 (re_a, re_b), half2 (im_a, im_b).
 template <>
 struct SpinorView<P16> {
   using R = float;
@@ -249,9 +274,11 @@ struct SpinorView<P16> {
       uint4 d = __ldg(p + k * stride + site);
       const __half2* h = reinterpret_cast<const __half2*>(&d);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        float2 f = __half22float2(h[j]);
-        v[4 * k + j] = {f.x * s, f.y * s};
+      for (int j = 0; j < 2; ++j) {
+        const int q = 2 * k + j, b = q < 3 ? q : q + 3;
+        const float2 re = __half22float2(h[2 * j]), im = __half22float2(h[2 * j + 1]);
+        v[b] = {re.x * s, im.x * s};
+        v[b + 3] = {re.y * s, im.y * s};
       }
     }
   }
@@ -266,8 +293,43 @@ struct SpinorView<P16> {
       uint4 d;
       __half2* h = reinterpret_cast<__half2*>(&d);
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        h[j] = __floats2half2_rn(v[4 * k + j].re * inv, v[4 * k + j].im * inv);
+      for (int j = 0; j < 2; ++j) {
+        const int q = 2 * k + j, b = q < 3 ? q : q + 3;
+        h[2 * j] = __floats2half2_rn(v[b].re * inv, v[b + 3].re * inv);
+        h[2 * j + 1] = __floats2half2_rn(v[b].im * inv, v[b + 3].im * inv);
+      }
+      p[k * stride + site] = d;
+    }
+  }
+  __device__ __forceinline__ void load_p(long site, P2 w[6]) const {
+    const float s = __ldg(norm + site);
+    const float2 s2 = make_float2(s, s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 d = __ldg(p + k * stride + site);
+      const __half2* h = reinterpret_cast<const __half2*>(&d);
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        w[2 * k + j] = {__fmul2_rn(__half22float2(h[2 * j]), s2), __fmul2_rn(__half22float2(h[2 * j + 1]), s2)};
+    }
+  }
+  __device__ __forceinline__ void store_p(long site, const P2 w[6]) const {
+    float m = 0.f;
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(w[q].re.x), fabsf(w[q].re.y)), fmaxf(fabsf(w[q].im.x), fabsf(w[q].im.y))));
+    float inv = (m > 0.f) ? 1.0f / m : 0.f;
+    norm[site] = m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 d;
+      __half2* h = reinterpret_cast<__half2*>(&d);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const P2& w2 = w[2 * k + j];
+        h[2 * j] = __floats2half2_rn(w2.re.x * inv, w2.re.y * inv);
+        h[2 * j + 1] = __floats2half2_rn(w2.im.x * inv, w2.im.y * inv);
+      }
       p[k * stride + site] = d;
     }
   }

@@ -27,12 +27,12 @@ using namespace dwcol;
 
 constexpr int kFusedMaxLs = 32;  // tile of 32 sites x Ls slices x 96 B within 96 KB
 
-template <int P, int RECON, int BY>
+// PK = 1: the hop with packed FP32x2 arithmetic (stencil.cuh)
+template <int P, int RECON, int BY, int PK>
 __global__ void __launch_bounds__(32 * BY) k_dw_hop_w(HopArgs<P, RECON> A, ColCoef<float> c) {
   using R = typename MathType<P>::type;
   static_assert(sizeof(R) == 4, "the fused stencil computes in FP32");
   if (A.stop && *A.stop) return;
-  __shared__ SmLinks<R> sm;
   extern __shared__ __align__(16) unsigned char smraw[];
   R* tile = reinterpret_cast<R*>(smraw);
   constexpr int cs = 24 * 32;  // stride between slices of the tile
@@ -41,29 +41,62 @@ __global__ void __launch_bounds__(32 * BY) k_dw_hop_w(HopArgs<P, RECON> A, ColCo
   const int cb = blockIdx.x * 32 + tx;
   const bool valid = cb < A.g.Vh;
   const int Ls = A.ls;
-  stage_links_sm<P, RECON, BY>(A, sm, tx, ty, cb, valid);
-  __syncthreads();
-  const SpinorView<P> in[1] = {A.in.offset_rhs(r)};
   const R sg = A.dagger ? R(1) : R(-1);
-  for (int s = ty; s < Ls; s += BY) {
-    Cx<R> acc[1][12];
+  if constexpr (PK) {
+    __shared__ SmLinks<float> sm;
+    stage_links_sm<P, RECON, BY>(A, sm, tx, ty, cb, valid);
+    __syncthreads();
+    const SpinorView<P> in = A.in.offset_rhs(r);
+    for (int s = ty; s < Ls; s += BY) {
+      P2 acc[6];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
-    if (valid) {
-      const long soff[1] = {(long)s * A.g.Vh};
-      hop_link_sm<P, RECON, 1, 0>(A, sm, tx, sg, in, soff, 1, acc);
-      hop_link_sm<P, RECON, 1, 1>(A, sm, tx, sg, in, soff, 1, acc);
-      hop_link_sm<P, RECON, 1, 2>(A, sm, tx, sg, in, soff, 1, acc);
-      hop_link_sm<P, RECON, 1, 3>(A, sm, tx, sg, in, soff, 1, acc);
-      hop_link_sm<P, RECON, 1, 4>(A, sm, tx, sg, in, soff, 1, acc);
-      hop_link_sm<P, RECON, 1, 5>(A, sm, tx, sg, in, soff, 1, acc);
-      hop_link_sm<P, RECON, 1, 6>(A, sm, tx, sg, in, soff, 1, acc);
-      hop_link_sm<P, RECON, 1, 7>(A, sm, tx, sg, in, soff, 1, acc);
+      for (int q = 0; q < 6; ++q) acc[q] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      if (valid) {
+        const long soff = (long)s * A.g.Vh;
+        hop_link_smp<P, RECON, 0>(A, sm, tx, sg, in, soff, acc);
+        hop_link_smp<P, RECON, 1>(A, sm, tx, sg, in, soff, acc);
+        hop_link_smp<P, RECON, 2>(A, sm, tx, sg, in, soff, acc);
+        hop_link_smp<P, RECON, 3>(A, sm, tx, sg, in, soff, acc);
+        hop_link_smp<P, RECON, 4>(A, sm, tx, sg, in, soff, acc);
+        hop_link_smp<P, RECON, 5>(A, sm, tx, sg, in, soff, acc);
+        hop_link_smp<P, RECON, 6>(A, sm, tx, sg, in, soff, acc);
+        hop_link_smp<P, RECON, 7>(A, sm, tx, sg, in, soff, acc);
+      }
+      // spin pair q: canonical components b (lane x) and b + 3 (lane y)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const int b = q < 3 ? q : q + 3;
+        tile[s * cs + (2 * b) * 32 + tx] = acc[q].re.x;
+        tile[s * cs + (2 * b + 1) * 32 + tx] = acc[q].im.x;
+        tile[s * cs + (2 * (b + 3)) * 32 + tx] = acc[q].re.y;
+        tile[s * cs + (2 * (b + 3) + 1) * 32 + tx] = acc[q].im.y;
+      }
     }
+  } else {
+    __shared__ SmLinks<R> sm;
+    stage_links_sm<P, RECON, BY>(A, sm, tx, ty, cb, valid);
+    __syncthreads();
+    const SpinorView<P> in[1] = {A.in.offset_rhs(r)};
+    for (int s = ty; s < Ls; s += BY) {
+      Cx<R> acc[1][12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      tile[s * cs + (2 * k) * 32 + tx] = acc[0][k].re;
-      tile[s * cs + (2 * k + 1) * 32 + tx] = acc[0][k].im;
+      for (int k = 0; k < 12; ++k) acc[0][k] = {R(0), R(0)};
+      if (valid) {
+        const long soff[1] = {(long)s * A.g.Vh};
+        hop_link_sm<P, RECON, 1, 0>(A, sm, tx, sg, in, soff, 1, acc);
+        hop_link_sm<P, RECON, 1, 1>(A, sm, tx, sg, in, soff, 1, acc);
+        hop_link_sm<P, RECON, 1, 2>(A, sm, tx, sg, in, soff, 1, acc);
+        hop_link_sm<P, RECON, 1, 3>(A, sm, tx, sg, in, soff, 1, acc);
+        hop_link_sm<P, RECON, 1, 4>(A, sm, tx, sg, in, soff, 1, acc);
+        hop_link_sm<P, RECON, 1, 5>(A, sm, tx, sg, in, soff, 1, acc);
+        hop_link_sm<P, RECON, 1, 6>(A, sm, tx, sg, in, soff, 1, acc);
+        hop_link_sm<P, RECON, 1, 7>(A, sm, tx, sg, in, soff, 1, acc);
+      }
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        tile[s * cs + (2 * k) * 32 + tx] = acc[0][k].re;
+        tile[s * cs + (2 * k + 1) * 32 + tx] = acc[0][k].im;
+      }
     }
   }
   __syncthreads();
@@ -112,24 +145,28 @@ struct FusedLaunch {
   cudaStream_t st;
 };
 
-template <int P, int RECON, int BY>
+template <int P, int RECON, int BY, int PK>
 void launch_fused(FusedLaunch<P, RECON>* L) {
   static bool attr_set = false;
   if (!attr_set) {
-    QCD_CK(cudaFuncSetAttribute(k_dw_hop_w<P, RECON, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    QCD_CK(cudaFuncSetAttribute(k_dw_hop_w<P, RECON, BY, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kFusedMaxLs * 24 * 32 * (int)sizeof(float)));
     attr_set = true;
   }
-  k_dw_hop_w<P, RECON, BY><<<dim3(L->nsb, (unsigned)L->nrhs), dim3(32, BY), L->smem, L->st>>>(L->args, L->coef);
+  k_dw_hop_w<P, RECON, BY, PK><<<dim3(L->nsb, (unsigned)L->nrhs), dim3(32, BY), L->smem, L->st>>>(L->args,
+                                                                                                  L->coef);
 }
 
 template <int P, int RECON>
 void run_fused(void* ctx, const LaunchCfg& cfg) {
   auto* L = (FusedLaunch<P, RECON>*)ctx;
-  switch (cfg.tile) {
-    case 4: launch_fused<P, RECON, 4>(L); break;
-    case 16: launch_fused<P, RECON, 16>(L); break;
-    default: launch_fused<P, RECON, 8>(L); break;
+  switch (cfg.tile) {  // BY, + 100 for the packed arithmetic
+    case 4: launch_fused<P, RECON, 4, 0>(L); break;
+    case 16: launch_fused<P, RECON, 16, 0>(L); break;
+    case 104: launch_fused<P, RECON, 4, 1>(L); break;
+    case 108: launch_fused<P, RECON, 8, 1>(L); break;
+    case 116: launch_fused<P, RECON, 16, 1>(L); break;
+    default: launch_fused<P, RECON, 8, 0>(L); break;
   }
 }
 
@@ -162,7 +199,7 @@ void fused_impl(const qcd_gauge* gh, const void* links, const DwParams& p, const
   L.nsb = (unsigned)((gh->lat.Vh + 31) / 32);
   L.nrhs = in.nrhs;
   L.st = st;
-  const std::vector<LaunchCfg> cands = {{128, 4}, {256, 8}, {512, 16}};
+  const std::vector<LaunchCfg> cands = {{128, 4}, {256, 8}, {512, 16}, {128, 104}, {256, 108}, {512, 116}};
   char key[160];
   snprintf(key, sizeof key, "dwhopw p%d r%d L%dx%dx%dx%d ls%d nrhs%d xp%d mob%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], in.ls, in.nrhs, A.xpay, (int)p.mobius());

@@ -169,5 +169,120 @@ __device__ __forceinline__ void stage_links_sm(const HopArgs<P, RECON>& A, SmLin
   }
 }
 
+
+// ----------------------------------------------------------------------------- packed FP32x2
+// The same stencil with the two spins of a chiral half as the two lanes of
+// Blackwell's packed FP32 instructions (__ffma2_rn / __fadd2_rn / __fmul2_rn,
+// each lane rounded as its scalar counterpart): the link multiplies both spins
+// of the half spinor by the same matrix, so one FFMA2 does the work of two
+// FFMAs with the link element duplicated in both lanes.  Pairs come from
+// SpinorView::load_p (spins 0/1 of colour c at [c], spins 2/3 at [3 + c]).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 swp(float2 a) { return make_float2(a.y, a.x); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+// h = u + sg B l per colour, lanes = the two spins (B from the chiral basis above)
+template <int MU>
+__device__ __forceinline__ void project_p(const P2 w[6], float sg, P2 h[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const P2& u = w[c];
+    const P2& l = w[3 + c];
+    if (MU == 0) {  // B l = -i (l_1, l_0)
+      h[c].re = fma2(bc2(sg), swp(l.im), u.re);
+      h[c].im = fma2(bc2(-sg), swp(l.re), u.im);
+    } else if (MU == 1) {  // B l = (-l_1, l_0)
+      h[c].re = fma2(make_float2(-sg, sg), swp(l.re), u.re);
+      h[c].im = fma2(make_float2(-sg, sg), swp(l.im), u.im);
+    } else if (MU == 2) {  // B l = (-i l_0, i l_1)
+      h[c].re = fma2(make_float2(sg, -sg), l.im, u.re);
+      h[c].im = fma2(make_float2(-sg, sg), l.re, u.im);
+    } else {  // B l = l
+      h[c].re = fma2(bc2(sg), l.re, u.re);
+      h[c].im = fma2(bc2(sg), l.im, u.im);
+    }
+  }
+}
+
+// acc += f (g, sg B^dag g), f = +-1 the boundary factor of the hop
+template <int MU>
+__device__ __forceinline__ void reconstruct_p(const P2 g[3], float sg, float f, P2 acc[6]) {
+  const float fs = f * sg;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c].re = fma2(bc2(f), g[c].re, acc[c].re);
+    acc[c].im = fma2(bc2(f), g[c].im, acc[c].im);
+    if (MU == 0) {  // B^dag g = i (g_1, g_0)
+      acc[3 + c].re = fma2(bc2(-fs), swp(g[c].im), acc[3 + c].re);
+      acc[3 + c].im = fma2(bc2(fs), swp(g[c].re), acc[3 + c].im);
+    } else if (MU == 1) {  // B^dag g = (g_1, -g_0)
+      acc[3 + c].re = fma2(make_float2(fs, -fs), swp(g[c].re), acc[3 + c].re);
+      acc[3 + c].im = fma2(make_float2(fs, -fs), swp(g[c].im), acc[3 + c].im);
+    } else if (MU == 2) {  // B^dag g = (i g_0, -i g_1)
+      acc[3 + c].re = fma2(make_float2(-fs, fs), g[c].im, acc[3 + c].re);
+      acc[3 + c].im = fma2(make_float2(fs, -fs), g[c].re, acc[3 + c].im);
+    } else {
+      acc[3 + c].re = fma2(bc2(fs), g[c].re, acc[3 + c].re);
+      acc[3 + c].im = fma2(bc2(fs), g[c].im, acc[3 + c].im);
+    }
+  }
+}
+
+// Link element k of direction L as (re, re, im, im), from the compact staging
+// (two elements per float4) with the lanes duplicated in registers (FFMA2 takes
+// the duplicated operand without extra instructions).
+__device__ __forceinline__ void link_elems(const SmLinks<float>& sm, int L, int tx, float4 e[9]) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float4 v = sm.U[L][k][tx];
+    e[2 * k] = make_float4(v.x, v.x, v.y, v.y);
+    if (k < 4) e[2 * k + 1] = make_float4(v.z, v.z, v.w, v.w);
+  }
+}
+
+// acc += the hop from direction L (mu = L / 2, backward if L odd) for one slice,
+// packed: g = U h (U^dag h backward) with both spins of h in the lanes
+template <int P, int RECON, int L>
+__device__ __forceinline__ void hop_link_smp(const HopArgs<P, RECON>& A, const SmLinks<float>& sm, int tx, float sg,
+                                             const SpinorView<P>& in, long soff, P2 acc[6]) {
+  constexpr int MU = L >> 1;
+  constexpr bool BACK = (L & 1) != 0;
+  const long ncb = sm.nb[L][tx];
+  const float f = sm.neg[L][tx] ? -1.f : 1.f;
+  const float sgn = BACK ? -sg : sg;
+  P2 w[6], h[3], g[3];
+  in.load_p(soff + ncb, w);
+  project_p<MU>(w, sgn, h);
+  // -Im h (forward) or -Re h (backward) for the terms with a minus sign
+  float2 nh[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) nh[b] = BACK ? __fmul2_rn(bc2(-1.f), h[b].re) : __fmul2_rn(bc2(-1.f), h[b].im);
+  float4 e[9];
+  link_elems(sm, L, tx, e);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float2 gr = make_float2(0.f, 0.f), gi = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      // forward: U_ab; backward: conj(U_ba)
+      const float4 u = e[BACK ? b * 3 + a : a * 3 + b];
+      const float2 ur = make_float2(u.x, u.y), ui = make_float2(u.z, u.w);
+      if (!BACK) {  // (ur + i ui) h: re = ur h.re - ui h.im, im = ur h.im + ui h.re
+        gr = fma2(ur, h[b].re, gr);
+        gr = fma2(ui, nh[b], gr);
+        gi = fma2(ur, h[b].im, gi);
+        gi = fma2(ui, h[b].re, gi);
+      } else {  // (ur - i ui) h: re = ur h.re + ui h.im, im = ur h.im - ui h.re
+        gr = fma2(ur, h[b].re, gr);
+        gr = fma2(ui, h[b].im, gr);
+        gi = fma2(ur, h[b].im, gi);
+        gi = fma2(ui, nh[b], gi);
+      }
+    }
+    g[a] = {gr, gi};
+  }
+  reconstruct_p<MU>(g, sgn, f, acc);
+}
+
 }  // namespace stencil
 }  // namespace qcd

@@ -385,6 +385,105 @@ __device__ __forceinline__ void hop_sm(const HopArgs<P, RECON>& A) {
   }
 }
 
+// The shared-memory kernel with packed FP32x2 arithmetic (stencil.cuh): one
+// slice per thread, spinors loaded as spin pairs; RED as in hop_sm.
+template <int P, int RECON, int BY, int RED>
+__device__ __forceinline__ void hop_smp(const HopArgs<P, RECON>& A) {
+  if (A.stop && *A.stop) return;
+  __shared__ SmLinks<float> sm;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int sblock = fdiv(blockIdx.x, A.d_ntiles);
+  const int stile = blockIdx.x - sblock * A.ntiles;
+  const int cb = sblock * 32 + tx;
+  const bool valid = cb < A.g.Vh;
+  stage_links_sm<P, RECON, BY>(A, sm, tx, ty, cb, valid);
+  __syncthreads();
+  const int q0 = stile * BY + ty;
+  if (q0 >= A.nslices) return;      // a whole warp (one row of slices)
+  if (!valid && RED == 0) return;  // sites past Vh: with RED they add zero to the warp's sum
+  const int r = fdiv(q0, A.d_ls), s = q0 - r * A.ls;
+  const SpinorView<P> in = A.in.offset_rhs(r);
+  const long soff = (long)s * A.g.Vh;
+  float red[3] = {0.f, 0.f, 0.f};
+  if (valid) {
+    P2 acc[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) acc[q] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const float sg = A.dagger ? 1.f : -1.f;
+    hop_link_smp<P, RECON, 0>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 1>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 2>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 3>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 4>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 5>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 6>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 7>(A, sm, tx, sg, in, soff, acc);
+    const long site = soff + cb;
+    const float2 a2 = bc2((float)A.a);
+    P2 o[6];
+    if (A.xpay) {
+      A.x.offset_rhs(r).load_p(site, o);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) o[q] = {fma2(a2, acc[q].re, o[q].re), fma2(a2, acc[q].im, o[q].im)};
+    } else {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) o[q] = {__fmul2_rn(a2, acc[q].re), __fmul2_rn(a2, acc[q].im)};
+    }
+    A.out.offset_rhs(r).store_p(site, o);
+    if constexpr (RED == 1) {  // (rt, out) = sum conj(rt) out
+      P2 w[6];
+      A.rt.offset_rhs(r).load_p(site, w);
+      float2 dr = make_float2(0.f, 0.f), di = dr, dj = dr;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        dr = fma2(w[q].re, o[q].re, dr);
+        dr = fma2(w[q].im, o[q].im, dr);
+        di = fma2(w[q].re, o[q].im, di);
+        dj = fma2(w[q].im, o[q].re, dj);
+      }
+      red[0] = dr.x + dr.y;
+      red[1] = (di.x + di.y) - (dj.x + dj.y);
+    } else if constexpr (RED == 2) {  // (out, x) = sum conj(out) x, |out|^2
+      P2 xs[6];
+      A.x.offset_rhs(r).load_p(site, xs);
+      float2 dr = make_float2(0.f, 0.f), di = dr, dj = dr, oo = dr;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        dr = fma2(o[q].re, xs[q].re, dr);
+        dr = fma2(o[q].im, xs[q].im, dr);
+        di = fma2(o[q].re, xs[q].im, di);
+        dj = fma2(o[q].im, xs[q].re, dj);
+        oo = fma2(o[q].re, o[q].re, oo);
+        oo = fma2(o[q].im, o[q].im, oo);
+      }
+      red[0] = dr.x + dr.y;
+      red[1] = (di.x + di.y) - (dj.x + dj.y);
+      red[2] = oo.x + oo.y;
+    }
+  }
+  if constexpr (RED != 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      for (int o = 16; o > 0; o >>= 1) red[k] += __shfl_down_sync(0xffffffffu, red[k], o);
+    if (tx == 0) {
+      const long nsb = (A.g.Vh + 31) / 32;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) A.partial[((long)q0 * nsb + sblock) * 4 + k] = (double)red[k];
+    }
+  }
+}
+
+template <int P, int RECON, int BY, int RED>
+__global__ void __launch_bounds__(32 * BY) k_hop_smp(HopArgs<P, RECON> A) {
+  hop_smp<P, RECON, BY, RED>(A);
+}
+
+// the same with the registers bounded so that 24 warps fit on an SM
+template <int P, int RECON, int BY, int RED>
+__global__ void __launch_bounds__(32 * BY, 24 / BY) k_hop_smp_occ(HopArgs<P, RECON> A) {
+  hop_smp<P, RECON, BY, RED>(A);
+}
+
 template <int P, int RECON, int BY, int TS, int RED>
 __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
   hop_sm<P, RECON, BY, TS, RED>(A);
@@ -459,11 +558,27 @@ void launch_sm(HopLaunch<P, RECON>* L) {
     k_hop_sm<P, RECON, BY, TS, RED><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
 }
 
+// OCC = 1: the register-bounded kernel (24 warps per SM)
+template <int P, int RECON, int BY, int RED = 0, int OCC = 0>
+void launch_smp(HopLaunch<P, RECON>* L) {
+  HopArgs<P, RECON> A = L->args;
+  A.ntiles = (A.nslices + BY - 1) / BY;
+  A.d_ntiles = make_fastdiv((unsigned)A.ntiles);
+  long sblocks = (A.g.Vh + 31) / 32;
+  const dim3 grid((unsigned)(sblocks * A.ntiles)), blk(32, BY);
+  if constexpr (OCC)
+    k_hop_smp_occ<P, RECON, BY, RED><<<grid, blk, 0, L->st>>>(A);
+  else
+    k_hop_smp<P, RECON, BY, RED><<<grid, blk, 0, L->st>>>(A);
+}
+
 // cfg.tile > 0: register tile of that many slices per thread (k_hop), 101 /
 // 201: one slice per thread with prefetch mode 1 / 2;
 // cfg.tile < 0: shared-memory links (k_hop_sm), -tile = 10 * BY + TS for
 // BY thread rows of TS slices each; -tile = 200 + 10 * BY + TS: the same with at most
-// 64 registers per thread (32 resident warps per SM)
+// 64 registers per thread (32 resident warps per SM); -tile = 500 + 10 * BY + 1:
+// packed FP32x2 arithmetic, one slice per thread (k_hop_smp); 600 + ...: the
+// same with the registers bounded for 24 resident warps
 template <int P, int RECON>
 void run_cfg(void* ctx, const LaunchCfg& cfg) {
   auto* L = (HopLaunch<P, RECON>*)ctx;
@@ -474,6 +589,10 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case -81: L->args.red == 1 ? launch_sm<P, RECON, 8, 1, 1>(L) : launch_sm<P, RECON, 8, 1, 2>(L); break;
       case -241: L->args.red == 1 ? launch_sm<P, RECON, 4, 1, 1, 1>(L) : launch_sm<P, RECON, 4, 1, 2, 1>(L); break;
       case -281: L->args.red == 1 ? launch_sm<P, RECON, 8, 1, 1, 1>(L) : launch_sm<P, RECON, 8, 1, 2, 1>(L); break;
+      case -541: L->args.red == 1 ? launch_smp<P, RECON, 4, 1>(L) : launch_smp<P, RECON, 4, 2>(L); break;
+      case -581: L->args.red == 1 ? launch_smp<P, RECON, 8, 1>(L) : launch_smp<P, RECON, 8, 2>(L); break;
+      case -641: L->args.red == 1 ? launch_smp<P, RECON, 4, 1, 1>(L) : launch_smp<P, RECON, 4, 2, 1>(L); break;
+      case -681: L->args.red == 1 ? launch_smp<P, RECON, 8, 1, 1>(L) : launch_smp<P, RECON, 8, 2, 1>(L); break;
       default: L->args.red == 1 ? launch_sm<P, RECON, 4, 1, 1>(L) : launch_sm<P, RECON, 4, 1, 2>(L);
     }
   } else {
@@ -488,6 +607,10 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case -81: launch_sm<P, RECON, 8, 1>(L); break;
       case -241: launch_sm<P, RECON, 4, 1, 0, 1>(L); break;
       case -281: launch_sm<P, RECON, 8, 1, 0, 1>(L); break;
+      case -541: launch_smp<P, RECON, 4>(L); break;
+      case -581: launch_smp<P, RECON, 8>(L); break;
+      case -641: launch_smp<P, RECON, 4, 0, 1>(L); break;
+      case -681: launch_smp<P, RECON, 8, 0, 1>(L); break;
       default: launch_sm<P, RECON, 8, 2>(L); break;
     }
   }
@@ -544,6 +667,10 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64 && A.nslices >= 16) cands.push_back({256, -82});
   if (P == P32 && A.nslices >= 4) cands.push_back({128, -241});
   if (P == P32 && A.nslices >= 8) cands.push_back({256, -281});
+  if (P != P64 && A.nslices >= 4)
+    for (int t : {-541, -641}) cands.push_back({128, t});
+  if (P != P64 && A.nslices >= 8)
+    for (int t : {-581, -681}) cands.push_back({256, t});
   if (A.red) {  // the fused reduction exists for one slice per thread only
     cands.clear();
     for (int b : blocks) cands.push_back({b, 1});
@@ -551,7 +678,8 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64)  // one slice per thread with prefetches (memory-bound precisions)
     for (int pf : {101, 201})
       for (int b : blocks) cands.push_back({b, pf});
-  if (multi_red) cands = {{128, -41}, {256, -81}, {128, -241}, {256, -281}};  // shared-memory links, one slice per thread
+  if (multi_red)
+    cands = {{128, -41}, {256, -81}, {128, -241}, {256, -281}, {128, -541}, {256, -581}, {128, -641}, {256, -681}};  // shared-memory links, one slice per thread
   char key[160];
   snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d red%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay, A.red);

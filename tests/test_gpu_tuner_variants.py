@@ -1,8 +1,9 @@
 """Every launch shape the stencil autotuner can choose computes the same operator.
 
 Each candidate (register tiles of 1 / 2 / 4 slices, the L1-prefetching single-slice
-kernels, the shared-memory link kernels, and the fused-reduction stencils of the
-BiCGStab iteration with and without prefetches) is forced through a tuning-cache
+kernels, the shared-memory link kernels with scalar and packed FP32x2 arithmetic, the
+fused-reduction stencils of the BiCGStab iteration with and without prefetches, and the
+domain-wall stencil with the fifth-dimension inverse in its epilogue) is forced through a tuning-cache
 file (QCD_TUNECACHE) in a child process, on a lattice of its own so that every
 cache key names one candidate, and its result is compared with the oracle."""
 import json
@@ -46,6 +47,21 @@ for case in json.loads(sys.argv[1]):
             a = o[r].cpu().numpy()
             err = max(err, float(np.linalg.norm(a - ref) / np.linalg.norm(ref)))
         res.append(err)
+    elif case["kind"] == "dwmhat":
+        Ls = case["Ls"]
+        b5, c5 = (1.5, 0.5) if case["mob"] else (1.0, 0.0)
+        f = qcd.mobius(Ls, 1.8, 0.02, b5, c5)
+        psi = inputs.gaussian_source((Ls, V, 4, 3), 2)
+        pe = psi.copy()
+        pe[:, ora.parity(L) == 1] = 0
+        o = torch.empty((Ls, V, 4, 3), dtype=torch.complex128, device="cuda")
+        err = 0.0
+        for dag in (False, True):
+            qcd.dslash(g, f, "MHAT_DAG" if dag else "MHAT", torch.from_numpy(psi).cuda(), o, prec=case["prec"])
+            torch.cuda.synchronize()
+            ref = ora.mobius_mhat(L, BC, Ls, 1.8, 0.02, b5, c5, U, pe, dagger=dag)
+            err = max(err, float(np.linalg.norm(o.cpu().numpy() - ref) / np.linalg.norm(ref)))
+        res.append(err)
     elif case["kind"] == "dwsolve":
         Ls = case["Ls"]
         f = qcd.dwf(Ls, 1.8, 0.02)
@@ -80,12 +96,12 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
     device()
     # (tile code, block) of every candidate family; the shared-memory kernels fix their block
     shapes = [(1, 128), (2, 64), (4, 256), (101, 64), (201, 128), (-41, 128), (-42, 128), (-81, 256), (-82, 256),
-              (-241, 128), (-281, 256)]
+              (-241, 128), (-281, 256), (-541, 128), (-581, 256), (-641, 128), (-681, 256)]
     cases, lines, tol = [], [], []
     t = 4
     for prec, recon in (("f32", 12), ("f32", 18), ("f16", 12)):
         for tile, block in shapes:
-            if tile < -200 and prec != "f32":
+            if tile in (-241, -281) and prec != "f32":
                 continue  # the register-bounded shapes are FP32 only
             L = (4, 4, 4, t)
             t += 2
@@ -101,7 +117,8 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
             lines.append(f"{_key(L, 'f32', 12, 1, xp, red)}\t{block}\t{tile}")
         tol.append(1e-10)
     # the fused-reduction shared-memory stencils of the batched (several rhs) iteration
-    for tile, block in ((-41, 128), (-81, 256), (-241, 128), (-281, 256)):
+    for tile, block in ((-41, 128), (-81, 256), (-241, 128), (-281, 256), (-541, 128), (-581, 256),
+                        (-641, 128), (-681, 256)):
         L = (4, 4, 8, t)
         t += 2
         cases.append({"kind": "solve", "L": L, "recon": 12, "nrhs": 4})
@@ -109,12 +126,23 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
             lines.append(f"{_key(L, 'f32', 12, 4, xp, red)}\t{block}\t{tile}")
         tol.append(1e-10)
     # the fused-reduction shared-memory stencils of the domain-wall CG (Re(p, q) over all slices)
-    for tile, block in ((-41, 128), (-81, 256)):
+    for tile, block in ((-41, 128), (-81, 256), (-581, 256), (-641, 128)):
         L = (4, 4, 2, t)
         t += 2
         cases.append({"kind": "dwsolve", "L": L, "recon": 12, "Ls": 8})
         lines.append(f"{_key(L, 'f32', 12, 8, 1, 1)}\t{block}\t{tile}")
         tol.append(1e-10)
+    # the domain-wall stencil with W in its epilogue: thread rows 4 / 8 / 16, plain or packed
+    # arithmetic, Shamir and Mobius, FP32 and FP16, both adjoints of Mhat
+    for tile, block in ((4, 128), (8, 256), (16, 512), (104, 128), (108, 256), (116, 512)):
+        for prec, mob in (("f32", 0), ("f16", 1)):
+            L = (4, 2, 4, t)
+            t += 2
+            cases.append({"kind": "dwmhat", "L": L, "recon": 12, "Ls": 6, "prec": prec, "mob": mob})
+            for xp in (0, 1):
+                lines.append(f"dwhopw p{1 if prec == 'f32' else 2} r12 L{L[0]}x{L[1]}x{L[2]}x{L[3]} ls6 nrhs1 "
+                             f"xp{xp} mob{mob}\t{block}\t{tile}")
+            tol.append(1e-6 if prec == "f32" else 2e-3)
     cache = tmp_path / "tune.txt"
     cache.write_text("\n".join(lines) + "\n")
     env = dict(os.environ, QCD_TUNECACHE=str(cache), PYTHONPATH=ROOT + os.pathsep + os.environ.get("PYTHONPATH", ""))
