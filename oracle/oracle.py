@@ -76,6 +76,11 @@ def num_threads() -> int:
     return lib().ora_num_threads()
 
 
+def set_num_threads(n: int) -> None:
+    """Threads used by the following oracle calls (timing only; results do not depend on it)."""
+    lib().ora_set_num_threads(int(n))
+
+
 def gamma(k: int) -> np.ndarray:
     """Dirac matrix gamma_{k+1} for k = 0..3, gamma_5 for k = 4 (chiral basis)."""
     out = np.zeros((4, 4, 2), dtype=np.float64)

@@ -91,6 +91,15 @@ int ora_num_threads(void) {
 #endif
 }
 
+/* Threads of the following oracle calls (n >= 1); a no-op without OpenMP. */
+void ora_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Geometry                                                                  */
 /* ------------------------------------------------------------------------ */

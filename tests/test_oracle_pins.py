@@ -399,3 +399,21 @@ def test_spectra_explain_the_choice_of_solver():
     ed = np.linalg.eigvals(D)
     assert ew.real.min() > 0
     assert ed.real.min() < 0 < ed.real.max()
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count():
+    """The benchmark times the oracle on one thread and on all; each output site is computed
+    independently, so the results are identical."""
+    L = (4, 4, 2, 6)
+    V = ora.volume(L)
+    U = inputs.gauge_field(L, 0.3, 71)
+    psi = inputs.gaussian_source((V, 4, 3), 72)
+    n = ora.num_threads()
+    try:
+        ora.set_num_threads(1)
+        a = ora.wilson(L, BC_T, 0.12, U, psi)
+        ora.set_num_threads(max(n, 2))
+        b = ora.wilson(L, BC_T, 0.12, U, psi)
+    finally:
+        ora.set_num_threads(n)
+    assert np.array_equal(a, b)
