@@ -63,16 +63,19 @@ def run_dwf(args):
         a_ = torch.empty(nb, dtype=torch.uint8, device=dev)
         o_ = torch.empty(nb, dtype=torch.uint8, device=dev)
         qcd.field_pack(g, f, prec, 1, bd, a_)
-        if args.profile != "none":  # ncu: tune, then profile 3 launches of the FP32 hop
+        if args.profile != "none":  # ncu: tune, then profile 3 launches of the FP32 hop (or of Mhat)
+            op = "MHAT" if args.profile == "mhat" else "D_EO"
+            if op == "MHAT":
+                qcd.field_pack(g, f, prec, 0, bd, a_)
             for _ in range(3):
-                qcd.dslash(g, f, "D_EO", a_, o_, prec=prec, layout=qcd.INTERNAL)
+                qcd.dslash(g, f, op, a_, o_, prec=prec, layout=qcd.INTERNAL)
             torch.cuda.synchronize()
             torch.cuda.profiler.start()
             for _ in range(3):
-                qcd.dslash(g, f, "D_EO", a_, o_, prec=prec, layout=qcd.INTERNAL)
+                qcd.dslash(g, f, op, a_, o_, prec=prec, layout=qcd.INTERNAL)
             torch.cuda.synchronize()
             torch.cuda.profiler.stop()
-            print("profile dwf hop done", flush=True)
+            print(f"profile dwf {op} done", flush=True)
             return
         ms = _time_launches(lambda: qcd.dslash(g, f, "D_EO", a_, o_, prec=prec, layout=qcd.INTERNAL))
         ms_m = _time_launches(lambda: qcd.dslash(g, f, "MHAT", a_, o_, prec=prec, layout=qcd.INTERNAL), n=10)

@@ -13,6 +13,8 @@
 // (one thread per (site, complex component) column), and writes the result
 // with the a / x epilogue.  HBM traffic: the links once per site, the input
 // spinors (neighbour re-reads from L2), the output, and x.
+#include <type_traits>
+
 #include "common.cuh"
 #include "dwf_col.cuh"
 #include "internal.h"
@@ -27,7 +29,8 @@ using namespace dwcol;
 
 constexpr int kFusedMaxLs = 32;  // tile of 32 sites x Ls slices x 96 B within 96 KB
 
-// PK = 1: the hop with packed FP32x2 arithmetic (stencil.cuh)
+// PK = 1: the hop with packed FP32x2 arithmetic (stencil.cuh); PK = 2: the same
+// with the links staged as two rows
 template <int P, int RECON, int BY, int PK>
 __global__ void __launch_bounds__(32 * BY) k_dw_hop_w(HopArgs<P, RECON> A, ColCoef<float> c) {
   using R = typename MathType<P>::type;
@@ -43,8 +46,12 @@ __global__ void __launch_bounds__(32 * BY) k_dw_hop_w(HopArgs<P, RECON> A, ColCo
   const int Ls = A.ls;
   const R sg = A.dagger ? R(1) : R(-1);
   if constexpr (PK) {
-    __shared__ SmLinks<float> sm;
-    stage_links_sm<P, RECON, BY>(A, sm, tx, ty, cb, valid);
+    using SM = typename std::conditional<PK == 2, SmLinks12, SmLinks<float>>::type;
+    __shared__ SM sm;
+    if constexpr (PK == 2)
+      stage_links_sm12<P, RECON, BY>(A, sm, tx, ty, cb, valid);
+    else
+      stage_links_sm<P, RECON, BY>(A, sm, tx, ty, cb, valid);
     __syncthreads();
     const SpinorView<P> in = A.in.offset_rhs(r);
     for (int s = ty; s < Ls; s += BY) {
@@ -160,12 +167,14 @@ void launch_fused(FusedLaunch<P, RECON>* L) {
 template <int P, int RECON>
 void run_fused(void* ctx, const LaunchCfg& cfg) {
   auto* L = (FusedLaunch<P, RECON>*)ctx;
-  switch (cfg.tile) {  // BY, + 100 for the packed arithmetic
+  switch (cfg.tile) {  // BY, + 100 for the packed arithmetic, + 200 for that with two-row links
     case 4: launch_fused<P, RECON, 4, 0>(L); break;
     case 16: launch_fused<P, RECON, 16, 0>(L); break;
     case 104: launch_fused<P, RECON, 4, 1>(L); break;
     case 108: launch_fused<P, RECON, 8, 1>(L); break;
     case 116: launch_fused<P, RECON, 16, 1>(L); break;
+    case 204: launch_fused<P, RECON, 4, RECON == 12 ? 2 : 1>(L); break;  // two-row links need 12-real storage
+    case 208: launch_fused<P, RECON, 8, RECON == 12 ? 2 : 1>(L); break;
     default: launch_fused<P, RECON, 8, 0>(L); break;
   }
 }
@@ -199,7 +208,11 @@ void fused_impl(const qcd_gauge* gh, const void* links, const DwParams& p, const
   L.nsb = (unsigned)((gh->lat.Vh + 31) / 32);
   L.nrhs = in.nrhs;
   L.st = st;
-  const std::vector<LaunchCfg> cands = {{128, 4}, {256, 8}, {512, 16}, {128, 104}, {256, 108}, {512, 116}};
+  std::vector<LaunchCfg> cands = {{128, 4}, {256, 8}, {512, 16}, {128, 104}, {256, 108}, {512, 116}};
+  if (RECON == 12) {
+    cands.push_back({128, 204});
+    cands.push_back({256, 208});
+  }
   char key[160];
   snprintf(key, sizeof key, "dwhopw p%d r%d L%dx%dx%dx%d ls%d nrhs%d xp%d mob%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], in.ls, in.nrhs, A.xpay, (int)p.mobius());

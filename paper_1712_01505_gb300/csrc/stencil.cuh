@@ -240,10 +240,58 @@ __device__ __forceinline__ void link_elems(const SmLinks<float>& sm, int L, int 
   }
 }
 
+// Links in shared memory as their first two rows (12 reals, three 16-byte
+// loads per link); row 2 = conj(row0 x row1) is rebuilt in registers by every
+// thread that uses the link: fewer L1/shared-memory wavefronts for ~24 more
+// FP32 instructions per link use.
+struct SmLinks12 {
+  float4 U[8][3][32];        // [2 mu + backward][element pair of rows 0-1][site]
+  int nb[8][32];             // neighbour checkerboard index
+  unsigned char neg[8][32];  // 1 if the hop carries the antiperiodic sign
+};
+
+template <int P, int RECON, int BY>
+__device__ __forceinline__ void stage_links_sm12(const HopArgs<P, RECON>& A, SmLinks12& sm, int tx, int ty, int cb,
+                                                 bool valid) {
+  using R = typename MathType<P>::type;
+  if (!valid) return;
+  SiteCoords c = cb_to_site(A.g, cb, A.out_parity);
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    if (l % BY != ty) continue;
+    const int mu = l >> 1;
+    int wrap;
+    int j = neighbour_index(A.g, c, mu, (l & 1) ? -1 : +1, &wrap);
+    sm.nb[l][tx] = j >> 1;
+    sm.neg[l][tx] = (unsigned char)(wrap && A.g.apbc[mu]);
+    Cx<R> U[9];
+    if ((l & 1) == 0)
+      A.U.load(A.out_parity, mu, cb, U);  // U_mu(x)
+    else
+      A.U.load(1 - A.out_parity, mu, j >> 1, U);  // U_mu(x - mu)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      sm.U[l][k][tx] = make_float4(U[2 * k].re, U[2 * k].im, U[2 * k + 1].re, U[2 * k + 1].im);
+  }
+}
+
+__device__ __forceinline__ void link_elems(const SmLinks12& sm, int L, int tx, float4 e[9]) {
+  Cx<float> u[9];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 v = sm.U[L][k][tx];
+    u[2 * k] = {v.x, v.y};
+    u[2 * k + 1] = {v.z, v.w};
+  }
+  reconstruct_row2(u);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) e[k] = make_float4(u[k].re, u[k].re, u[k].im, u[k].im);
+}
+
 // acc += the hop from direction L (mu = L / 2, backward if L odd) for one slice,
 // packed: g = U h (U^dag h backward) with both spins of h in the lanes
-template <int P, int RECON, int L>
-__device__ __forceinline__ void hop_link_smp(const HopArgs<P, RECON>& A, const SmLinks<float>& sm, int tx, float sg,
+template <int P, int RECON, int L, typename SM>
+__device__ __forceinline__ void hop_link_smp(const HopArgs<P, RECON>& A, const SM& sm, int tx, float sg,
                                              const SpinorView<P>& in, long soff, P2 acc[6]) {
   constexpr int MU = L >> 1;
   constexpr bool BACK = (L & 1) != 0;

@@ -20,6 +20,7 @@
 // accumulation = 1320 flops.
 #include <cstdio>
 #include <string>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -387,16 +388,21 @@ __device__ __forceinline__ void hop_sm(const HopArgs<P, RECON>& A) {
 
 // The shared-memory kernel with packed FP32x2 arithmetic (stencil.cuh): one
 // slice per thread, spinors loaded as spin pairs; RED as in hop_sm.
-template <int P, int RECON, int BY, int RED>
+// L12 = 1: links staged as two rows (SmLinks12), row 2 rebuilt per use
+template <int P, int RECON, int BY, int RED, int L12>
 __device__ __forceinline__ void hop_smp(const HopArgs<P, RECON>& A) {
   if (A.stop && *A.stop) return;
-  __shared__ SmLinks<float> sm;
+  using SM = typename std::conditional<L12 != 0, SmLinks12, SmLinks<float>>::type;
+  __shared__ SM sm;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int sblock = fdiv(blockIdx.x, A.d_ntiles);
   const int stile = blockIdx.x - sblock * A.ntiles;
   const int cb = sblock * 32 + tx;
   const bool valid = cb < A.g.Vh;
-  stage_links_sm<P, RECON, BY>(A, sm, tx, ty, cb, valid);
+  if constexpr (L12 != 0)
+    stage_links_sm12<P, RECON, BY>(A, sm, tx, ty, cb, valid);
+  else
+    stage_links_sm<P, RECON, BY>(A, sm, tx, ty, cb, valid);
   __syncthreads();
   const int q0 = stile * BY + ty;
   if (q0 >= A.nslices) return;      // a whole warp (one row of slices)
@@ -473,15 +479,15 @@ __device__ __forceinline__ void hop_smp(const HopArgs<P, RECON>& A) {
   }
 }
 
-template <int P, int RECON, int BY, int RED>
+template <int P, int RECON, int BY, int RED, int L12>
 __global__ void __launch_bounds__(32 * BY) k_hop_smp(HopArgs<P, RECON> A) {
-  hop_smp<P, RECON, BY, RED>(A);
+  hop_smp<P, RECON, BY, RED, L12>(A);
 }
 
 // the same with the registers bounded so that 24 warps fit on an SM
-template <int P, int RECON, int BY, int RED>
+template <int P, int RECON, int BY, int RED, int L12>
 __global__ void __launch_bounds__(32 * BY, 24 / BY) k_hop_smp_occ(HopArgs<P, RECON> A) {
-  hop_smp<P, RECON, BY, RED>(A);
+  hop_smp<P, RECON, BY, RED, L12>(A);
 }
 
 template <int P, int RECON, int BY, int TS, int RED>
@@ -558,8 +564,8 @@ void launch_sm(HopLaunch<P, RECON>* L) {
     k_hop_sm<P, RECON, BY, TS, RED><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
 }
 
-// OCC = 1: the register-bounded kernel (24 warps per SM)
-template <int P, int RECON, int BY, int RED = 0, int OCC = 0>
+// OCC = 1: the register-bounded kernel (24 warps per SM); L12 = 1: two-row links
+template <int P, int RECON, int BY, int RED = 0, int OCC = 0, int L12 = 0>
 void launch_smp(HopLaunch<P, RECON>* L) {
   HopArgs<P, RECON> A = L->args;
   A.ntiles = (A.nslices + BY - 1) / BY;
@@ -567,9 +573,9 @@ void launch_smp(HopLaunch<P, RECON>* L) {
   long sblocks = (A.g.Vh + 31) / 32;
   const dim3 grid((unsigned)(sblocks * A.ntiles)), blk(32, BY);
   if constexpr (OCC)
-    k_hop_smp_occ<P, RECON, BY, RED><<<grid, blk, 0, L->st>>>(A);
+    k_hop_smp_occ<P, RECON, BY, RED, L12><<<grid, blk, 0, L->st>>>(A);
   else
-    k_hop_smp<P, RECON, BY, RED><<<grid, blk, 0, L->st>>>(A);
+    k_hop_smp<P, RECON, BY, RED, L12><<<grid, blk, 0, L->st>>>(A);
 }
 
 // cfg.tile > 0: register tile of that many slices per thread (k_hop), 101 /
@@ -578,7 +584,8 @@ void launch_smp(HopLaunch<P, RECON>* L) {
 // BY thread rows of TS slices each; -tile = 200 + 10 * BY + TS: the same with at most
 // 64 registers per thread (32 resident warps per SM); -tile = 500 + 10 * BY + 1:
 // packed FP32x2 arithmetic, one slice per thread (k_hop_smp); 600 + ...: the
-// same with the registers bounded for 24 resident warps
+// same with the registers bounded for 24 resident warps; 700 + ...: that with
+// the links staged as two rows
 template <int P, int RECON>
 void run_cfg(void* ctx, const LaunchCfg& cfg) {
   auto* L = (HopLaunch<P, RECON>*)ctx;
@@ -593,6 +600,10 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case -581: L->args.red == 1 ? launch_smp<P, RECON, 8, 1>(L) : launch_smp<P, RECON, 8, 2>(L); break;
       case -641: L->args.red == 1 ? launch_smp<P, RECON, 4, 1, 1>(L) : launch_smp<P, RECON, 4, 2, 1>(L); break;
       case -681: L->args.red == 1 ? launch_smp<P, RECON, 8, 1, 1>(L) : launch_smp<P, RECON, 8, 2, 1>(L); break;
+      case -741: L->args.red == 1 ? launch_smp<P, RECON, 4, 1, 1, RECON == 12>(L)
+                                  : launch_smp<P, RECON, 4, 2, 1, RECON == 12>(L); break;
+      case -781: L->args.red == 1 ? launch_smp<P, RECON, 8, 1, 1, RECON == 12>(L)
+                                  : launch_smp<P, RECON, 8, 2, 1, RECON == 12>(L); break;
       default: L->args.red == 1 ? launch_sm<P, RECON, 4, 1, 1>(L) : launch_sm<P, RECON, 4, 1, 2>(L);
     }
   } else {
@@ -611,6 +622,8 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case -581: launch_smp<P, RECON, 8>(L); break;
       case -641: launch_smp<P, RECON, 4, 0, 1>(L); break;
       case -681: launch_smp<P, RECON, 8, 0, 1>(L); break;
+      case -741: launch_smp<P, RECON, 4, 0, 1, RECON == 12>(L); break;  // 18-real: the -641 kernel
+      case -781: launch_smp<P, RECON, 8, 0, 1, RECON == 12>(L); break;
       default: launch_sm<P, RECON, 8, 2>(L); break;
     }
   }
@@ -667,10 +680,13 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64 && A.nslices >= 16) cands.push_back({256, -82});
   if (P == P32 && A.nslices >= 4) cands.push_back({128, -241});
   if (P == P32 && A.nslices >= 8) cands.push_back({256, -281});
+  // (two-row staging, -7x1, only where the links are stored as 12 reals: row 2 is then rebuilt anyway)
   if (P != P64 && A.nslices >= 4)
-    for (int t : {-541, -641}) cands.push_back({128, t});
+    for (int t : {-541, -641, -741})
+      if (t != -741 || RECON == 12) cands.push_back({128, t});
   if (P != P64 && A.nslices >= 8)
-    for (int t : {-581, -681}) cands.push_back({256, t});
+    for (int t : {-581, -681, -781})
+      if (t != -781 || RECON == 12) cands.push_back({256, t});
   if (A.red) {  // the fused reduction exists for one slice per thread only
     cands.clear();
     for (int b : blocks) cands.push_back({b, 1});
@@ -678,8 +694,13 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64)  // one slice per thread with prefetches (memory-bound precisions)
     for (int pf : {101, 201})
       for (int b : blocks) cands.push_back({b, pf});
-  if (multi_red)
-    cands = {{128, -41}, {256, -81}, {128, -241}, {256, -281}, {128, -541}, {256, -581}, {128, -641}, {256, -681}};  // shared-memory links, one slice per thread
+  if (multi_red) {  // shared-memory links, one slice per thread
+    cands = {{128, -41}, {256, -81}, {128, -241}, {256, -281}, {128, -541}, {256, -581}, {128, -641}, {256, -681}};
+    if (RECON == 12) {
+      cands.push_back({128, -741});
+      cands.push_back({256, -781});
+    }
+  }
   char key[160];
   snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d red%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay, A.red);

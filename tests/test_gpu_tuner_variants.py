@@ -96,13 +96,16 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
     device()
     # (tile code, block) of every candidate family; the shared-memory kernels fix their block
     shapes = [(1, 128), (2, 64), (4, 256), (101, 64), (201, 128), (-41, 128), (-42, 128), (-81, 256), (-82, 256),
-              (-241, 128), (-281, 256), (-541, 128), (-581, 256), (-641, 128), (-681, 256)]
+              (-241, 128), (-281, 256), (-541, 128), (-581, 256), (-641, 128), (-681, 256), (-741, 128),
+              (-781, 256)]
     cases, lines, tol = [], [], []
     t = 4
     for prec, recon in (("f32", 12), ("f32", 18), ("f16", 12)):
         for tile, block in shapes:
             if tile in (-241, -281) and prec != "f32":
                 continue  # the register-bounded shapes are FP32 only
+            if tile in (-741, -781) and recon != 12:
+                continue  # two-row link staging exists for 12-real links only
             L = (4, 4, 4, t)
             t += 2
             cases.append({"kind": "hop", "L": L, "prec": prec, "recon": recon, "nrhs": 16})
@@ -118,7 +121,7 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
         tol.append(1e-10)
     # the fused-reduction shared-memory stencils of the batched (several rhs) iteration
     for tile, block in ((-41, 128), (-81, 256), (-241, 128), (-281, 256), (-541, 128), (-581, 256),
-                        (-641, 128), (-681, 256)):
+                        (-641, 128), (-681, 256), (-741, 128), (-781, 256)):
         L = (4, 4, 8, t)
         t += 2
         cases.append({"kind": "solve", "L": L, "recon": 12, "nrhs": 4})
@@ -126,7 +129,7 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
             lines.append(f"{_key(L, 'f32', 12, 4, xp, red)}\t{block}\t{tile}")
         tol.append(1e-10)
     # the fused-reduction shared-memory stencils of the domain-wall CG (Re(p, q) over all slices)
-    for tile, block in ((-41, 128), (-81, 256), (-581, 256), (-641, 128)):
+    for tile, block in ((-41, 128), (-81, 256), (-581, 256), (-641, 128), (-781, 256)):
         L = (4, 4, 2, t)
         t += 2
         cases.append({"kind": "dwsolve", "L": L, "recon": 12, "Ls": 8})
@@ -134,7 +137,7 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
         tol.append(1e-10)
     # the domain-wall stencil with W in its epilogue: thread rows 4 / 8 / 16, plain or packed
     # arithmetic, Shamir and Mobius, FP32 and FP16, both adjoints of Mhat
-    for tile, block in ((4, 128), (8, 256), (16, 512), (104, 128), (108, 256), (116, 512)):
+    for tile, block in ((4, 128), (8, 256), (16, 512), (104, 128), (108, 256), (116, 512), (204, 128), (208, 256)):
         for prec, mob in (("f32", 0), ("f16", 1)):
             L = (4, 2, 4, t)
             t += 2
