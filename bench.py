@@ -50,6 +50,7 @@ NDSLASH = 10
 FLOP_SITE = metrics.HOP_FLOP_SITE      # 1320 per output site of one half-dslash (hopping term)
 BYTES_SITE_FP32 = {r: int(metrics.hop_compulsory_bytes("f32", r)) for r in (12, 18)}  # links + in + out
 BYTES_SITE_FP64 = int(metrics.hop_compulsory_bytes("f64", 18))
+BYTES_SITE_FP16 = int(metrics.hop_compulsory_bytes("f16", RECON))
 WORKLOAD = "wilson_32x32x32x64_kappa0.125_eps0.2_z2"
 PROFILE = os.path.join(ROOT, "profiles", "wilson_dslash_fp32_32x32x32x64.md")
 KERNEL_SOURCES = ["paper_1712_01505_gb300/csrc/wilson.cu", "paper_1712_01505_gb300/csrc/stencil.cuh",
@@ -395,6 +396,33 @@ def main():
     other_outer = {"outer": other, "ms": round(e0.elapsed_time(e1), 3), "iters": info_o[0]["iters"],
                    "updates": info_o[0]["outer_updates"], "true_resid": info_o[0]["true_resid"]}
 
+    # ---- the mixed solve with FP16 inner iterations (per-site scaled spinors, 12-real FP16
+    # links, FP32 arithmetic), once, and the standalone FP16 D_eo
+    x_dev.zero_()
+    kw16 = dict(solve_kw, inner="f16", delta=0.0)  # the library's FP16 reliable-update factor
+    qcd.solve(g, f, b_dev, x_dev, **kw16)  # warm-up (tuning, workspace, graphs)
+    x_dev.zero_()
+    e0.record(stream)
+    info16, _ = qcd.solve(g, f, b_dev, x_dev, check=False, **kw16)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    f16_inner = {"ms": round(e0.elapsed_time(e1), 3), "iters": info16[0]["iters"],
+                 "updates": info16[0]["outer_updates"], "true_resid": info16[0]["true_resid"],
+                 "converged": bool(info16[0]["converged"])}
+    nb16 = qcd.field_bytes(g, f, "f16")
+    in16 = torch.empty(nb16, dtype=torch.uint8, device=dev)
+    out16 = torch.empty(nb16, dtype=torch.uint8, device=dev)
+    qcd.field_pack(g, f, "f16", 1, b_dev, in16)
+    for _ in range(3):
+        qcd.dslash(g, f, "D_EO", in16, out16, prec="f16", layout=qcd.INTERNAL)
+    e0.record(stream)
+    for _ in range(10):
+        qcd.dslash(g, f, "D_EO", in16, out16, prec="f16", layout=qcd.INTERNAL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    d16_ms = e0.elapsed_time(e1) / 10
+    del in16, out16
+
     # ---- standalone FP64 D_eo rate (ALU-bound on GB300)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -422,7 +450,7 @@ def main():
     x_host = torch.zeros((V, 4, 3), dtype=torch.complex128).pin_memory().numpy()
     o_host = torch.zeros((V, 4, 3), dtype=torch.complex128).pin_memory().numpy()
     e2e_ms = []
-    for rep in range(2):
+    for rep in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         qcd.dslash(g, f, "D_EO", b_host, o_host, prec="f32")
@@ -461,11 +489,15 @@ def main():
                    "fp64_gbs": round(BYTES_SITE_FP64 * Vh / (d64_ms / 1e3) / 1e9, 1),
                    "df64_ms": round(ddf_ms, 4),
                    "df64_gflops": round(FLOP_SITE * Vh / (ddf_ms / 1e3) / 1e9, 1),
-                   "df64_gbs": round(BYTES_SITE_FP64 * Vh / (ddf_ms / 1e3) / 1e9, 1)},
+                   "df64_gbs": round(BYTES_SITE_FP64 * Vh / (ddf_ms / 1e3) / 1e9, 1),
+                   "fp16_ms": round(d16_ms, 4),
+                   "fp16_gflops": round(FLOP_SITE * Vh / (d16_ms / 1e3) / 1e9, 1),
+                   "fp16_gbs": round(BYTES_SITE_FP16 * Vh / (d16_ms / 1e3) / 1e9, 1),
+                   "fp16_frac": round(BYTES_SITE_FP16 * Vh / (d16_ms / 1e3) / 1e9 / hbm, 4)},
         "solve": {"mixed_ms": round(mixed_ms, 3), "mixed_iters": infos[-1]["iters"],
                   "mixed_updates": infos[-1]["outer_updates"], "mixed_true_resid": infos[-1]["true_resid"],
                   "fp64": fp64, "speedup_vs_fp64": round(fp64["ms"] / mixed_ms, 3) if fp64 else None,
-                  "other_outer": other_outer},
+                  "other_outer": other_outer, "f16_inner": f16_inner},
         "e2e": {"value": round(e2e_val, 3), "unit": "GFLOP/s", "ms": round(min(e2e_ms), 3),
                 "h2d_bytes_per_step": 2 * spinor_bytes, "d2h_bytes_per_step": 2 * spinor_bytes},
         "gpu_launches": n_launch,
