@@ -141,8 +141,9 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(U, psi, budget_s=12.0):
-    """The FP64 oracle's hopping term D_eo on the full lattice, timed on the host cores."""
+def cpu_baseline(U, psi, budget_s=12.0, solve=True):
+    """The FP64 oracle's hopping term D_eo on the full lattice, timed on the host cores (all of
+    them and one), and its FP64 solve of the benchmark system."""
     from oracle import oracle as ora
 
     par = ora.parity(L)
@@ -171,11 +172,18 @@ def cpu_baseline(U, psi, budget_s=12.0):
                 break
     finally:
         ora.set_num_threads(cores)
-    return {"value": round(gflops, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-            "sample": f"{reps} oracle FP64 D_eo applications on the full 32^3x64 lattice "
-                      f"({Vh} output sites each, {el:.1f} s)",
-            "value_1thread": round(FLOP_SITE * Vh * reps1 / el1 / 1e9, 4),
-            "sample_1thread": f"{reps1} applications on one thread ({el1:.1f} s)"}
+    out = {"value": round(gflops, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+           "sample": f"{reps} oracle FP64 D_eo applications on the full 32^3x64 lattice "
+                     f"({Vh} output sites each, {el:.1f} s)",
+           "value_1thread": round(FLOP_SITE * Vh * reps1 / el1 / 1e9, 4),
+           "sample_1thread": f"{reps1} applications on one thread ({el1:.1f} s)"}
+    if solve:  # the oracle's FP64 even-odd BiCGStab on the same system, to the same 1e-10
+        t0 = time.perf_counter()
+        _, it, res = ora.wilson_solve(L, BC, KAPPA, U, psi, tol=TOL)
+        out["solve_s"] = round(time.perf_counter() - t0, 2)
+        out["solve_iters"] = it
+        out["solve_true_resid"] = res
+    return out
 
 
 def run_reference(args):

@@ -178,3 +178,79 @@ def test_mhat_at_the_fused_limit_and_beyond(Ls, mobius):
             qcd.dslash(g, f, "MHAT_DAG" if dag else "MHAT", to_dev(psi), out, prec=prec)
             torch.cuda.synchronize()
             _check(out, ora.mobius_mhat(L, BC, Ls, M5, MF, b5, c5, U, pe, dagger=dag), prec)
+
+
+def _neighbours(L, sites):
+    """Canonical indices of the 8 neighbours (x +- mu) of each canonical site; shape (n, 8)."""
+    Lx, Ly, Lz, Lt = L
+    x = sites % Lx
+    y = (sites // Lx) % Ly
+    z = (sites // (Lx * Ly)) % Lz
+    t = sites // (Lx * Ly * Lz)
+    c = [x, y, z, t]
+    out = []
+    for mu in range(4):
+        for d in (1, -1):
+            cc = list(c)
+            cc[mu] = (cc[mu] + d) % L[mu]
+            out.append(cc[0] + Lx * (cc[1] + Ly * (cc[2] + Lz * cc[3])))
+    return np.stack(out, axis=1)
+
+
+def _mhat_sampled(L, Ls, b5, c5, U, psi, xs, dagger):
+    """(Mhat psi_e)(x) at even sites xs for all slices, from the oracle's site-restricted hop and
+    the dense fifth-dimension blocks: Mhat = 1 - 1/4 W H_eo W H_oe (adjoint: with W^T and H^dag,
+    W^T applied first)."""
+    V = int(np.prod(L))
+    par = ora.parity(L)
+    pe = psi.copy()
+    pe[:, par == 1] = 0
+    if dagger:
+        pe = ora.mobius_block(Ls, M5, MF, b5, c5, "W", pe, dagger=True)
+        pe[:, par == 1] = 0
+    ys = np.unique(_neighbours(L, xs).reshape(-1))  # odd neighbours of the sampled even sites
+    t1 = np.stack([ora.hop_sites(L, BC, U, pe[s], ys, dagger=dagger) for s in range(Ls)])
+    if not dagger:
+        t1 = ora.mobius_block(Ls, M5, MF, b5, c5, "W", t1)
+    else:
+        t1 = ora.mobius_block(Ls, M5, MF, b5, c5, "W", t1, dagger=True)
+    u = np.empty((Ls, len(xs), 4, 3), dtype=complex)
+    for s in range(Ls):
+        full = np.zeros((V, 4, 3), dtype=complex)
+        full[ys] = t1[s]
+        u[s] = ora.hop_sites(L, BC, U, full, xs, dagger=dagger)
+    if not dagger:
+        u = ora.mobius_block(Ls, M5, MF, b5, c5, "W", u)
+    return psi[:, xs] - 0.25 * u
+
+
+@pytest.mark.parametrize("mobius", [False, True])
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_full_size_fused_mhat_on_sampled_sites(mobius, prec):
+    """Domain-wall benchmark lattice (16^3 x 32, Ls = 16, eps = 0.2 links seed 3, Gaussian source
+    seed 0): Mhat and Mhat^dag in the benchmark's INTERNAL-layout launches (the hop with W in its
+    epilogue, tuner-chosen shape), checked on sampled even sites the oracle computes one by one."""
+    device()
+    L, Ls = (16, 16, 16, 32), 16
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.2, 3)
+    psi = inputs.gaussian_source((Ls, V, 4, 3), 0)
+    even = np.flatnonzero(ora.parity(L) == 0)
+    rng = np.random.default_rng(17)
+    xs = np.concatenate([even[:8], even[-8:], rng.choice(even, 32, replace=False)])
+    b5, c5 = (B5, C5) if mobius else (1.0, 0.0)
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=12)
+    f = qcd.mobius(Ls, M5, MF, b5, c5)
+    nb = qcd.field_bytes(g, f, prec)
+    bi = torch.empty(nb, dtype=torch.uint8, device=device())
+    bo = torch.empty(nb, dtype=torch.uint8, device=device())
+    qcd.field_pack(g, f, prec, 0, to_dev(psi), bi)
+    out = torch.zeros((Ls, V, 4, 3), dtype=torch.complex128, device=device())
+    idx = torch.from_numpy(xs).to(device())
+    for dag in (False, True):
+        qcd.dslash(g, f, "MHAT_DAG" if dag else "MHAT", bi, bo, prec=prec, layout=qcd.INTERNAL)
+        qcd.field_unpack(g, f, prec, 0, bo, out)
+        torch.cuda.synchronize()
+        ref = _mhat_sampled(L, Ls, b5, c5, U, psi, xs, dag)
+        assert rel_err(out[:, idx].cpu().numpy(), ref) < TOL[prec], (dag, prec)
+    g.free()
