@@ -20,6 +20,18 @@
 
 namespace qcd {
 
+// ----------------------------------------------------------------------------- launch order
+// Programmatic dependent launch (sm_90 and later): a kernel launched with the
+// programmatic-serialization attribute (launch_k in internal.h) may be scheduled
+// while its predecessor in the stream finishes.  pdl_enter(), the first statement
+// of such a kernel, waits until the predecessor grid has completed and its memory
+// operations are visible, then allows the next kernel to begin launching.  Without
+// a programmatic predecessor both instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ----------------------------------------------------------------------------- complex
 template <typename R>
 struct Cx {

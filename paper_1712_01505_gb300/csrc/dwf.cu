@@ -45,6 +45,7 @@ using namespace dwcol;
 template <typename R>
 __global__ void __launch_bounds__(256) k_col(ColCoef<R> c, AnyView in, AnyView out, long Vh, int dagger, R scale,
                                              AnyView x, int has_x, const int* stop) {
+  pdl_enter();
   if (stop && *stop) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
@@ -174,10 +175,10 @@ void run_col(const DwParams& p, const ColSpec& spec, const Field& in, Field& out
     attr_set = true;
   }
   if (dbl)
-    k_col<double><<<grid, blk, smem, st>>>(make_coef<double>(p, spec), any_view(in), any_view(out), in.Vh, dagger,
+    launch_k(k_col<double>, grid, blk, smem, st, make_coef<double>(p, spec), any_view(in), any_view(out), in.Vh, dagger,
                                            scale, xv, x != nullptr, stop);
   else
-    k_col<float><<<grid, blk, smem, st>>>(make_coef<float>(p, spec), any_view(in), any_view(out), in.Vh, dagger,
+    launch_k(k_col<float>, grid, blk, smem, st, make_coef<float>(p, spec), any_view(in), any_view(out), in.Vh, dagger,
                                           (float)scale, xv, x != nullptr, stop);
   QCD_LAUNCH_CK();
 }

@@ -33,6 +33,7 @@ constexpr int kFusedMaxLs = 32;  // tile of 32 sites x Ls slices x 96 B within 9
 // with the links staged as two rows
 template <int P, int RECON, int BY, int PK>
 __global__ void __launch_bounds__(32 * BY) k_dw_hop_w(HopArgs<P, RECON> A, ColCoef<float> c) {
+  pdl_enter();
   using R = typename MathType<P>::type;
   static_assert(sizeof(R) == 4, "the fused stencil computes in FP32");
   if (A.stop && *A.stop) return;
@@ -160,7 +161,7 @@ void launch_fused(FusedLaunch<P, RECON>* L) {
                                 kFusedMaxLs * 24 * 32 * (int)sizeof(float)));
     attr_set = true;
   }
-  k_dw_hop_w<P, RECON, BY, PK><<<dim3(L->nsb, (unsigned)L->nrhs), dim3(32, BY), L->smem, L->st>>>(L->args,
+  launch_k(k_dw_hop_w<P, RECON, BY, PK>, dim3(L->nsb, (unsigned)L->nrhs), dim3(32, BY), L->smem, L->st, L->args,
                                                                                                   L->coef);
 }
 

@@ -35,6 +35,24 @@ void set_launches(long n);
     ::qcd::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__); \
   } while (0)
 
+// Launch a kernel with the programmatic-serialization attribute (unless QCD_PDL=0):
+// every kernel launched this way starts with pdl_enter() (common.cuh).
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  ::qcd::cuda_check(cudaLaunchKernelEx(&cfg, kernel, args...), "kernel launch", __FILE__, __LINE__);
+}
+
 // ----------------------------------------------------------------------------- lattice
 struct Lattice {
   int L[4];

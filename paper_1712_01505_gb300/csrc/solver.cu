@@ -101,6 +101,7 @@ __device__ __forceinline__ void write_partial(double v[NR], double* partial, int
 // p = r + beta (p - omega v); rho = rho_new
 template <typename R>
 __global__ void k_bicg_p(AnyView r_, AnyView p_, AnyView v_, long n, Scal* sc, const int* ctl) {
+  pdl_enter();
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
   Scal& s = sc[r];
@@ -127,6 +128,7 @@ __global__ void k_bicg_p(AnyView r_, AnyView p_, AnyView v_, long n, Scal* sc, c
 // partial sums of (a, b) = sum conj(a) b  -> [re, im]
 template <typename R>
 __global__ void k_cdot(AnyView a_, AnyView b_, long n, double* partial, const Scal* sc, const int* ctl) {
+  pdl_enter();
   if (ctl && STOPPED(ctl)) return;
   int r = blockIdx.y;
   if (sc && !sc[r].active) return;
@@ -217,6 +219,7 @@ __device__ __forceinline__ bool block_omega(Scal& s, const double* partial, int 
 template <typename R>
 __global__ void k_bicg_s(AnyView r_, AnyView v_, AnyView s_, long n, Scal* sc, int* ctl, const double* partial,
                          int nblk, const int* nb_dev) {
+  pdl_enter();
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
   Scal& s = sc[r];
@@ -237,6 +240,7 @@ __global__ void k_bicg_s(AnyView r_, AnyView v_, AnyView s_, long n, Scal* sc, i
 // partial sums of (t, s) [re, im] and |t|^2
 template <typename R>
 __global__ void k_ts_tt(AnyView t_, AnyView s_, long n, double* partial, const Scal* sc, const int* ctl) {
+  pdl_enter();
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
   if (!sc[r].active) return;
@@ -265,6 +269,7 @@ template <typename R, typename RX>
 __global__ void k_bicg_xr(AnyView x_, AnyView p_, AnyView s_, AnyView t_, AnyView r_, AnyView rt_,
                           long n, const double* partial_in, int nblk, const int* nb_dev, double* partial_out,
                           Scal* sc, int* ctl) {
+  pdl_enter();
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
   Scal& s = sc[r];
@@ -310,6 +315,7 @@ __global__ void k_bicg_xr(AnyView x_, AnyView p_, AnyView s_, AnyView t_, AnyVie
 // and the next beta; with decide != 0 (one right-hand side) any flag stops the chunk
 // at once, otherwise k_decide weighs the flags of all right-hand sides
 __global__ void k_bicg_check(Scal* sc, const double* partial, int nblk, int* ctl, int decide) {
+  pdl_enter();
   if (STOPPED(ctl)) return;
   int r = blockIdx.x;
   Scal& s = sc[r];
@@ -343,6 +349,7 @@ __global__ void k_bicg_check(Scal* sc, const double* partial, int nblk, int* ctl
 // p = r + beta p; rr = rr_new
 template <typename R>
 __global__ void k_cg_p(AnyView r_, AnyView p_, long n, Scal* sc, const int* ctl) {
+  pdl_enter();
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
   Scal& s = sc[r];
@@ -391,6 +398,7 @@ __device__ __forceinline__ bool block_cg_alpha(Scal& s, const double* partial, i
 template <typename R, typename RX>
 __global__ void k_cg_xr(AnyView x_, AnyView p_, AnyView q_, AnyView r_, long n, const double* partial_in,
                         int nblk, const int* nb_dev, double* partial_out, Scal* sc, int* ctl) {
+  pdl_enter();
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
   Scal& s = sc[r];
@@ -425,6 +433,7 @@ __global__ void k_cg_xr(AnyView x_, AnyView p_, AnyView q_, AnyView r_, long n, 
 
 // end of an iteration: rr_new, flags and the next beta; decide as in k_bicg_check
 __global__ void k_cg_check(Scal* sc, const double* partial, int nblk, int* ctl, int decide) {
+  pdl_enter();
   if (STOPPED(ctl)) return;
   int r = blockIdx.x;
   Scal& s = sc[r];
@@ -449,6 +458,7 @@ __global__ void k_cg_check(Scal* sc, const double* partial, int nblk, int* ctl, 
 // partial sums of Re(a, b)
 template <typename R>
 __global__ void k_rdot(AnyView a_, AnyView b_, long n, double* partial, const Scal* sc, const int* ctl) {
+  pdl_enter();
   if (STOPPED(ctl)) return;
   int r = blockIdx.y;
   if (!sc[r].active) return;
@@ -474,6 +484,7 @@ __global__ void k_reset(int* ctl) { *ctl = 0; }
 // further factor 10 past its trigger (or breakdown / NaN, which stop at once
 // where they are detected).
 __global__ void k_decide(const Scal* sc, int nrhs, int* ctl) {
+  pdl_enter();
   if (STOPPED(ctl) || threadIdx.x) return;
   int nact = 0, nflag = 0, urgent = 0;
   for (int r = 0; r < nrhs; ++r) {
@@ -544,7 +555,7 @@ struct Solver {
   template <typename R, typename RX>
   void body_t(dim3 grid, long nn, int dag) {
     if (bicg()) {
-      k_bicg_p<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(p), any_view(v), nn, sc, ctl);
+      launch_k(k_bicg_p<R>, grid, kThreads, 0, st, any_view(r), any_view(p), any_view(v), nn, sc, ctl);
       QCD_LAUNCH_CK();
       if (fused()) {
         // (rt, v) and (t, s), |t|^2 formed in the epilogue of the stencil that writes v / t
@@ -552,7 +563,7 @@ struct Solver {
         RedSpec red1{1, &rt, bpartial, partial, counters, npart};
         RedSpec red2{2, nullptr, bpartial, partial, counters, npart};
         apply_mhat(opin, p, v, dag, st, "in", ctl, &red1);
-        k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
+        launch_k(k_bicg_s<R>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
                                                npart);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl, &red2);
@@ -561,34 +572,34 @@ struct Solver {
         RedSpec red1{1, &rt, bpartial, partial, nullptr, nullptr};
         RedSpec red2{2, nullptr, bpartial, partial, nullptr, nullptr};
         apply_mhat(opin, p, v, dag, st, "in", ctl, &red1);
-        k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, 1,
+        launch_k(k_bicg_s<R>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, 1,
                                                nullptr);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl, &red2);
       } else {
         apply_mhat(opin, p, v, dag, st, "in", ctl);
-        k_cdot<R><<<grid, kThreads, 0, st>>>(any_view(rt), any_view(v), nn, partial, sc, ctl);
+        launch_k(k_cdot<R>, grid, kThreads, 0, st, any_view(rt), any_view(v), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
-        k_bicg_s<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
+        launch_k(k_bicg_s<R>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
                                                nullptr);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl);
-        k_ts_tt<R><<<grid, kThreads, 0, st>>>(any_view(t), any_view(s), nn, partial, sc, ctl);
+        launch_k(k_ts_tt<R>, grid, kThreads, 0, st, any_view(t), any_view(s), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
       }
-      k_bicg_xr<R, RX><<<grid, kThreads, 0, st>>>(any_view(xin), any_view(p), any_view(s), any_view(t),
+      launch_k(k_bicg_xr<R, RX>, grid, kThreads, 0, st, any_view(xin), any_view(p), any_view(s), any_view(t),
                                                   any_view(r), any_view(rt), nn, partial,
                                                   fused_multi() ? 1 : (int)nblk, fused() ? ctl + 2 : nullptr,
                                                   partial2, sc, ctl);
       QCD_LAUNCH_CK();
-      k_bicg_check<<<nrhs, kThreads, 0, st>>>(sc, partial2, nblk, ctl, nrhs == 1);
+      launch_k(k_bicg_check, nrhs, kThreads, 0, st, sc, partial2, nblk, ctl, nrhs == 1);
       QCD_LAUNCH_CK();
       if (nrhs > 1) {
-        k_decide<<<1, 32, 0, st>>>(sc, nrhs, ctl);
+        launch_k(k_decide, 1, 32, 0, st, sc, nrhs, ctl);
         QCD_LAUNCH_CK();
       }
     } else {
-      k_cg_p<R><<<grid, kThreads, 0, st>>>(any_view(r), any_view(p), nn, sc, ctl);
+      launch_k(k_cg_p<R>, grid, kThreads, 0, st, any_view(r), any_view(p), nn, sc, ctl);
       QCD_LAUNCH_CK();
       apply_mhat(opin, p, w, 0, st, "in", ctl);
       int nb = (int)nblk;
@@ -603,16 +614,16 @@ struct Solver {
           nb = ls;  // one sum per slice
       } else {
         apply_mhat(opin, w, q, 1, st, "in", ctl);
-        k_rdot<R><<<grid, kThreads, 0, st>>>(any_view(p), any_view(q), nn, partial, sc, ctl);
+        launch_k(k_rdot<R>, grid, kThreads, 0, st, any_view(p), any_view(q), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
       }
-      k_cg_xr<R, RX><<<grid, kThreads, 0, st>>>(any_view(xin), any_view(p), any_view(q), any_view(r),
+      launch_k(k_cg_xr<R, RX>, grid, kThreads, 0, st, any_view(xin), any_view(p), any_view(q), any_view(r),
                                                 nn, partial, nb, nb_dev, partial2, sc, ctl);
       QCD_LAUNCH_CK();
-      k_cg_check<<<nrhs, kThreads, 0, st>>>(sc, partial2, nblk, ctl, nrhs == 1);
+      launch_k(k_cg_check, nrhs, kThreads, 0, st, sc, partial2, nblk, ctl, nrhs == 1);
       QCD_LAUNCH_CK();
       if (nrhs > 1) {
-        k_decide<<<1, 32, 0, st>>>(sc, nrhs, ctl);
+        launch_k(k_decide, 1, 32, 0, st, sc, nrhs, ctl);
         QCD_LAUNCH_CK();
       }
     }
@@ -672,10 +683,10 @@ struct Solver {
   void cdot_host(const Field& a, const Field& b, std::vector<double>& re, std::vector<double>& im) {
     dim3 grid(nblk, nrhs);
     if (a.prec == QCD_F64)
-      k_cdot<double><<<grid, kThreads, 0, st>>>(any_view(a), any_view(b), a.nsites(), partial, nullptr,
+      launch_k(k_cdot<double>, grid, kThreads, 0, st, any_view(a), any_view(b), a.nsites(), partial, nullptr,
                                                 nullptr);
     else
-      k_cdot<float><<<grid, kThreads, 0, st>>>(any_view(a), any_view(b), a.nsites(), partial, nullptr,
+      launch_k(k_cdot<float>, grid, kThreads, 0, st, any_view(a), any_view(b), a.nsites(), partial, nullptr,
                                                nullptr);
     QCD_LAUNCH_CK();
     std::vector<double> h((size_t)nblk * nrhs * kMaxPartial);

@@ -66,6 +66,14 @@ void set_tuning(int mode) {
   g_mode = mode;
 }
 
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("QCD_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 int sm_count() {
   static int n = 0;
   if (!n) {

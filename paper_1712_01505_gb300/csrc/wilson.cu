@@ -148,6 +148,7 @@ __device__ __forceinline__ void prefetch_before(const HopArgs<P, RECON>& A, cons
 
 template <int P, int RECON, int TILE, int PF>
 __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
+  pdl_enter();
   using R = typename MathType<P>::type;
   if (A.stop && *A.stop) return;
   // block -> (site block, slice tile), tiles of one site block adjacent in
@@ -203,6 +204,7 @@ constexpr int kRedGroup = 64;
 
 template <int P, int RECON, int RED, int PF>
 __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
+  pdl_enter();
   using R = typename MathType<P>::type;
   if (A.stop && *A.stop) return;
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
@@ -481,29 +483,34 @@ __device__ __forceinline__ void hop_smp(const HopArgs<P, RECON>& A) {
 
 template <int P, int RECON, int BY, int RED, int L12>
 __global__ void __launch_bounds__(32 * BY) k_hop_smp(HopArgs<P, RECON> A) {
+  pdl_enter();
   hop_smp<P, RECON, BY, RED, L12>(A);
 }
 
 // the same with the registers bounded so that 24 warps fit on an SM
 template <int P, int RECON, int BY, int RED, int L12>
 __global__ void __launch_bounds__(32 * BY, 24 / BY) k_hop_smp_occ(HopArgs<P, RECON> A) {
+  pdl_enter();
   hop_smp<P, RECON, BY, RED, L12>(A);
 }
 
 template <int P, int RECON, int BY, int TS, int RED>
 __global__ void __launch_bounds__(32 * BY) k_hop_sm(HopArgs<P, RECON> A) {
+  pdl_enter();
   hop_sm<P, RECON, BY, TS, RED>(A);
 }
 
 // the same with the registers bounded so that 1024 threads (32 warps) fit on an SM
 template <int P, int RECON, int BY, int TS, int RED>
 __global__ void __launch_bounds__(32 * BY, 32 / BY) k_hop_sm_occ(HopArgs<P, RECON> A) {
+  pdl_enter();
   hop_sm<P, RECON, BY, TS, RED>(A);
 }
 
 // per slice q: out[q * 4 + k] = sum over the nsb site blocks of partial[(q * nsb + b) * 4 + k]
 // in a fixed order (one block per slice); the consumer adds the ls slices of a right-hand side
 __global__ void k_red_rows(const double* __restrict__ partial, long nsb, double* __restrict__ out) {
+  pdl_enter();
   const int q = blockIdx.x;
   double v[3] = {0.0, 0.0, 0.0};
   for (long b = threadIdx.x; b < nsb; b += blockDim.x)
@@ -541,15 +548,15 @@ void launch_tile(HopLaunch<P, RECON>* L, int block) {
   long sblocks = (A.g.Vh + block - 1) / block;
   if constexpr (TILE == 1 && P != P16) {
     if (A.red == 1) {
-      k_hop_red<P, RECON, 1, PF><<<(unsigned)sblocks, block, 0, L->st>>>(A);
+      launch_k(k_hop_red<P, RECON, 1, PF>, (unsigned)sblocks, block, 0, L->st, A);
       return;
     }
     if (A.red == 2) {
-      k_hop_red<P, RECON, 2, PF><<<(unsigned)sblocks, block, 0, L->st>>>(A);
+      launch_k(k_hop_red<P, RECON, 2, PF>, (unsigned)sblocks, block, 0, L->st, A);
       return;
     }
   }
-  k_hop<P, RECON, TILE, PF><<<(unsigned)(sblocks * A.ntiles), block, 0, L->st>>>(A);
+  launch_k(k_hop<P, RECON, TILE, PF>, (unsigned)(sblocks * A.ntiles), block, 0, L->st, A);
 }
 
 template <int P, int RECON, int BY, int TS, int RED = 0, int OCC = 0>
@@ -559,9 +566,9 @@ void launch_sm(HopLaunch<P, RECON>* L) {
   A.d_ntiles = make_fastdiv((unsigned)A.ntiles);
   long sblocks = (A.g.Vh + 31) / 32;
   if constexpr (OCC)
-    k_hop_sm_occ<P, RECON, BY, TS, RED><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
+    launch_k(k_hop_sm_occ<P, RECON, BY, TS, RED>, (unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st, A);
   else
-    k_hop_sm<P, RECON, BY, TS, RED><<<(unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st>>>(A);
+    launch_k(k_hop_sm<P, RECON, BY, TS, RED>, (unsigned)(sblocks * A.ntiles), dim3(32, BY), 0, L->st, A);
 }
 
 // OCC = 1: the register-bounded kernel (24 warps per SM); L12 = 1: two-row links
@@ -573,9 +580,9 @@ void launch_smp(HopLaunch<P, RECON>* L) {
   long sblocks = (A.g.Vh + 31) / 32;
   const dim3 grid((unsigned)(sblocks * A.ntiles)), blk(32, BY);
   if constexpr (OCC)
-    k_hop_smp_occ<P, RECON, BY, RED, L12><<<grid, blk, 0, L->st>>>(A);
+    launch_k(k_hop_smp_occ<P, RECON, BY, RED, L12>, grid, blk, 0, L->st, A);
   else
-    k_hop_smp<P, RECON, BY, RED, L12><<<grid, blk, 0, L->st>>>(A);
+    launch_k(k_hop_smp<P, RECON, BY, RED, L12>, grid, blk, 0, L->st, A);
 }
 
 // cfg.tile > 0: register tile of that many slices per thread (k_hop), 101 /
@@ -708,7 +715,7 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   run_cfg<P, RECON>(&L, cfg);
   QCD_LAUNCH_CK();
   if (multi_red) {  // per right-hand side sums of the per-warp partials
-    k_red_rows<<<(unsigned)A.nslices, 256, 0, st>>>(A.partial, (A.g.Vh + 31) / 32, A.gpartial);
+    launch_k(k_red_rows, (unsigned)A.nslices, 256, 0, st, A.partial, (A.g.Vh + 31) / 32, A.gpartial);
     QCD_LAUNCH_CK();
   }
 }
