@@ -303,6 +303,10 @@ qcd_status qcd_norm2(const qcd_gauge* g, const qcd_fermion* fermion, const void*
 /* Diagnostics and test hooks (environment variables, read by the library):
  *   QCD_TUNECACHE=<file>   the autotuner's persistent cache (see qcd_set_tuning);
  *   QCD_TUNE_VERBOSE=1     print every timed launch shape to stderr;
+ *   QCD_PDL=0              launch the kernels without programmatic dependent
+ *                          launch (by default each stencil / solver kernel may be
+ *                          scheduled while its predecessor drains; results are
+ *                          the same either way);
  *   QCD_FAULT=alloc        every device workspace allocation fails (QCD_ERR_OOM);
  *   QCD_FAULT=nan          qcd_solve poisons its inner residual with NaN after the
  *                          first restart, which the device reductions must report
