@@ -239,8 +239,9 @@ def main():
                     help="precision of the outer steps of the mixed solve: df64 = double-float stencil "
                          "(FP32 pairs), f64 = IEEE FP64 stencil; the final residual is FP64 either way")
     ap.add_argument("--delta", type=float, default=None,
-                    help="reliable-update factor of the mixed solves (default: 1e-4 for the FP32 Wilson solves "
-                         "of the bench line, the library's per-precision default elsewhere)")
+                    help="reliable-update factor of the mixed solves (default: 1e-5 for the FP32 Wilson solves "
+                         "of the bench line and the batched workload, the library's per-precision default "
+                         "for domain-wall)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -282,7 +283,7 @@ def main():
     out64 = torch.empty(nb64, dtype=torch.uint8, device=dev)
     qcd.field_pack(g, f, "f32", 1, b_dev, in32)
     qcd.field_pack(g, f, "f64", 1, b_dev, in64)
-    delta = 1e-4 if args.delta is None else args.delta
+    delta = 1e-5 if args.delta is None else args.delta
     solve_kw = dict(method=qcd.BICGSTAB, tol=TOL, inner="f32", use_graph=True, graph_chunk=32, delta=delta,
                     outer=args.outer)
 

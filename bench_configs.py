@@ -187,7 +187,7 @@ def run_batched(args):
                                             layout=qcd.INTERNAL))
     alg12 = Vh * (8 * 48 + 12 * 192)
     kw = dict(method=qcd.BICGSTAB, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32,
-              delta=(args.delta or 1e-4), outer=args.outer)
+              delta=(args.delta or 1e-5), outer=args.outer)
     x = torch.zeros_like(bd)
     qcd.solve(g, f, bd, x, nrhs=12, **kw)  # warm-up
     x.zero_()
