@@ -165,3 +165,48 @@ def test_solver_fault_injection_on_the_host(small, fault, status, inner):
     x.zero_()
     info, st = qcd.solve(g, f, b, x, tol=1e-10, inner=inner, use_graph=True)
     assert st == qcd.OK and info[0]["converged"]
+
+
+_PDL_CHILD = r"""
+import sys
+import numpy as np, torch
+from paper_1712_01505_gb300 import inputs, qcd
+L, BC = (8, 4, 4, 8), (1, 1, 1, -1)
+V = int(np.prod(L))
+U = torch.from_numpy(inputs.gauge_field(L, 0.3, 41)).cuda()
+b = torch.from_numpy(inputs.gaussian_source((V, 4, 3), 42)).cuda()
+g = qcd.Gauge.load(U, L, BC, recon=12)
+f = qcd.wilson(0.12)
+o = torch.empty_like(b)
+qcd.dslash(g, f, "MHAT", b, o, prec="f32")
+x = torch.zeros_like(b)
+qcd.solve(g, f, b, x, method=qcd.BICGSTAB, tol=1e-10, inner="f32", outer="df64", use_graph=True, graph_chunk=8)
+Ls = 8
+bd = torch.from_numpy(inputs.gaussian_source((Ls, V, 4, 3), 43)).cuda()
+fd = qcd.mobius(Ls, 1.8, 0.02, 1.5, 0.5)
+xd = torch.zeros_like(bd)
+qcd.solve(g, fd, bd, xd, method=qcd.CG_NORMAL, tol=1e-10, inner="f32", use_graph=True, graph_chunk=8)
+torch.cuda.synchronize()
+np.save(sys.argv[1], np.concatenate([o.cpu().numpy().ravel(), x.cpu().numpy().ravel(), xd.cpu().numpy().ravel()]))
+"""
+
+
+def test_programmatic_launch_does_not_change_results(tmp_path):
+    """QCD_PDL=0 (plain stream order) and the default (programmatic dependent launch) give the
+    same bits for an operator, a Wilson BiCGStab and a Mobius CG solve (both runs share one
+    tuning cache, so they run the same launch shapes)."""
+    device()
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, QCD_TUNECACHE=str(tmp_path / "tune.txt"),
+               PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    outs = []
+    for pdl in ("0", "1"):
+        out = tmp_path / f"pdl{pdl}.npy"
+        r = subprocess.run([sys.executable, "-c", _PDL_CHILD, str(out)], cwd=root, env=dict(env, QCD_PDL=pdl),
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append(np.load(out))
+    assert np.array_equal(outs[0], outs[1])
