@@ -417,3 +417,29 @@ def test_oracle_results_do_not_depend_on_the_thread_count():
     finally:
         ora.set_num_threads(n)
     assert np.array_equal(a, b)
+
+
+def test_action_gauge_invariance_and_force_covariance():
+    """S[U', Omega phi] = S[U, phi] with U'_mu(x) = Omega(x) U_mu(x) Omega(x+mu)^dag, and the link
+    gradient G = dS/dRe U + i dS/dIm U transforms as G'_mu(x) = Omega(x) G_mu(x) Omega(x+mu)^dag
+    (S is invariant, so dS = Re tr(G^dag dU) must be too)."""
+    L, k = (4, 2, 2, 4), 0.12
+    V = ora.volume(L)
+    U = inputs.gauge_field(L, 0.4, 121)
+    Om = inputs.random_gauge_transform(V, 122)
+    phi = inputs.gaussian_source((V, 4, 3), 123)
+
+    def transform(M):  # Omega(x) M_mu(x) Omega(x+mu)^dag for a (4, V, 3, 3) array
+        out = np.empty_like(M)
+        for mu in range(4):
+            out[mu] = Om @ M[mu] @ np.conj(np.swapaxes(shift_fwd(Om, L, mu), -1, -2))
+        return out
+
+    S0, eta, X = ora.wilson_action(L, BC_T, k, U, phi, tol=1e-14)
+    S1, eta1, X1 = ora.wilson_action(L, BC_T, k, transform(U), np.einsum("xab,xsb->xsa", Om, phi), tol=1e-14)
+    assert abs(S1 - S0) <= 1e-11 * S0
+    g0 = ora.wilson_force(L, BC_T, k, X, eta)
+    g1 = ora.wilson_force(L, BC_T, k, X1, eta1)
+    G0 = g0[..., 0] + 1j * g0[..., 1]
+    G1 = g1[..., 0] + 1j * g1[..., 1]
+    assert np.abs(G1 - transform(G0)).max() <= 1e-10 * np.abs(G0).max()
