@@ -168,11 +168,10 @@ void run_col(const DwParams& p, const ColSpec& spec, const Field& in, Field& out
   const size_t smem = (size_t)p.Ls * 24 * SB * rb;
   dim3 blk(SB, 256 / SB);
   dim3 grid((unsigned)((in.Vh + SB - 1) / SB), in.nrhs);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_mask{0};
+  if (first_use_on_device(attr_mask)) {
     QCD_CK(cudaFuncSetAttribute(k_col<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
     QCD_CK(cudaFuncSetAttribute(k_col<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-    attr_set = true;
   }
   if (dbl)
     launch_k(k_col<double>, grid, blk, smem, st, make_coef<double>(p, spec), any_view(in), any_view(out), in.Vh, dagger,

@@ -190,10 +190,9 @@ void dw_ainv_df(const DwParams& p, const Field& in, Field& out, int dagger, doub
   const size_t smem = (size_t)Ls * 24 * SB * sizeof(F2);
   dim3 blk(SB, 256 / SB);
   dim3 grid((unsigned)((in.Vh + SB - 1) / SB), in.nrhs);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_mask{0};
+  if (first_use_on_device(attr_mask)) {
     QCD_CK(cudaFuncSetAttribute(k_ainv_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-    attr_set = true;
   }
   k_ainv_df<<<grid, blk, smem, st>>>(c, dview(in), dview(out), in.Vh, dagger, split_host(scale),
                                      x ? dview(*x) : dview(out), x != nullptr, stop);

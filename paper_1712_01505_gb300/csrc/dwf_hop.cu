@@ -155,11 +155,10 @@ struct FusedLaunch {
 
 template <int P, int RECON, int BY, int PK>
 void launch_fused(FusedLaunch<P, RECON>* L) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_mask{0};
+  if (first_use_on_device(attr_mask)) {
     QCD_CK(cudaFuncSetAttribute(k_dw_hop_w<P, RECON, BY, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kFusedMaxLs * 24 * 32 * (int)sizeof(float)));
-    attr_set = true;
   }
   launch_k(k_dw_hop_w<P, RECON, BY, PK>, dim3(L->nsb, (unsigned)L->nrhs), dim3(32, BY), L->smem, L->st, L->args,
                                                                                                   L->coef);

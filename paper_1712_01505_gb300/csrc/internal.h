@@ -1,5 +1,6 @@
 // Host-side internals of libqcd shared between translation units.
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -34,6 +35,16 @@ void set_launches(long n);
     ::qcd::note_launches(1);      \
     ::qcd::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__); \
   } while (0)
+
+// True the first time a call site asks on the current device (mask: that call
+// site's static bitmask of devices): per-device one-time setup such as raising
+// a kernel's dynamic shared-memory limit.
+inline bool first_use_on_device(std::atomic<unsigned long long>& mask) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  return (mask.fetch_or(bit) & bit) == 0;
+}
 
 // Launch a kernel with the programmatic-serialization attribute (unless QCD_PDL=0):
 // every kernel launched this way starts with pdl_enter() (common.cuh).
