@@ -254,3 +254,26 @@ def test_full_size_fused_mhat_on_sampled_sites(mobius, prec):
         ref = _mhat_sampled(L, Ls, b5, c5, U, psi, xs, dag)
         assert rel_err(out[:, idx].cpu().numpy(), ref) < TOL[prec], (dag, prec)
     g.free()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64"])
+def test_mhat_at_the_largest_ls(prec):
+    """Ls = 64, the library's limit: the column kernels stage 8 sites per block (the staging
+    tile of 64 slices x 24 reals fills the shared memory), in every precision of the operator."""
+    device()
+    L, Ls = (2, 2, 2, 4), 64
+    V, U, psi = _case(L, Ls, 97)
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    par = ora.parity(L)
+    pe = psi.copy()
+    pe[:, par == 1] = 0
+    out = torch.empty((Ls, V, 4, 3), dtype=torch.complex128, device=device())
+    for b5, c5 in ((1.0, 0.0), (B5, C5)):
+        f = qcd.mobius(Ls, M5, MF, b5, c5)
+        for dag in (False, True):
+            qcd.dslash(g, f, "MHAT_DAG" if dag else "MHAT", to_dev(psi), out, prec=prec)
+            torch.cuda.synchronize()
+            _check(out, ora.mobius_mhat(L, BC, Ls, M5, MF, b5, c5, U, pe, dagger=dag), prec)
+    with pytest.raises(qcd.QCDError, match="ERR_ARG"):
+        qcd.dslash(g, qcd.mobius(65, M5, MF, B5, C5), "MHAT", to_dev(inputs.gaussian_source((65, V, 4, 3), 98)),
+                   torch.empty((65, V, 4, 3), dtype=torch.complex128, device=device()), prec="f32")
