@@ -227,7 +227,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-solve", action="store_true")
-    ap.add_argument("--profile", default="none", choices=["none", "dslash", "step", "mhat"],
+    ap.add_argument("--profile", default="none", choices=["none", "dslash", "step", "mhat", "cg"],
                     help="for ncu: 'dslash' runs only the standalone FP32 D_eo launches, 'step' one step "
                          "between cudaProfilerStart/Stop (use ncu --profile-from-start off); no JSON line")
     ap.add_argument("--profile-prec", default="f32", choices=["f32", "f64", "df64"],

@@ -63,6 +63,18 @@ def run_dwf(args):
         a_ = torch.empty(nb, dtype=torch.uint8, device=dev)
         o_ = torch.empty(nb, dtype=torch.uint8, device=dev)
         qcd.field_pack(g, f, prec, 1, bd, a_)
+        if args.profile == "cg":  # ncu: one warmed-up CG solve (FP32 inner, double-float outer steps)
+            kw = dict(method=qcd.CG_NORMAL, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32, outer="df64")
+            x = torch.zeros_like(bd)
+            qcd.solve(g, f, bd, x, **kw)
+            x.zero_()
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            info, _ = qcd.solve(g, f, bd, x, **kw)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+            print(f"profile dwf cg done: {info[0]}", flush=True)
+            return
         if args.profile != "none":  # ncu: tune, then profile 3 launches of the FP32 hop (or of Mhat)
             op = "MHAT" if args.profile == "mhat" else "D_EO"
             if op == "MHAT":
