@@ -373,3 +373,44 @@ def mobius_block(Ls, M5, mf, b5, c5, which, psi, dagger=False):
     M = {"A": A, "B": B, "Binv": _block_inv(B) if which == "Binv" else None,
          "W": np.einsum("satb,tbuc->sauc", B, _block_inv(A)) if which == "W" else None}[which]
     return _block_apply(M, psi, dagger)
+
+
+def mobius_solve(L, bc, Ls, M5, mf, b5, c5, U, b, tol=1e-12, maxiter=20000):
+    """Solve D_M x = b (Mobius, or Eq. (2) at b5 = 1, c5 = 0) through the even-odd system of
+    D B^-1 in x' = B x: bhat = W (b_e + 1/2 H_eo W b_o), CG (Hestenes-Stiefel) on
+    Mhat^dag Mhat x'_e = Mhat^dag bhat, x'_o = W (b_o + 1/2 H_oe x'_e), x = B^-1 x'.
+    Returns (x, CG iterations, |b - D x| / |b|)."""
+    par = parity(L)
+    b = _c(b)
+    be, bo = b.copy(), b.copy()
+    be[:, par == 1] = 0
+    bo[:, par == 0] = 0
+    W = lambda v, dag=False: mobius_block(Ls, M5, mf, b5, c5, "W", v, dag)
+    t = W(bo)
+    t[:, par == 0] = 0
+    bhat = W(be + 0.5 * _hop5(L, bc, U, t, out_parity=0))
+    bhat[:, par == 1] = 0
+    mh = lambda v, dag=False: mobius_mhat(L, bc, Ls, M5, mf, b5, c5, U, v, dagger=dag)
+    rhs = mh(bhat, True)
+    x = np.zeros_like(b)
+    r = rhs.copy()
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    stop = (tol * np.linalg.norm(rhs)) ** 2
+    it = 0
+    while rr > stop and it < maxiter:
+        q = mh(mh(p), True)
+        alpha = rr / np.vdot(p, q).real
+        x += alpha * p
+        r -= alpha * q
+        rr_new = np.vdot(r, r).real
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    t = x.copy()
+    xo = W(bo + 0.5 * _hop5(L, bc, U, t, out_parity=1))
+    xo[:, par == 0] = 0
+    xp = x + xo
+    xs = mobius_block(Ls, M5, mf, b5, c5, "Binv", xp)
+    res = np.linalg.norm(b - mobius(L, bc, Ls, M5, mf, b5, c5, U, xs)) / np.linalg.norm(b)
+    return xs, it, res

@@ -10,6 +10,7 @@ from tests.test_oracle_pins import match_spectra, momenta
 
 BC = (1, 1, 1, -1)
 M5, MF = 1.8, 0.02
+B5_PIN, C5_PIN = 1.5, 0.5
 
 
 def _dense(op, n):
@@ -178,3 +179,20 @@ def test_dense_solve():
     b = inputs.gaussian_source(shape, 7).reshape(n)
     x = np.linalg.solve(D, b)
     assert np.linalg.norm(ora.mobius(L, BC, Ls, M5, MF, b5, c5, U, x.reshape(shape)).reshape(n) - b) < 1e-11
+
+
+def test_even_odd_solve_equals_the_dense_solution():
+    """The oracle's even-odd CG solve (x' = B x, Schur system of D B^-1, reconstruction, B^-1)
+    reproduces numpy.linalg.solve on the dense D, Mobius and Shamir."""
+    L, Ls = (2, 2, 2, 4), 4
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.3, 10)
+    shape = (Ls, V, 4, 3)
+    n = Ls * V * 12
+    b = inputs.gaussian_source(shape, 11)
+    for b5, c5 in ((B5_PIN, C5_PIN), (1.0, 0.0)):
+        D = _dense(lambda e: ora.mobius(L, BC, Ls, M5, MF, b5, c5, U, e.reshape(shape)).reshape(n), n)
+        xd = np.linalg.solve(D, b.reshape(n)).reshape(shape)
+        x, it, res = ora.mobius_solve(L, BC, Ls, M5, MF, b5, c5, U, b, tol=1e-13)
+        assert res <= 1e-12 and it > 0
+        assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
