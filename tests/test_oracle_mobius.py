@@ -77,7 +77,7 @@ def test_free_spectrum_momentum_space():
     ev = np.linalg.eigvals(D)
     g = [ora.gamma(k) for k in range(5)]
     Pp, Pm = 0.5 * (np.eye(4) + g[4]), 0.5 * (np.eye(4) - g[4])
-    S = np.zeros((4 * Ls, 4 * Ls))
+    S = np.zeros((4 * Ls, 4 * Ls), dtype=complex)
     for s in range(Ls):
         if s + 1 < Ls:
             S[4 * s:4 * s + 4, 4 * (s + 1):4 * (s + 2)] = Pm
