@@ -10,7 +10,8 @@ One step = one pass of the hot path on that input:
   1. the standalone even-odd hopping stencil D_eo in FP32 (NDSLASH launches)
      and in FP64 (one launch), on internal-layout device buffers;
   2. the mixed-precision even-odd BiCGStab solve (FP32 inner iterations,
-     FP64 reliable updates) to |b - M x| / |b| <= 1e-10 on the full system,
+     IEEE-FP64 reliable updates: true residual, solution accumulation and
+     reductions in FP64) to |b - M x| / |b| <= 1e-10 on the full system,
      from canonical device buffers (source preparation, solve, reconstruction
      and the final FP64 true residual included).
 `value` is the whole-step dslash rate: 1320 flop per output site for every
@@ -230,14 +231,16 @@ def main():
     ap.add_argument("--profile", default="none", choices=["none", "dslash", "step", "mhat", "cg"],
                     help="for ncu: 'dslash' runs only the standalone FP32 D_eo launches, 'step' one step "
                          "between cudaProfilerStart/Stop (use ncu --profile-from-start off); no JSON line")
-    ap.add_argument("--profile-prec", default="f32", choices=["f32", "f64", "df64"],
-                    help="precision of the D_eo launches of --profile dslash")
+    ap.add_argument("--profile-prec", default="f32", choices=["f32", "f64", "df64", "f16"],
+                    help="precision of the D_eo launches of --profile dslash (and of the domain-wall hop / "
+                         "Mhat of --workload dwf --profile dslash / mhat)")
     ap.add_argument("--workload", default="wilson32", choices=["wilson32", "dwf", "batched", "force"],
                     help="wilson32 (default, the bench line); the others characterise the other "
                          "configurations (domain-wall CG, 12-rhs propagator, force) and print their own line")
-    ap.add_argument("--outer", default="df64", choices=["f64", "df64"],
-                    help="precision of the outer steps of the mixed solve: df64 = double-float stencil "
-                         "(FP32 pairs), f64 = IEEE FP64 stencil; the final residual is FP64 either way")
+    ap.add_argument("--outer", default="f64", choices=["f64", "df64"],
+                    help="precision of the outer steps of the mixed solve: f64 = IEEE FP64 stencil (the "
+                         "default), df64 = double-float stencil (FP32 pairs); the final residual is IEEE FP64 "
+                         "either way")
     ap.add_argument("--delta", type=float, default=None,
                     help="reliable-update factor of the mixed solves (default: 1e-5 for the FP32 Wilson solves "
                          "of the bench line and the batched workload, the library's per-precision default "
@@ -360,12 +363,12 @@ def main():
         if not inf["converged"] or inf["true_resid"] > TOL:
             raise SystemExit(f"solve failed to converge: {inf}")
 
-    def hops_in_solve(inf):
-        # 4 inner half-dslashes per BiCGStab iteration; outer precision (FP64 or double-float):
-        # 1 (source), 2 per outer step (the true residual; none before the first since x0 = 0),
-        # 1 (reconstruction); FP64: 1 (even part of the final full-system residual; the odd
-        # part reuses the reconstruction's H_oe x_e)
-        return 4 * inf["iters"] + 1 + 2 * inf["outer_updates"] + 1 + 1
+    def hops_in_solve(inf, outer=args.outer):
+        # 4 inner half-dslashes per BiCGStab iteration, 1 for the source and 2 per outer step
+        # (none before the first since x0 = 0).  IEEE-FP64 outer steps reconstruct x_o and form
+        # the full-system residual themselves, so the last one ends the solve; double-float
+        # outer steps add the reconstruction and the even half of the final FP64 residual.
+        return 4 * inf["iters"] + 1 + 2 * inf["outer_updates"] + (2 if outer == "df64" else 0)
 
     hops = sum(NDSLASH + 1 + hops_in_solve(inf) for inf in infos)
     # whole job: the slowest rank's time, every rank's work
@@ -479,8 +482,8 @@ def main():
         "data": "synthetic: smoothed-random SU(3) links and Z2 noise source (seeded)",
         "config": {"workload": WORKLOAD, "lattice": list(L), "kappa": KAPPA, "eps": EPS, "recon": RECON,
                    "solver": "EO BiCGStab, FP32 inner + reliable updates in "
-                             + ("double-float (FP32 pairs)" if args.outer == "df64" else "FP64")
-                             + ", FP64 final residual, CUDA graph chunks of 32",
+                             + ("double-float (FP32 pairs)" if args.outer == "df64" else "IEEE FP64")
+                             + " (FP64 solution and reductions), FP64 final residual, CUDA graph chunks of 32",
                    "outer": args.outer,
                    "tol": TOL, "ndslash_per_step": NDSLASH, "delta": delta,
                    "l2": "inputs larger than L2 (links 403 MB, each parity vector 101 MB)",

@@ -59,6 +59,8 @@ def run_dwf(args):
     bd = torch.from_numpy(b).to(dev)
     hop = {}
     for prec, site_b, link_b in (("f32", 96, 48), ("f16", 52, 24)):
+        if args.profile in ("dslash", "mhat") and prec != args.profile_prec:
+            continue
         nb = qcd.field_bytes(g, f, prec)
         a_ = torch.empty(nb, dtype=torch.uint8, device=dev)
         o_ = torch.empty(nb, dtype=torch.uint8, device=dev)

@@ -175,6 +175,12 @@ void check_prec(int prec) {
     raise(QCD_ERR_ARG, "unknown precision %d", prec);
 }
 
+// [a, a + n) and [b, b + n) must not share a byte
+void check_disjoint(const void* a, const void* b, size_t n) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  if (x < y + n && y < x + n) raise(QCD_ERR_ARG, "in and out must not overlap (%zu-byte fields)", n);
+}
+
 void check_gauge(const qcd_gauge* g) {
   if (!g) raise(QCD_ERR_ARG, "gauge handle is NULL");
   int dev = 0;
@@ -394,12 +400,14 @@ qcd_status qcd_dslash(const qcd_gauge* gc, const qcd_fermion* fermion, qcd_prec 
       if (!is_device_ptr(in) || !is_device_ptr(out)) raise(QCD_ERR_ARG, "internal buffers must be device memory");
       Field fi = internal_field(g, prec, ls, nrhs, in);
       Field fo = internal_field(g, prec, ls, nrhs, out);
+      check_disjoint(in, out, fi.data_bytes() + fi.norm_bytes());
       if (op == QCD_OP_D_EO) hop(g, fi, fo, 0, 0, 1.0, nullptr, st);
       else if (op == QCD_OP_D_OE) hop(g, fi, fo, 1, 0, 1.0, nullptr, st);
       else apply_mhat(c, fi, fo, op == QCD_OP_MHAT_DAG, st, "dslash");
       return;
     }
     size_t cb = (size_t)nrhs * ls * g->lat.V * 12 * 16;
+    check_disjoint(in, out, cb);
     Staged si = stage_in(g, "io.in", in, cb, st, true);
     Staged so = stage_in(g, "io.out", out, cb, st, false);
     Field a = ws_field(g, "d.a", prec, ls, nrhs);
@@ -508,6 +516,8 @@ qcd_status qcd_mhat_noalloc(const qcd_gauge* gc, const qcd_fermion* fermion, qcd
     if (in == out) raise(QCD_ERR_ARG, "in and out must not overlap");
     if (nrhs < 1 || nrhs > 64) raise(QCD_ERR_ARG, "nrhs = %d must be in [1, 64]", nrhs);
     if (!is_device_ptr(in) || !is_device_ptr(out)) raise(QCD_ERR_ARG, "in and out must be device memory");
+    const Field fi = internal_field(gc, prec, 1, nrhs, in);
+    check_disjoint(in, out, fi.data_bytes() + fi.norm_bytes());
     mhat_noalloc(gc, *fermion, prec, dagger, in, out, nrhs, (cudaStream_t)stream);
   });
 }
@@ -583,3 +593,4 @@ qcd_status qcd_mom_energy(const void* P, int64_t nlinks, double* out, void* stre
 }
 
 }  // extern "C"
+

@@ -525,7 +525,7 @@ struct Solver {
   int* counters = nullptr;     // their group counters (zero between launches)
   unsigned nblk = 1;
   // fields
-  Field b_e, b_o, bh, x64, r64, t64, u64;   // FP64
+  Field b_e, b_o, bh, x64, r64, t64, u64, xo64, re64;  // FP64
   Field r, rt, p, v, s, t, q, w, xin;        // inner
   std::vector<Scal> hsc;
 
@@ -734,6 +734,13 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   S.r64 = ws_field(g, "s.r64", QCD_F64, ls, nrhs);
   S.t64 = ws_field(g, "s.t64", QCD_F64, ls, nrhs);
   S.u64 = ws_field(g, "s.u64", QCD_F64, ls, nrhs);
+  // IEEE-FP64 outer steps of the Wilson solve keep the reconstructed odd half of x
+  const bool wil64 = !dwf && !(prm.outer == QCD_DF64 && S.inner != QCD_F64);
+  if (wil64) S.xo64 = ws_field(g, "s.xo64", QCD_F64, ls, nrhs);
+  // ... and the even half r_e of the full-system residual: the inner residual itself for
+  // BiCGStab, the source of Mhat^dag r_e for CG on the normal equations
+  if (wil64 && !S.bicg()) S.re64 = ws_field(g, "s.re64", QCD_F64, ls, nrhs);
+  Field& r_e64 = S.bicg() ? S.r64 : S.re64;
   S.r = ws_field(g, "s.r", S.inner, ls, nrhs);
   S.p = ws_field(g, "s.p", S.inner, ls, nrhs);
   if (S.bicg()) {
@@ -855,6 +862,31 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
       blas_norm2(r_outer, rn.data(), st, g);
       return;
     }
+    if (wil64) {
+      // Wilson with IEEE-FP64 outer steps: reconstruct x_o = b_o + kappa h, h = H_oe x_e,
+      // and form the even half of the full-system residual,
+      //   r_e = b_e - x_e + kappa H_eo x_o  (= bhat - Mhat x_e; the odd half is zero up to
+      // the rounding of x_o), so that the outer step that reaches the target has already
+      // computed the final solution and its true residual.
+      if (x_is_zero) {
+        blas_copy(S.bh, r_e64, st);  // x = (0, b_o): r_e = bhat, h = 0
+        blas_copy(S.b_o, S.xo64, st);
+        blas_zero(S.u64, st);
+      } else {
+        hop(g, S.x64, S.u64, 1, dag, 1.0, nullptr, st);  // h
+        blas_copy(S.b_o, S.xo64, st);
+        blas_axpby(f.kappa, S.u64, 1.0, S.xo64, st);  // x_o
+        blas_copy(S.b_e, S.t64, st);
+        blas_axpby(-1.0, S.x64, 1.0, S.t64, st);  // b_e - x_e
+        hop(g, S.xo64, r_e64, 0, dag, f.kappa, &S.t64, st);  // r_e
+      }
+      blas_norm2(r_e64, rfull.data(), st, g);
+      for (int r = 0; r < nrhs; ++r) rfull[r] = std::sqrt(rfull[r]);
+      // the inner residual: r_e (BiCGStab) or Mhat^dag r_e (CG)
+      if (!S.bicg()) apply_mhat(S.op64, r_e64, S.r64, 1, st, "o64");
+      blas_norm2(S.r64, rn.data(), st, g);
+      return;
+    }
     if (x_is_zero) {
       blas_copy(S.bh, S.t64, st);  // rhat = bhat
     } else {
@@ -965,6 +997,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   // a chunk stops short of the expected next outer step and the last few
   // iterations run in chunks of 8 / 2: few launches are wasted after a stop.
   int last_stop = 0, gap = 0;
+  bool resid_stale = false;  // x64 changed since the last true_residual (plain FP64 solves)
   while (nactive > 0) {
     int maxit = 0;
     for (int r = 0; r < nrhs; ++r)
@@ -987,6 +1020,8 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     } else {
       S.run_chunk(k, graph && !capped);
     }
+    // a plain FP64 solve iterates on x64 itself: the outer step's x_o and residual are stale
+    if (S.inner == QCD_F64) resid_stale = true;
     S.download();
     bool any = false;
     for (int r = 0; r < nrhs; ++r)
@@ -1013,6 +1048,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     }
     if (S.inner != QCD_F64) blas_axpby(1.0, S.xin, 1.0, dfo ? x_d : S.x64, st);
     true_residual(false);
+    resid_stale = false;
     nactive = 0;
     for (int r = 0; r < nrhs; ++r) {
       if (conv[r]) continue;
@@ -1029,7 +1065,19 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   // ---- reconstruct the odd sites and write the solution
   std::vector<double> re_(nrhs), ro_(nrhs);
   Field xe = S.x64, xo = S.t64;
-  if (!dwf) {
+  if (wil64) {
+    // x_e = x64 and x_o, h and r_e of the last outer step (recomputed if a plain FP64
+    // solve stopped at maxiter after iterating past it)
+    if (resid_stale) true_residual(false);
+    unpack_field(lat, 0, S.x64, x, st);
+    unpack_field(lat, 1, S.xo64, x, st);
+    blas_norm2(r_e64, re_.data(), st, g);
+    // odd half of the full residual: b_o - x_o + kappa h (rounding of the reconstruction)
+    blas_copy(S.b_o, S.bh, st);
+    blas_axpby(-1.0, S.xo64, 1.0, S.bh, st);
+    blas_axpby(f.kappa, S.u64, 1.0, S.bh, st);
+    blas_norm2(S.bh, ro_.data(), st, g);
+  } else if (!dwf) {
     // h = H_oe x_e (kept), x_o = b_o + kappa h
     if (dfo) {
       hop_df(g, x_d, u_d, 1, dag, 1.0, nullptr, nullptr, 0.0, st);

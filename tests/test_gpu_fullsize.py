@@ -1,0 +1,97 @@
+"""The full-size solves, judged by the oracle.
+
+Each test runs a solve the benchmark times, on the benchmark's lattice, links, source and solver
+settings, and evaluates |b - A x| / |b| with the FP64 CPU oracle's unpreconditioned operator
+(Eq. (1) for Wilson, Eq. (2) for domain-wall).  The solve must reach 1e-10 on the full system
+(Sec. II C: the solver's job is x = D^-1 b), whatever the inner and outer precisions, and the
+true residual the library reports must describe the x it returned.
+
+Workloads: Wilson 32^3 x 64 (kappa = 0.125, eps = 0.2 links of seed 2, complex Z2 source),
+domain-wall 16^3 x 32 x Ls 16 (M5 = 1.8, mf = 0.02, eps = 0.2 links of seed 3, Gaussian
+source), and the 12 point sources of Wilson 24^3 x 48 (kappa = 0.124, eps = 0.2, seed 4).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as ora
+from paper_1712_01505_gb300 import inputs, qcd
+from tests.gpu_util import device, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+BC = (1, 1, 1, -1)
+TOL = 1e-10
+
+
+def _residual(b, Ax):
+    return float(np.linalg.norm((b - Ax).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def _check(info, res):
+    assert res <= TOL, (res, info)
+    assert info["converged"] and info["true_resid"] <= TOL
+    # the reported residual is the one of the returned x (both FP64; the sums differ in order)
+    assert abs(info["true_resid"] - res) <= 1e-3 * res, (info["true_resid"], res)
+
+
+@pytest.fixture(scope="module")
+def wilson32():
+    device()
+    L, kappa = (32, 32, 32, 64), 0.125
+    U = inputs.gauge_field(L, 0.2, 2)
+    b = inputs.z2_source((int(np.prod(L)), 4, 3), 0)
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=12)
+    yield L, kappa, U, b, g
+    g.free()
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("inner,outer,delta", [("f32", "f64", 1e-5), ("f32", "df64", 1e-5), ("f16", "f64", 0.0),
+                                               ("f64", "f64", 0.0)])
+def test_wilson_32x32x32x64_bicgstab_judged_by_the_oracle(wilson32, inner, outer, delta):
+    L, kappa, U, b, g = wilson32
+    f = qcd.wilson(kappa)
+    bd = to_dev(b)
+    x = torch.zeros_like(bd)
+    info, _ = qcd.solve(g, f, bd, x, method=qcd.BICGSTAB, tol=TOL, inner=inner, outer=outer, delta=delta,
+                        use_graph=True, graph_chunk=32)
+    xh = x.cpu().numpy()
+    del x, bd
+    _check(info[0], _residual(b, ora.wilson(L, BC, kappa, U, xh)))
+
+
+@pytest.mark.parametrize("inner,outer", [("f16", "f64"), ("f32", "f64"), ("f32", "df64")])
+def test_domain_wall_16x16x16x32_ls16_cg_judged_by_the_oracle(inner, outer):
+    device()
+    L, Ls, M5, mf = (16, 16, 16, 32), 16, 1.8, 0.02
+    U = inputs.gauge_field(L, 0.2, 3)
+    b = inputs.gaussian_source((Ls, int(np.prod(L)), 4, 3), 0)
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=12)
+    bd = to_dev(b)
+    x = torch.zeros_like(bd)
+    info, _ = qcd.solve(g, qcd.dwf(Ls, M5, mf), bd, x, method=qcd.CG_NORMAL, tol=TOL, inner=inner, outer=outer,
+                        use_graph=True, graph_chunk=32)
+    xh = x.cpu().numpy()
+    g.free()
+    del x, bd
+    torch.cuda.empty_cache()
+    _check(info[0], _residual(b, ora.dw(L, BC, Ls, M5, mf, U, xh)))
+
+
+@pytest.mark.parametrize("outer", ["f64", "df64"])
+def test_twelve_point_sources_24x24x24x48_judged_by_the_oracle(outer):
+    device()
+    L, kappa = (24, 24, 24, 48), 0.124
+    U = inputs.gauge_field(L, 0.2, 4)
+    x0, b = inputs.point_sources(L, 0)
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=12)
+    bd = to_dev(b)
+    x = torch.zeros_like(bd)
+    info, _ = qcd.solve(g, qcd.wilson(kappa), bd, x, nrhs=12, method=qcd.BICGSTAB, tol=TOL, inner="f32",
+                        outer=outer, delta=1e-5, use_graph=True, graph_chunk=32)
+    xh = x.cpu().numpy()
+    g.free()
+    del x, bd
+    torch.cuda.empty_cache()
+    for k in range(12):
+        _check(info[k], _residual(b[k], ora.wilson(L, BC, kappa, U, xh[k])))

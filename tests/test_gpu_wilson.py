@@ -190,9 +190,12 @@ def test_gauge_covariance_on_gpu():
     assert max_err(out1, rot) < 1e-13
 
 
-def test_sampled_sites_at_32x32x32x64_fp32():
-    """Full-size config (32^3 x 64, eps = 0.2, kappa = 0.125): the FP32 INTERNAL-layout D_EO in the
-    benchmark's launch configuration, checked on sampled output sites the oracle computes one by one."""
+@pytest.mark.parametrize("prec,recons", [("f32", (18, 12)), ("f16", (12, 18)), ("f64", (18,))])
+def test_sampled_sites_at_32x32x32x64(prec, recons):
+    """Full-size config (32^3 x 64, eps = 0.2, kappa = 0.125): the INTERNAL-layout D_EO in the
+    benchmark's launch configuration, checked on sampled output sites the oracle computes one by one:
+    FP32 (the benchmark's stencil), FP16 (the inner stencil of the FP16 solves) and FP64 (the stencil
+    of the outer steps and of the final residual, which decides convergence)."""
     device()
     L = (32, 32, 32, 64)
     V = int(np.prod(L))
@@ -205,19 +208,22 @@ def test_sampled_sites_at_32x32x32x64_fp32():
     inp = psi.copy()
     inp[par == 0] = 0
     ref = ora.hop_sites(L, BC, U, inp, sites)
-    for recon in (18, 12):
+    for recon in recons:
         g = qcd.Gauge.load(to_dev(U), L, BC, recon=recon)
         f = qcd.wilson(0.125)
-        nb = qcd.field_bytes(g, f, "f32")
+        nb = qcd.field_bytes(g, f, prec)
         bi = torch.empty(nb, dtype=torch.uint8, device=device())
         bo = torch.empty(nb, dtype=torch.uint8, device=device())
-        qcd.field_pack(g, f, "f32", 1, to_dev(psi), bi)
-        qcd.dslash(g, f, "D_EO", bi, bo, prec="f32", layout=qcd.INTERNAL)
+        qcd.field_pack(g, f, prec, 1, to_dev(psi), bi)
+        qcd.dslash(g, f, "D_EO", bi, bo, prec=prec, layout=qcd.INTERNAL)
         out = torch.zeros((V, 4, 3), dtype=torch.complex128, device=device())
-        qcd.field_unpack(g, f, "f32", 0, bo, out)
+        qcd.field_unpack(g, f, prec, 0, bo, out)
         torch.cuda.synchronize()
         got = out[torch.from_numpy(sites).to(device())].cpu().numpy()
-        assert rel_err(got, ref) < 1e-6
+        if prec == "f64":
+            assert max_err(got, ref) < 1e-13
+        else:
+            assert rel_err(got, ref) < (1e-6 if prec == "f32" else 2e-3)
         g.free()
         del bi, bo, out
         torch.cuda.empty_cache()
