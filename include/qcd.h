@@ -350,6 +350,97 @@ qcd_status qcd_set_tuning(int32_t mode);
 qcd_status qcd_mhat_noalloc(const qcd_gauge* g, const qcd_fermion* fermion, qcd_prec prec,
                             int32_t dagger, const void* in, void* out, int32_t nrhs, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Domain decomposition (Sec. IV D; the multi-node runs of Sec. V B-C).
+ *
+ * The global lattice L[mu] is divided into P[mu] subdomains per direction, of
+ * local extent l[mu] = L[mu] / P[mu], which must be even and >= 2 (a site's
+ * parity is then the same in local and global coordinates).  Subdomain id =
+ * c_x + P_x (c_y + P_y (c_z + P_z c_t)) for grid coordinates c; it holds the
+ * global sites c[mu] l[mu] + x[mu], 0 <= x[mu] < l[mu], in the canonical order
+ * of the local lattice (x + l_x (y + l_y (z + l_z t))).
+ *
+ * A half-dslash of output parity p: every subdomain packs, for each cut
+ * direction mu (P[mu] > 1), its two faces of input-parity sites as spin-projected
+ * half spinors (6 complex numbers, 12 reals per face site; Sec. IV D) -- the low
+ * face x_mu = 0 as (1 + sg gamma_mu) psi for the forward hops of its -mu
+ * neighbour, the high face as U_mu^dag (1 - sg gamma_mu) psi for the backward
+ * hops of its +mu neighbour (sg = -1, or +1 for the adjoint); the faces travel
+ * while the interior hops are computed; the hops across the faces are then
+ * added to the boundary sites.  Boundary factors bc[mu] = -1 apply to the hops
+ * that cross the global boundary.  Subdomains held by this process exchange by
+ * device-to-device copies; subdomains of other processes by NCCL send / receive
+ * (qcd_dd_attach_nccl), with the solver's FP64 sums all-reduced by NCCL.
+ * -------------------------------------------------------------------------- */
+typedef struct {
+  int32_t L[4];   /* global extents                                              */
+  int32_t P[4];   /* subdomains per direction (>= 1)                             */
+  int32_t bc[4];  /* global boundary factors, +1 or -1                           */
+  int32_t recon;  /* 12 or 18 reals per stored FP32 link                         */
+} qcd_dd_geom;
+
+typedef struct qcd_dd qcd_dd;
+
+/* One face message of a subdomain, for the half-dslash of either parity.
+ * Sends: side 0 = the low face (x_mu = 0), to the -mu neighbour; side 1 = the
+ * high face, to the +mu neighbour.  Receives: side 0 = the halo of the forward
+ * hops, from the +mu neighbour's low face; side 1 = the halo of the backward
+ * hops, from the -mu neighbour's high face.  nsites = face sites of one parity
+ * (l_x l_y l_z l_t / l_mu / 2), each 6 complex numbers in the field's
+ * precision, stored component-major. */
+typedef struct {
+  int32_t mu;
+  int32_t side;
+  int32_t peer;   /* the other subdomain's id */
+  int32_t nsites;
+} qcd_dd_msg;
+
+/* The messages of subdomain `id` in the order the NCCL transport posts them
+ * (per cut direction in increasing mu: side 0, side 1).  Host only, no GPU
+ * needed.  sends / recvs (may be NULL) receive up to 8 entries each.  Returns
+ * the number of messages of each kind, or -1 on invalid arguments. */
+int32_t qcd_dd_plan(const qcd_dd_geom* geom, int32_t id, qcd_dd_msg* sends, qcd_dd_msg* recvs);
+
+/* Local canonical indices of the sites of one face message, in message order:
+ * the sites of `parity` on the face x_mu = 0 (side 0) or x_mu = l_mu - 1
+ * (side 1); `sites` holds nsites entries.  Host only. */
+qcd_status qcd_dd_face_sites(const qcd_dd_geom* geom, int32_t mu, int32_t side, int32_t parity,
+                             int64_t* sites);
+
+/* Create the subdomains ids[0 .. nlocal) held by this process.  U[k]: the
+ * canonical local gauge field (4, V_loc, 3, 3) complex128 of subdomain ids[k]
+ * (links U_mu(x) of its own sites), device or host.  Each subdomain keeps its
+ * own link copies (FP64, FP32) and workspace on the current device.
+ * QCD_ERR_ARG for extents that do not divide into even local extents >= 2,
+ * ids out of range or repeated. */
+qcd_status qcd_dd_create(const qcd_dd_geom* geom, int32_t nlocal, const int32_t* ids, const void* const* U,
+                         void* stream, qcd_dd** out);
+qcd_status qcd_dd_free(qcd_dd* dd);
+
+/* NCCL transport between processes (one subdomain per process, rank = its id,
+ * nranks = the number of subdomains).  qcd_dd_nccl_unique_id writes the 128-byte
+ * ncclUniqueId that rank 0 creates and the caller distributes; libnccl.so.2 is
+ * loaded at run time.  QCD_ERR_UNSUPPORTED if NCCL cannot be loaded. */
+qcd_status qcd_dd_nccl_unique_id(void* id);
+qcd_status qcd_dd_attach_nccl(qcd_dd* dd, const void* unique_id, int32_t nranks, int32_t rank);
+
+/* Operators on the local subdomains: in[k], out[k] are canonical local fields
+ * (V_loc, 4, 3) complex128 on the device for subdomain ids[k] (the order given
+ * to qcd_dd_create).  op: QCD_OP_D_EO, QCD_OP_D_OE, QCD_OP_MHAT, QCD_OP_MHAT_DAG
+ * (Wilson, as qcd_dslash); prec: QCD_F64 or QCD_F32.  Asynchronous on `stream`
+ * (the exchange runs on the handle's own stream, ordered by events). */
+qcd_status qcd_dd_dslash(qcd_dd* dd, const qcd_fermion* fermion, qcd_prec prec, int32_t op,
+                         const void* const* in, void* const* out, void* stream);
+
+/* Even-odd BiCGStab on the subdomains (Wilson, one right-hand side): inner
+ * QCD_F64, or QCD_F32 with FP64 reliable updates (params->delta; 0 selects
+ * 0.01); tol is the target |b - M x| / |b| on the full global system; dagger,
+ * x0_given, graphs and CG are not available.  b[k], x[k]: canonical local
+ * fields on the device.  info: one entry for the whole system.  Every process
+ * must call it together (the dot products are global). */
+qcd_status qcd_dd_solve(qcd_dd* dd, const qcd_fermion* fermion, const qcd_solver_params* params,
+                        const void* const* b, void* const* x, qcd_solve_info* info, void* stream);
+
 /* Instrumentation: the number of kernels this library has launched in this
  * process so far (a replayed CUDA graph counts each of its kernel nodes). */
 qcd_status qcd_kernel_launches(uint64_t* count);

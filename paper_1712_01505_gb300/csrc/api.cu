@@ -594,3 +594,66 @@ qcd_status qcd_mom_energy(const void* P, int64_t nlinks, double* out, void* stre
 
 }  // extern "C"
 
+// ----------------------------------------------------------------------------- domain decomposition
+extern "C" {
+
+int32_t qcd_dd_plan(const qcd_dd_geom* geom, int32_t id, qcd_dd_msg* sends, qcd_dd_msg* recvs) {
+  int32_t n = -1;
+  if (guarded([&] { n = dd_plan(geom, id, sends, recvs); }) != QCD_OK) return -1;
+  return n;
+}
+
+qcd_status qcd_dd_face_sites(const qcd_dd_geom* geom, int32_t mu, int32_t side, int32_t parity,
+                             int64_t* sites) {
+  return guarded([&] { dd_face_sites(geom, mu, side, parity, sites); });
+}
+
+qcd_status qcd_dd_create(const qcd_dd_geom* geom, int32_t nlocal, const int32_t* ids, const void* const* U,
+                         void* stream, qcd_dd** out) {
+  NvtxRange nvtx_range("qcd_dd_create");
+  if (out) *out = nullptr;
+  return guarded([&] {
+    if (!out) raise(QCD_ERR_ARG, "out is NULL");
+    dd_create(geom, nlocal, ids, U, (cudaStream_t)stream, out);
+  });
+}
+
+qcd_status qcd_dd_free(qcd_dd* dd) {
+  return guarded([&] { dd_free(dd); });
+}
+
+qcd_status qcd_dd_nccl_unique_id(void* id) {
+  return guarded([&] { dd_nccl_unique_id(id); });
+}
+
+qcd_status qcd_dd_attach_nccl(qcd_dd* dd, const void* unique_id, int32_t nranks, int32_t rank) {
+  return guarded([&] { dd_attach_nccl(dd, unique_id, nranks, rank); });
+}
+
+qcd_status qcd_dd_dslash(qcd_dd* dd, const qcd_fermion* fermion, qcd_prec prec, int32_t op,
+                         const void* const* in, void* const* out, void* stream) {
+  NvtxRange nvtx_range("qcd_dd_dslash");
+  return guarded([&] {
+    if (!dd || !in || !out) raise(QCD_ERR_ARG, "NULL argument");
+    check_fermion(fermion);
+    check_prec(prec);
+    dd_dslash(dd, *fermion, prec, op, in, out, (cudaStream_t)stream);
+  });
+}
+
+qcd_status qcd_dd_solve(qcd_dd* dd, const qcd_fermion* fermion, const qcd_solver_params* params,
+                        const void* const* b, void* const* x, qcd_solve_info* info, void* stream) {
+  NvtxRange nvtx_range("qcd_dd_solve");
+  qcd_status s = guarded([&] {
+    if (!dd || !params || !b || !x || !info) raise(QCD_ERR_ARG, "NULL argument");
+    check_fermion(fermion);
+    dd_solve(dd, *fermion, *params, b, x, info, (cudaStream_t)stream);
+  });
+  if (s == QCD_OK && info && !info->converged) {
+    t_err = "solve did not reach tol (see info)";
+    return (qcd_status)info->status;
+  }
+  return s;
+}
+
+}  // extern "C"

@@ -246,6 +246,20 @@ void apply_full_parity(const OpCtx& c, const Field& in_same, const Field& in_oth
                        int parity, int dagger, cudaStream_t st, const char* tag);
 AnyView any_view(const Field& f);
 
+// ----------------------------------------------------------------------------- domain decomposition (dd.cu)
+void dd_geom_check(const qcd_dd_geom* g);
+int dd_plan(const qcd_dd_geom* g, int id, qcd_dd_msg* sends, qcd_dd_msg* recvs);
+void dd_face_sites(const qcd_dd_geom* g, int mu, int side, int parity, int64_t* out);
+void dd_create(const qcd_dd_geom* geom, int nlocal, const int32_t* ids, const void* const* U, cudaStream_t st,
+               qcd_dd** out);
+void dd_free(qcd_dd* d);
+void dd_nccl_unique_id(void* id);
+void dd_attach_nccl(qcd_dd* d, const void* uid, int nranks, int rank);
+void dd_dslash(qcd_dd* d, const qcd_fermion& f, int prec, int op, const void* const* in, void* const* out,
+               cudaStream_t st);
+void dd_solve(qcd_dd* d, const qcd_fermion& f, const qcd_solver_params& prm, const void* const* b, void* const* x,
+              qcd_solve_info* info, cudaStream_t st);
+
 // ----------------------------------------------------------------------------- tuner (tune.cu)
 struct LaunchCfg {
   int block;  // threads per block

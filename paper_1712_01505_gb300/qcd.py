@@ -43,7 +43,8 @@ BICGSTAB, CG_NORMAL = 0, 1
 SYMBOLS = ["qcd_gauge_load", "qcd_gauge_free", "qcd_field_bytes", "qcd_field_pack", "qcd_field_unpack",
            "qcd_dslash", "qcd_solve", "qcd_force", "qcd_last_error", "qcd_set_tuning", "qcd_kernel_launches",
            "qcd_mhat_noalloc", "qcd_norm2", "qcd_force_eo", "qcd_force_project", "qcd_link_update",
-           "qcd_mom_update", "qcd_mom_energy"]
+           "qcd_mom_update", "qcd_mom_energy", "qcd_dd_plan", "qcd_dd_face_sites", "qcd_dd_create", "qcd_dd_free",
+           "qcd_dd_nccl_unique_id", "qcd_dd_attach_nccl", "qcd_dd_dslash", "qcd_dd_solve"]
 
 
 class QCDError(RuntimeError):
@@ -76,6 +77,16 @@ class SolveInfo(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DDGeom(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32 * 4), ("P", ctypes.c_int32 * 4), ("bc", ctypes.c_int32 * 4),
+                ("recon", ctypes.c_int32)]
+
+
+class DDMsg(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_int32), ("side", ctypes.c_int32), ("peer", ctypes.c_int32),
+                ("nsites", ctypes.c_int32)]
 
 
 _lib = None
@@ -114,10 +125,22 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qcd_link_update.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int64, vp]
     lib.qcd_mom_update.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int64, vp]
     lib.qcd_mom_energy.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp]
+    pp = ctypes.POINTER(vp)
+    lib.qcd_dd_plan.argtypes = [ctypes.POINTER(DDGeom), i32, ctypes.POINTER(DDMsg), ctypes.POINTER(DDMsg)]
+    lib.qcd_dd_plan.restype = i32
+    lib.qcd_dd_face_sites.argtypes = [ctypes.POINTER(DDGeom), i32, i32, i32, ctypes.POINTER(ctypes.c_int64)]
+    lib.qcd_dd_create.argtypes = [ctypes.POINTER(DDGeom), i32, ctypes.POINTER(i32), pp, vp, ctypes.POINTER(vp)]
+    lib.qcd_dd_free.argtypes = [vp]
+    lib.qcd_dd_nccl_unique_id.argtypes = [vp]
+    lib.qcd_dd_attach_nccl.argtypes = [vp, vp, i32, i32]
+    lib.qcd_dd_dslash.argtypes = [vp, ctypes.POINTER(Fermion), i32, i32, pp, pp, vp]
+    lib.qcd_dd_solve.argtypes = [vp, ctypes.POINTER(Fermion), ctypes.POINTER(SolverParams), pp, pp,
+                                 ctypes.POINTER(SolveInfo), vp]
     for name in ("qcd_gauge_load", "qcd_gauge_free", "qcd_field_pack", "qcd_field_unpack", "qcd_dslash",
                  "qcd_solve", "qcd_force", "qcd_set_tuning", "qcd_kernel_launches", "qcd_mhat_noalloc",
                  "qcd_norm2", "qcd_force_eo", "qcd_force_project", "qcd_link_update", "qcd_mom_update",
-                 "qcd_mom_energy"):
+                 "qcd_mom_energy", "qcd_dd_face_sites", "qcd_dd_create", "qcd_dd_free", "qcd_dd_nccl_unique_id",
+                 "qcd_dd_attach_nccl", "qcd_dd_dslash", "qcd_dd_solve"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

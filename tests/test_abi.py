@@ -23,7 +23,7 @@ def lib():
 
 def header_functions():
     src = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:qcd_status|size_t|const char\*)\s+(qcd_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:qcd_status|size_t|int32_t|const char\*)\s+(qcd_\w+)\s*\(", src, re.M)))
 
 
 def test_header_declares_the_binding_symbols():
