@@ -263,6 +263,11 @@ struct SpinorView<P32> {
 #pragma unroll
     for (int q = 0; q < 6; ++q) p[q * stride + site] = make_float4(w[q].re.x, w[q].re.y, w[q].im.x, w[q].im.y);
   }
+  // the pairs without their site scale (FP32 has none: *scale = 1)
+  __device__ __forceinline__ void load_p_raw(long site, P2 w[6], float* scale) const {
+    load_p(site, w);
+    *scale = 1.f;
+  }
   __device__ __forceinline__ SpinorView offset_rhs(int r) const {
     SpinorView o = *this;
     o.p += (long)r * 6 * stride;
@@ -323,6 +328,17 @@ struct SpinorView<P16> {
 #pragma unroll
       for (int j = 0; j < 2; ++j)
         w[2 * k + j] = {__fmul2_rn(__half22float2(h[2 * j]), s2), __fmul2_rn(__half22float2(h[2 * j + 1]), s2)};
+    }
+  }
+  // the stored pairs psi/s and the site scale s (the caller applies s where it is cheapest)
+  __device__ __forceinline__ void load_p_raw(long site, P2 w[6], float* scale) const {
+    *scale = __ldg(norm + site);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 d = __ldg(p + k * stride + site);
+      const __half2* h = reinterpret_cast<const __half2*>(&d);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) w[2 * k + j] = {__half22float2(h[2 * j]), __half22float2(h[2 * j + 1])};
     }
   }
   __device__ __forceinline__ void store_p(long site, const P2 w[6]) const {

@@ -288,25 +288,14 @@ __device__ __forceinline__ void link_elems(const SmLinks12& sm, int L, int tx, f
   for (int k = 0; k < 9; ++k) e[k] = make_float4(u[k].re, u[k].re, u[k].im, u[k].im);
 }
 
-// acc += the hop from direction L (mu = L / 2, backward if L odd) for one slice,
-// packed: g = U h (U^dag h backward) with both spins of h in the lanes
-template <int P, int RECON, int L, typename SM>
-__device__ __forceinline__ void hop_link_smp(const HopArgs<P, RECON>& A, const SM& sm, int tx, float sg,
-                                             const SpinorView<P>& in, long soff, P2 acc[6]) {
-  constexpr int MU = L >> 1;
-  constexpr bool BACK = (L & 1) != 0;
-  const long ncb = sm.nb[L][tx];
-  const float f = sm.neg[L][tx] ? -1.f : 1.f;
-  const float sgn = BACK ? -sg : sg;
-  P2 w[6], h[3], g[3];
-  in.load_p(soff + ncb, w);
-  project_p<MU>(w, sgn, h);
+// g = U h (U^dag h for BACK) for both spins of h in the lanes; e[k] = link element k as
+// (re, re, im, im)
+template <bool BACK>
+__device__ __forceinline__ void link_mul_p(const float4 e[9], const P2 h[3], P2 g[3]) {
   // -Im h (forward) or -Re h (backward) for the terms with a minus sign
   float2 nh[3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) nh[b] = BACK ? __fmul2_rn(bc2(-1.f), h[b].re) : __fmul2_rn(bc2(-1.f), h[b].im);
-  float4 e[9];
-  link_elems(sm, L, tx, e);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     float2 gr = make_float2(0.f, 0.f), gi = make_float2(0.f, 0.f);
@@ -329,6 +318,49 @@ __device__ __forceinline__ void hop_link_smp(const HopArgs<P, RECON>& A, const S
     }
     g[a] = {gr, gi};
   }
+}
+
+// acc += the hop from direction L (mu = L / 2, backward if L odd) for one slice,
+// packed: g = U h (U^dag h backward) with both spins of h in the lanes.  The FP16
+// site scale multiplies the hop's boundary factor instead of the 24 loaded values.
+template <int P, int RECON, int L, typename SM>
+__device__ __forceinline__ void hop_link_smp(const HopArgs<P, RECON>& A, const SM& sm, int tx, float sg,
+                                             const SpinorView<P>& in, long soff, P2 acc[6]) {
+  constexpr int MU = L >> 1;
+  constexpr bool BACK = (L & 1) != 0;
+  const long ncb = sm.nb[L][tx];
+  const float sgn = BACK ? -sg : sg;
+  P2 w[6], h[3], g[3];
+  float scale;
+  in.load_p_raw(soff + ncb, w, &scale);
+  const float f = sm.neg[L][tx] ? -scale : scale;
+  project_p<MU>(w, sgn, h);
+  float4 e[9];
+  link_elems(sm, L, tx, e);
+  link_mul_p<BACK>(e, h, g);
+  reconstruct_p<MU>(g, sgn, f, acc);
+}
+
+// The same for one site whose links come from global memory (single-slice
+// stencil): direction MU, forward or backward.
+template <int P, int RECON, int MU, bool BACK>
+__device__ __forceinline__ void hop_link_gp(const HopArgs<P, RECON>& A, const SiteCoords& c, long cb, float sg,
+                                            const SpinorView<P>& in, long soff, P2 acc[6]) {
+  int wrap;
+  const int j = neighbour_index(A.g, c, MU, BACK ? -1 : +1, &wrap);
+  const long ncb = j >> 1;
+  const float sgn = BACK ? -sg : sg;
+  P2 w[6], h[3], g[3];
+  float scale;
+  in.load_p_raw(soff + ncb, w, &scale);
+  const float f = (wrap && A.g.apbc[MU]) ? -scale : scale;
+  Cx<float> u[9];
+  A.U.load(BACK ? 1 - A.out_parity : A.out_parity, MU, BACK ? ncb : cb, u);
+  float4 e[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) e[k] = make_float4(u[k].re, u[k].re, u[k].im, u[k].im);
+  project_p<MU>(w, sgn, h);
+  link_mul_p<BACK>(e, h, g);
   reconstruct_p<MU>(g, sgn, f, acc);
 }
 

@@ -192,6 +192,52 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
   }
 }
 
+// One (site, slice) per thread with the packed FP32x2 arithmetic of stencil.cuh
+// and the links read from global memory (FP32 / FP16): the single-slice stencil
+// for the precisions whose arithmetic, not HBM, bounds it (FP16: the site scale
+// rides on the hop's boundary factor, the link multiply and the projection run
+// two spins per instruction).  PF as in k_hop.
+template <int P, int RECON, int PF>
+__global__ void __launch_bounds__(256) k_hop_pk(HopArgs<P, RECON> A) {
+  pdl_enter();
+  if (A.stop && *A.stop) return;
+  const int sblock = fdiv(blockIdx.x, A.d_ntiles);
+  const int q = blockIdx.x - sblock * A.ntiles;
+  const int cb = sblock * blockDim.x + threadIdx.x;
+  if (cb >= A.g.Vh) return;
+  const SiteCoords c = cb_to_site(A.g, cb, A.out_parity);
+  const int r = fdiv(q, A.d_ls), s = q - r * A.ls;
+  const SpinorView<P> in = A.in.offset_rhs(r);
+  const long soff = (long)s * A.g.Vh;
+  P2 acc[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) acc[k] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  const float sg = A.dagger ? 1.f : -1.f;
+  prefetch_before<PF, P, RECON, 0>(A, c, cb, q);
+  hop_link_gp<P, RECON, 0, false>(A, c, cb, sg, in, soff, acc);
+  hop_link_gp<P, RECON, 0, true>(A, c, cb, sg, in, soff, acc);
+  prefetch_before<PF, P, RECON, 1>(A, c, cb, q);
+  hop_link_gp<P, RECON, 1, false>(A, c, cb, sg, in, soff, acc);
+  hop_link_gp<P, RECON, 1, true>(A, c, cb, sg, in, soff, acc);
+  prefetch_before<PF, P, RECON, 2>(A, c, cb, q);
+  hop_link_gp<P, RECON, 2, false>(A, c, cb, sg, in, soff, acc);
+  hop_link_gp<P, RECON, 2, true>(A, c, cb, sg, in, soff, acc);
+  hop_link_gp<P, RECON, 3, false>(A, c, cb, sg, in, soff, acc);
+  hop_link_gp<P, RECON, 3, true>(A, c, cb, sg, in, soff, acc);
+  const long site = soff + cb;
+  const float2 a2 = bc2((float)A.a);
+  P2 o[6];
+  if (A.xpay) {
+    A.x.offset_rhs(r).load_p(site, o);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o[k] = {fma2(a2, acc[k].re, o[k].re), fma2(a2, acc[k].im, o[k].im)};
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o[k] = {__fmul2_rn(a2, acc[k].re), __fmul2_rn(a2, acc[k].im)};
+  }
+  A.out.offset_rhs(r).store_p(site, o);
+}
+
 // Single right-hand side, out = x + a H in, with a BiCGStab inner product
 // formed in the epilogue from the values just stored (FP32 / FP64 storage,
 // so the stored and the computed values agree): RED = 1 gives (rt, out),
@@ -559,6 +605,19 @@ void launch_tile(HopLaunch<P, RECON>* L, int block) {
   launch_k(k_hop<P, RECON, TILE, PF>, (unsigned)(sblocks * A.ntiles), block, 0, L->st, A);
 }
 
+template <int P, int RECON, int PF>
+void launch_pk(HopLaunch<P, RECON>* L, int block) {
+  if constexpr (P == P64) {
+    raise(QCD_ERR_UNSUPPORTED, "no packed FP64 stencil");
+  } else {
+    HopArgs<P, RECON> A = L->args;
+    A.ntiles = A.nslices;
+    A.d_ntiles = make_fastdiv((unsigned)A.ntiles);
+    const long sblocks = (A.g.Vh + block - 1) / block;
+    launch_k(k_hop_pk<P, RECON, PF>, (unsigned)(sblocks * A.ntiles), block, 0, L->st, A);
+  }
+}
+
 template <int P, int RECON, int BY, int TS, int RED = 0, int OCC = 0>
 void launch_sm(HopLaunch<P, RECON>* L) {
   HopArgs<P, RECON> A = L->args;
@@ -586,7 +645,8 @@ void launch_smp(HopLaunch<P, RECON>* L) {
 }
 
 // cfg.tile > 0: register tile of that many slices per thread (k_hop), 101 /
-// 201: one slice per thread with prefetch mode 1 / 2;
+// 201: one slice per thread with prefetch mode 1 / 2; 301 / 311 / 321: one slice
+// per thread with packed arithmetic (k_hop_pk), prefetch mode 0 / 1 / 2;
 // cfg.tile < 0: shared-memory links (k_hop_sm), -tile = 10 * BY + TS for
 // BY thread rows of TS slices each; -tile = 200 + 10 * BY + TS: the same with at most
 // 64 registers per thread (32 resident warps per SM); -tile = 500 + 10 * BY + 1:
@@ -618,6 +678,9 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case 1: launch_tile<P, RECON, 1>(L, cfg.block); break;
       case 101: launch_tile<P, RECON, 1, 1>(L, cfg.block); break;
       case 201: launch_tile<P, RECON, 1, 2>(L, cfg.block); break;
+      case 301: launch_pk<P, RECON, 0>(L, cfg.block); break;
+      case 311: launch_pk<P, RECON, 1>(L, cfg.block); break;
+      case 321: launch_pk<P, RECON, 2>(L, cfg.block); break;
       case 2: launch_tile<P, RECON, 2>(L, cfg.block); break;
       case 4: launch_tile<P, RECON, 4>(L, cfg.block); break;
       case -41: launch_sm<P, RECON, 4, 1>(L); break;
@@ -701,6 +764,9 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64)  // one slice per thread with prefetches (memory-bound precisions)
     for (int pf : {101, 201})
       for (int b : blocks) cands.push_back({b, pf});
+  if (P != P64 && !A.red)  // one slice per thread, packed arithmetic, with 0, 1 or 2 directions of prefetch
+    for (int pk : {301, 311, 321})
+      for (int b : blocks) cands.push_back({b, pk});
   if (multi_red) {  // shared-memory links, one slice per thread
     cands = {{128, -41}, {256, -81}, {128, -241}, {256, -281}, {128, -541}, {256, -581}, {128, -641}, {256, -681}};
     if (RECON == 12) {

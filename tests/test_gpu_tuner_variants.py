@@ -1,7 +1,7 @@
 """Every launch shape the stencil autotuner can choose computes the same operator.
 
 Each candidate (register tiles of 1 / 2 / 4 slices, the L1-prefetching single-slice
-kernels, the shared-memory link kernels with scalar and packed FP32x2 arithmetic, the
+kernels, the packed single-slice kernels, the shared-memory link kernels with scalar and packed FP32x2 arithmetic, the
 fused-reduction stencils of the BiCGStab iteration with and without prefetches, and the
 domain-wall stencil with the fifth-dimension inverse in its epilogue) is forced through a tuning-cache
 file (QCD_TUNECACHE) in a child process, on a lattice of its own so that every
@@ -95,9 +95,9 @@ def _key(L, prec, recon, ns, xp, red):
 def test_every_stencil_candidate_matches_the_oracle(tmp_path):
     device()
     # (tile code, block) of every candidate family; the shared-memory kernels fix their block
-    shapes = [(1, 128), (2, 64), (4, 256), (101, 64), (201, 128), (-41, 128), (-42, 128), (-81, 256), (-82, 256),
-              (-241, 128), (-281, 256), (-541, 128), (-581, 256), (-641, 128), (-681, 256), (-741, 128),
-              (-781, 256)]
+    shapes = [(1, 128), (2, 64), (4, 256), (101, 64), (201, 128), (301, 64), (311, 128), (321, 256), (-41, 128),
+              (-42, 128), (-81, 256), (-82, 256), (-241, 128), (-281, 256), (-541, 128), (-581, 256), (-641, 128),
+              (-681, 256), (-741, 128), (-781, 256)]
     cases, lines, tol = [], [], []
     t = 4
     for prec, recon in (("f32", 12), ("f32", 18), ("f16", 12)):
@@ -110,6 +110,14 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
             t += 2
             cases.append({"kind": "hop", "L": L, "prec": prec, "recon": recon, "nrhs": 16})
             lines.append(f"{_key(L, prec, recon, 16, 0, 0)}\t{block}\t{tile}")
+            tol.append(1e-6 if prec == "f32" else 2e-3)
+    # the packed single-slice stencil on one right-hand side (the FP16 inner solves' D_eo)
+    for prec, recon in (("f32", 12), ("f16", 12), ("f16", 18)):
+        for tile, block in ((301, 128), (311, 256), (321, 64)):
+            L = (4, 4, 4, t)
+            t += 2
+            cases.append({"kind": "hop", "L": L, "prec": prec, "recon": recon, "nrhs": 1})
+            lines.append(f"{_key(L, prec, recon, 1, 0, 0)}\t{block}\t{tile}")
             tol.append(1e-6 if prec == "f32" else 2e-3)
     # the fused-reduction stencils of the FP32 BiCGStab iteration, plain and with prefetches
     for tile, block in ((1, 64), (101, 128), (201, 64)):
