@@ -792,6 +792,11 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     if (!S.bicg()) r_d = ws_field(g, "s.r_d", QCD_DF64, ls, nrhs);
   }
   const Field& r_outer = dfo ? (S.bicg() ? t_d : r_d) : S.r64;
+  // CG on the normal equations: the outer step computes the true residual rhat = bhat -
+  // Mhat x in the outer precision, where its cancellation happens, and the inner solver's
+  // residual Mhat^dag rhat with the inner operator (it is needed only to the inner
+  // precision), straight into the inner vector r
+  const bool cg_inner_normal = !S.bicg() && S.inner != QCD_F64;
 
   // ---- even-odd source: b_hat on the even sites
   pack_field(lat, 0, b, S.b_e, st);
@@ -838,6 +843,11 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   // |b - A x| on the full system from the even-odd residual rhat = bhat - Mhat x_e:
   // Wilson: (rhat, 0);  DWF: (A B^-1 rhat, 0)  (exact reconstruction of x_o)
   std::vector<double> rn(nrhs), rfull(nrhs);
+  auto normal_residual = [&](const Field& rhat) {
+    blas_copy(rhat, S.w, st);
+    apply_mhat(S.opin, S.w, S.r, 1, st, "in");
+    blas_norm2(S.r, rn.data(), st, g);
+  };
   auto true_residual = [&](bool x_is_zero) {
     if (dfo) {
       if (x_is_zero) {
@@ -858,7 +868,10 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
         blas_norm2(t_d, rfull.data(), st, g);
       }
       for (int r = 0; r < nrhs; ++r) rfull[r] = std::sqrt(rfull[r]);
-      if (!S.bicg()) apply_mhat(opdf, t_d, r_d, 1, st, "odf");
+      if (cg_inner_normal) {
+        normal_residual(t_d);
+        return;
+      }
       blas_norm2(r_outer, rn.data(), st, g);
       return;
     }
@@ -883,6 +896,10 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
       blas_norm2(r_e64, rfull.data(), st, g);
       for (int r = 0; r < nrhs; ++r) rfull[r] = std::sqrt(rfull[r]);
       // the inner residual: r_e (BiCGStab) or Mhat^dag r_e (CG)
+      if (cg_inner_normal) {
+        normal_residual(r_e64);
+        return;
+      }
       if (!S.bicg()) apply_mhat(S.op64, r_e64, S.r64, 1, st, "o64");
       blas_norm2(S.r64, rn.data(), st, g);
       return;
@@ -901,6 +918,10 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     }
     for (int r = 0; r < nrhs; ++r) rfull[r] = std::sqrt(rfull[r]);
     // the inner residual: rhat (BiCGStab) or Mhat^dag rhat (CG)
+    if (cg_inner_normal) {
+      normal_residual(S.t64);
+      return;
+    }
     if (S.bicg()) {
       blas_copy(S.t64, S.r64, st);
     } else {
@@ -927,7 +948,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
 
   auto restart_from_residual = [&](bool full) {
     // r (inner) = outer residual; the recursion continues from the true residual
-    blas_copy(r_outer, S.r, st);
+    if (!cg_inner_normal) blas_copy(r_outer, S.r, st);
     if (S.inner != QCD_F64) blas_zero(S.xin, st);
     std::vector<double> re, im;
     if (S.bicg()) {
