@@ -234,7 +234,7 @@ def main():
     ap.add_argument("--profile-prec", default="f32", choices=["f32", "f64", "df64", "f16"],
                     help="precision of the D_eo launches of --profile dslash (and of the domain-wall hop / "
                          "Mhat of --workload dwf --profile dslash / mhat)")
-    ap.add_argument("--workload", default="wilson32", choices=["wilson32", "dwf", "batched", "force"],
+    ap.add_argument("--workload", default="wilson32", choices=["wilson32", "dwf", "batched", "force", "dd"],
                     help="wilson32 (default, the bench line); the others characterise the other "
                          "configurations (domain-wall CG, 12-rhs propagator, force) and print their own line")
     ap.add_argument("--outer", default="f64", choices=["f64", "df64"],

@@ -10,6 +10,8 @@
            chunks, tuned tiles) against 12 single-rhs solves, FP32 inner + FP64, to 1e-10.
 * force:   Wilson 16^4, kappa = 0.12, eps = 0.3 (seed 5), Gaussian phi (seed 0): the backward
            pass of S = phi^dag (M^dag M)^-1 phi (adjoint solve + outer-product kernel).
+* dd:      the 32^3 x 64 Wilson system cut into 2, 4 or 16 subdomains of one process (domain
+           decomposition on one GPU): Mhat and the mixed BiCGStab against the single-domain ones.
 Each prints one JSON line.
 """
 from __future__ import annotations
@@ -45,6 +47,35 @@ def _peak():
     import os
     p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
     return float(json.load(open(p))["hbm_gbs"]) if os.path.exists(p) else 6800.0
+
+
+def _cpu_rate(fn, units, budget_s=6.0, max_reps=20):
+    """The oracle `fn` timed on the host cores over a bounded sample: (units per second, reps, seconds)."""
+    fn()  # warm-up (page-in, thread pool)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        fn()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= max_reps:
+            return units * reps / el, reps, el
+
+
+def _fp64_peak_tflops():
+    """FP64 throughput of this GPU measured live: cuBLAS DGEMM 4096^3 (best of 5 after a warm-up)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = _events()
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
 
 
 def run_dwf(args):
@@ -162,7 +193,33 @@ def run_dwf(args):
         mob[name] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "iters": info[0]["iters"],
                      "updates": info[0]["outer_updates"], "true_resid": info[0]["true_resid"]}
     mob["speedup_f32_df_vs_f64"] = round(mob["f64"]["ms"] / mob["f32_df"]["ms"], 3)
-    out = {"workload": "dwf_16x16x16x32_Ls16_M5_1.8_mf0.02", "hop": hop, "cg": res,
+    # roofline of the dominant kernels: the FP32 hop and the fused hop + W of Mhat (12-real links
+    # once per site, Ls spinors in and out; Mhat's second launch also reads x)
+    peak = _peak()
+    mhat_bytes = 2 * Vh * (8 * 48 + Ls * 2 * 96) + Vh * Ls * 96
+    roof = {"bound": "hbm", "kernel": "multi-slice hop, FP32 12-real (k_hop_smp)",
+            "achieved": hop["f32"]["hop_gbs"], "peak": peak, "unit": "GB/s", "frac": hop["f32"]["hop_frac"],
+            "algorithmic_bytes": Vh * (8 * 48 + Ls * 2 * 96), "traffic": None,
+            "note": "peak of measured copy bandwidth; 8 x 48 B links per 4D site + 96 B in + 96 B out per "
+                    "(site, slice)",
+            "mhat_fused_f32": {"bytes": mhat_bytes, "ms": hop["f32"]["mhat_ms"],
+                               "frac": round(mhat_bytes / hop["f32"]["mhat_ms"] / 1e6 / peak, 4)}}
+    cpu = None
+    if not getattr(args, "no_cpu_baseline", False):
+        from oracle import oracle as ora
+
+        par = ora.parity(L)
+        src = b.copy()
+        src[:, par == 0] = 0
+        rate, reps, el = _cpu_rate(lambda: ora._hop5(L, BC, U, src, out_parity=0), metrics.HOP_FLOP_SITE * Vh * Ls)
+        rate_d, reps_d, el_d = _cpu_rate(lambda: ora.dw(L, BC, Ls, M5, mf, U, b), 1.0)
+        cpu = {"value": round(rate / 1e9, 4), "unit": "GFLOP/s", "cores": ora.num_threads(), "kind": "oracle",
+               "sample": f"{reps} oracle FP64 domain-wall hops (4D hop on all {Ls} slices, {Vh} even sites) "
+                         f"in {el:.1f} s",
+               "dw_apply_s": round(1.0 / rate_d, 3),
+               "dw_apply_sample": f"{reps_d} applications of the full D_DW of Eq. (2) in {el_d:.1f} s"}
+    out = {"workload": "dwf_16x16x16x32_Ls16_M5_1.8_mf0.02", "hop": hop, "cg": res, "roofline": roof,
+           "cpu_baseline": cpu,
            "bicgstab_f32_df": bicg, "mobius_b5_1.5_c5_0.5": mob,
            "note": "cg keys: inner precision, _df = double-float outer steps (else IEEE FP64)",
            "speedup_f16_vs_f64": round(res["f64"]["ms"] / res["f16"]["ms"], 3),
@@ -188,7 +245,7 @@ def run_batched(args):
     o12 = torch.empty(nb12, dtype=torch.uint8, device=dev)
     qcd.field_pack(g, f, "f32", 1, bd, a12, nrhs=12)
     ms12 = _time_launches(lambda: qcd.dslash(g, f, "D_EO", a12, o12, prec="f32", nrhs=12, layout=qcd.INTERNAL))
-    if args.profile != "none":  # ncu: profile 3 launches of the 12-rhs hop (tuned above)
+    if args.profile not in ("none", "cg"):  # ncu: profile 3 launches of the 12-rhs hop (tuned above)
         torch.cuda.profiler.start()
         for _ in range(3):
             qcd.dslash(g, f, "D_EO", a12, o12, prec="f32", nrhs=12, layout=qcd.INTERNAL)
@@ -205,6 +262,14 @@ def run_batched(args):
     x = torch.zeros_like(bd)
     qcd.solve(g, f, bd, x, nrhs=12, **kw)  # warm-up
     x.zero_()
+    if args.profile == "cg":  # ncu launch list: one warmed-up batched solve
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        info, _ = qcd.solve(g, f, bd, x, nrhs=12, **kw)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(f"profile batched solve done: {[i['iters'] for i in info]}", flush=True)
+        return
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     info, _ = qcd.solve(g, f, bd, x, nrhs=12, **kw)
@@ -221,7 +286,22 @@ def run_batched(args):
         iters_seq.append(ik[0]["iters"])
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
-    out = {"workload": "wilson_24x24x24x48_kappa0.124_12pointsources", "x0": x0,
+    peak = _peak()
+    roof = {"bound": "hbm", "kernel": "12-rhs D_eo, FP32 12-real", "achieved": round(alg12 / ms12 / 1e6, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(alg12 / ms12 / 1e6 / peak, 4), "algorithmic_bytes": alg12,
+            "traffic": None, "note": "peak of measured copy bandwidth; 8 x 48 B links per site + 12 x (96 + 96) B"}
+    cpu = None
+    if not getattr(args, "no_cpu_baseline", False):
+        from oracle import oracle as ora
+
+        par = ora.parity(L)
+        src = b[0].copy()
+        src[par == 0] = 0
+        rate, reps, el = _cpu_rate(lambda: ora.hop(L, BC, U, src, out_parity=0), metrics.HOP_FLOP_SITE * Vh)
+        cpu = {"value": round(rate / 1e9, 4), "unit": "GFLOP/s", "cores": ora.num_threads(), "kind": "oracle",
+               "sample": f"{reps} oracle FP64 D_eo applications to one right-hand side ({Vh} sites) in {el:.1f} s"}
+    out = {"workload": "wilson_24x24x24x48_kappa0.124_12pointsources", "x0": x0, "roofline": roof,
+           "cpu_baseline": cpu,
            "dslash12_ms": round(ms12, 4), "dslash12_gflops": round(metrics.HOP_FLOP_SITE * Vh * 12 / ms12 / 1e6, 1),
            "dslash12_gbs": round(alg12 / ms12 / 1e6, 1), "dslash12_frac": round(alg12 / ms12 / 1e6 / _peak(), 4),
            "dslash1_x12_ms": round(12 * ms1, 4),
@@ -288,7 +368,26 @@ def run_force(args):
     ms_eo = _time_launches(lambda: qcd.force_eo(g, f, X, pt, out_t))
     ms_proj = _time_launches(lambda: qcd.force_project(g, out_t, Fm))
     ms_link = _time_launches(lambda: qcd.link_update(Uc, Pc, 0.02))
-    out = {"workload": "force_wilson_16x16x16x16_kappa0.12", "backward_ms": round(min(times[1:]) * 1e3, 3),
+    # the force kernel reads X and eta at a site and its neighbours (2 x 192 B per site from HBM)
+    # and writes 4 links x 144 B; about 250 FP64 flop per link: FP64-bound on this GPU
+    fp64_peak = _fp64_peak_tflops()
+    force_flop = 4 * V * 250
+    roof = {"bound": "alu", "kernel": "force outer product (k_force), FP64",
+            "achieved": round(force_flop / ms / 1e9, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+            "frac": round(force_flop / ms / 1e9 / fp64_peak, 4), "traffic": None,
+            "hbm_frac": round(V * (2 * 192 + 4 * 144) / ms / 1e6 / _peak(), 4),
+            "note": "peak = cuBLAS DGEMM 4096^3 measured in this run; ~250 FP64 flop per link"}
+    cpu = None
+    if not getattr(args, "no_cpu_baseline", False):
+        from oracle import oracle as ora
+
+        Xh = inputs.gaussian_source((V, 4, 3), 1)
+        rate, reps, el = _cpu_rate(lambda: ora.wilson_force(L, BC, kappa, Xh, phi), 1.0)
+        cpu = {"value": round(rate, 4), "unit": "force evaluations/s", "cores": ora.num_threads(), "kind": "oracle",
+               "sample": f"{reps} oracle FP64 force outer products on 16^4 in {el:.1f} s",
+               "gpu_kernel_per_s": round(1e3 / ms, 1)}
+    out = {"workload": "force_wilson_16x16x16x16_kappa0.12", "roofline": roof, "cpu_baseline": cpu,
+           "backward_ms": round(min(times[1:]) * 1e3, 3),
            "force_kernel_ms": round(ms, 4),
            "force_kernel_gbs": round(V * (2 * 192 + 4 * 144) / ms / 1e6, 1),
            "md": {"force_eval_ms": round(min(t_force) * 1e3, 3),
@@ -298,6 +397,61 @@ def run_force(args):
     print(json.dumps(out), flush=True)
 
 
+def run_dd(args):
+    """Domain decomposition on one GPU: the 32^3 x 64 Wilson system (config of the bench line) cut
+    into subdomains held by this process (faces exchanged by device copies while the interior is
+    computed): the decomposed Mhat and BiCGStab against the single-domain ones."""
+    from paper_1712_01505_gb300 import dd
+
+    L, kappa = (32, 32, 32, 64), 0.125
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.2, 2)
+    b = inputs.z2_source((V, 4, 3), 0)
+    dev = torch.device("cuda", 0)
+    f = qcd.wilson(kappa)
+    g = qcd.Gauge.load(torch.from_numpy(U).to(dev), L, BC, recon=12)
+    bd = torch.from_numpy(b).to(dev)
+    out = {"workload": "dd_wilson_32x32x32x64_kappa0.125", "note": "subdomains of one process on one GPU"}
+    src = bd.clone()
+    w = torch.empty_like(bd)
+    ref = {}
+    for prec in ("f32", "f64"):
+        ref[prec] = _time_launches(lambda: qcd.dslash(g, f, "MHAT", src, w, prec=prec), n=10)
+    kw = dict(method=qcd.BICGSTAB, tol=1e-10, inner="f32", delta=1e-5, outer="f64")
+    x = torch.zeros_like(bd)
+    qcd.solve(g, f, bd, x, **kw)
+    x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info1, _ = qcd.solve(g, f, bd, x, **kw)
+    torch.cuda.synchronize()
+    out["single"] = {"mhat_f32_ms": round(ref["f32"], 4), "mhat_f64_ms": round(ref["f64"], 4),
+                     "solve_ms": round((time.perf_counter() - t0) * 1e3, 2), "iters": info1[0]["iters"]}
+    g.free()
+    for P in ((1, 1, 1, 2), (1, 1, 2, 2), (2, 2, 2, 2)):
+        ids = list(range(int(np.prod(P))))
+        D = dd.Decomposition(L, P, BC, ids, [dd.scatter_gauge(U, L, P, s) for s in ids], recon=12)
+        bl = [torch.from_numpy(dd.scatter_spinor(b, L, P, s)).to(dev) for s in ids]
+        ol = [torch.empty_like(t) for t in bl]
+        t = {p: _time_launches(lambda: D.dslash(f, "MHAT", bl, ol, prec=p), n=10) for p in ("f32", "f64")}
+        xl = [torch.zeros_like(t_) for t_ in bl]
+        D.solve(f, bl, xl, tol=1e-10, inner="f32", delta=1e-5)
+        for t_ in xl:
+            t_.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info, _ = D.solve(f, bl, xl, tol=1e-10, inner="f32", delta=1e-5)
+        torch.cuda.synchronize()
+        out["P" + "x".join(map(str, P))] = {"mhat_f32_ms": round(t["f32"], 4), "mhat_f64_ms": round(t["f64"], 4),
+                                            "solve_ms": round((time.perf_counter() - t0) * 1e3, 2),
+                                            "iters": info["iters"], "updates": info["outer_updates"],
+                                            "true_resid": info["true_resid"]}
+        D.free()
+        del bl, ol, xl
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def run_workload(args):
     torch.cuda.set_device(0)
-    {"dwf": run_dwf, "batched": run_batched, "force": run_force}[args.workload](args)
+    {"dwf": run_dwf, "batched": run_batched, "force": run_force, "dd": run_dd}[args.workload](args)

@@ -217,7 +217,7 @@ void fused_impl(const qcd_gauge* gh, const void* links, const DwParams& p, const
   char key[160];
   snprintf(key, sizeof key, "dwhopw p%d r%d L%dx%dx%dx%d ls%d nrhs%d xp%d mob%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], in.ls, in.nrhs, A.xpay, (int)p.mobius());
-  LaunchCfg cfg = tune(key, cands, &run_fused<P, RECON>, &L, st);  // not while a graph is captured
+  LaunchCfg cfg = tune(key, cands, &run_fused<P, RECON>, &L, st, true, stop);  // not while captured or stopped
   run_fused<P, RECON>(&L, cfg);
   QCD_LAUNCH_CK();
 }

@@ -269,9 +269,10 @@ bool tuning_enabled();
 void set_tuning(int mode);
 // candidates are tried with `run` (which must be idempotent) when the key is
 // new and the stream is not capturing; returns the cached or chosen config.
+// `stop` (may be null): the kernels' stop word; no timing while it is raised.
 LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
                void (*run)(void* ctx, const LaunchCfg& cfg), void* ctx, cudaStream_t st,
-               bool allow_timing = true);
+               bool allow_timing = true, const int* stop = nullptr);
 
 // device properties
 int sm_count();

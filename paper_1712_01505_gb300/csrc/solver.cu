@@ -53,8 +53,18 @@ struct Scal {
   int active;
   int flag;
   int iters;
-  int pad;
+  int flag_iter;  // iters when flag was raised
 };
+
+// a right-hand side whose outer step is due waits at most this many iterations for
+// the others (several right-hand sides), so that steps due at about the same time
+// share one synchronisation
+constexpr int kFlagWait = 2;
+
+__device__ __forceinline__ void raise_flag(Scal& s, int fl) {
+  if (s.flag == FLAG_NONE) s.flag_iter = s.iters;
+  s.flag = fl;
+}
 
 constexpr int kThreads = 256;
 constexpr int kMaxPartial = 4;
@@ -328,11 +338,11 @@ __global__ void k_bicg_check(Scal* sc, const double* partial, int nblk, int* ctl
   s.rho_new[1] = d[1];
   s.r2 = d[2];
   if (bad(d[0]) || bad(d[1]) || bad(d[2])) {
-    s.flag = FLAG_NAN;
+    raise_flag(s, FLAG_NAN);
   } else if (d[2] <= s.stop2) {
-    s.flag = FLAG_CHECK;
+    raise_flag(s, FLAG_CHECK);
   } else if (s.delta2 > 0.0 && d[2] <= s.delta2 * s.r2_ref) {
-    s.flag = FLAG_UPDATE;
+    raise_flag(s, FLAG_UPDATE);
   }
   const double2 b = cmul2(cdiv(make_double2(d[0], d[1]), make_double2(s.rho[0], s.rho[1])),
                           cdiv(make_double2(s.alpha[0], s.alpha[1]), make_double2(s.omega[0], s.omega[1])));
@@ -445,11 +455,11 @@ __global__ void k_cg_check(Scal* sc, const double* partial, int nblk, int* ctl, 
   s.rr_new = d[0];
   s.r2 = d[0];
   if (bad(d[0]))
-    s.flag = FLAG_NAN;
+    raise_flag(s, FLAG_NAN);
   else if (d[0] <= s.stop2)
-    s.flag = FLAG_CHECK;
+    raise_flag(s, FLAG_CHECK);
   else if (s.delta2 > 0.0 && d[0] <= s.delta2 * s.r2_ref)
-    s.flag = FLAG_UPDATE;
+    raise_flag(s, FLAG_UPDATE);
   s.beta[0] = d[0] / s.rr;
   s.beta[1] = 0.0;
   if (decide && s.flag != FLAG_NONE) *ctl = 1;
@@ -477,12 +487,11 @@ __global__ void k_rdot(AnyView a_, AnyView b_, long n, double* partial, const Sc
 
 __global__ void k_reset(int* ctl) { *ctl = 0; }
 
-// End-of-iteration stop decision over all right-hand sides (<<<1, 32>>>).  A
-// right-hand side that has flagged (outer step due, target reached) keeps
-// iterating until every active one has flagged, so that the batch shares one
-// FP64 outer step, unless one of them is overdue: its residual has dropped a
-// further factor 10 past its trigger (or breakdown / NaN, which stop at once
-// where they are detected).
+// End-of-iteration stop decision over all right-hand sides (<<<1, 32>>>).  The
+// outer step is made for the right-hand sides that have flagged (outer step due,
+// target reached) only; a flagged one keeps iterating for up to kFlagWait
+// iterations while others may flag too, so that their steps share one host
+// synchronisation (breakdown / NaN stop at once).
 __global__ void k_decide(const Scal* sc, int nrhs, int* ctl) {
   pdl_enter();
   if (STOPPED(ctl) || threadIdx.x) return;
@@ -493,9 +502,7 @@ __global__ void k_decide(const Scal* sc, int nrhs, int* ctl) {
     ++nact;
     if (s.flag == FLAG_NONE) continue;
     ++nflag;
-    if (s.flag == FLAG_NAN || s.flag == FLAG_BREAKDOWN) ++urgent;
-    else if (s.flag == FLAG_UPDATE && s.r2 <= 0.01 * s.delta2 * s.r2_ref) ++urgent;
-    else if (s.flag == FLAG_CHECK && s.r2 <= 0.01 * s.stop2) ++urgent;
+    if (s.flag == FLAG_NAN || s.flag == FLAG_BREAKDOWN || s.iters - s.flag_iter >= kFlagWait) ++urgent;
   }
   if (nflag > 0 && (nflag == nact || urgent > 0)) *ctl = 1;
 }
@@ -681,6 +688,7 @@ struct Solver {
 
   // host-side complex dot products (rt, r) per rhs (synchronises)
   void cdot_host(const Field& a, const Field& b, std::vector<double>& re, std::vector<double>& im) {
+    const int nrhs = a.nrhs;
     dim3 grid(nblk, nrhs);
     if (a.prec == QCD_F64)
       launch_k(k_cdot<double>, grid, kThreads, 0, st, any_view(a), any_view(b), a.nsites(), partial, nullptr,
@@ -843,36 +851,44 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   // |b - A x| on the full system from the even-odd residual rhat = bhat - Mhat x_e:
   // Wilson: (rhat, 0);  DWF: (A B^-1 rhat, 0)  (exact reconstruction of x_o)
   std::vector<double> rn(nrhs), rfull(nrhs);
-  auto normal_residual = [&](const Field& rhat) {
-    blas_copy(rhat, S.w, st);
-    apply_mhat(S.opin, S.w, S.r, 1, st, "in");
-    blas_norm2(S.r, rn.data(), st, g);
+  // Outer-step pieces act on the right-hand sides [r0, r0 + n): views of the fields
+  // restricted to them (the whole field when n = nrhs)
+  auto sub = [&](const Field& f, int r0, int n) { return n == nrhs ? f : f.rhs_range(r0, n); };
+  auto normal_residual = [&](const Field& rhat, int r0, int n) {
+    Field w = sub(S.w, r0, n), r = sub(S.r, r0, n);
+    blas_copy(rhat, w, st);
+    apply_mhat(S.opin, w, r, 1, st, "in");
+    blas_norm2(r, rn.data() + r0, st, g);
   };
-  auto true_residual = [&](bool x_is_zero) {
+  auto true_residual = [&](bool x_is_zero, int r0, int n) {
+    double* rf = rfull.data() + r0;
+    Field t64 = sub(S.t64, r0, n), u64 = sub(S.u64, r0, n), x64 = sub(S.x64, r0, n), bh = sub(S.bh, r0, n);
+    Field r64 = sub(S.r64, r0, n);
     if (dfo) {
+      Field td = sub(t_d, r0, n), xd = sub(x_d, r0, n), ud = sub(u_d, r0, n), bhd = sub(bh_d, r0, n);
       if (x_is_zero) {
-        blas_copy(bh_d, t_d, st);
+        blas_copy(bhd, td, st);
       } else if (!dwf) {
         // rhat = bhat - x + kappa^2 H_eo H_oe x  (H -> H^dag for the adjoint system)
-        hop_df(g, x_d, u_d, 1, dag, 1.0, nullptr, nullptr, 0.0, st);
-        hop_df(g, u_d, t_d, 0, dag, f.kappa * f.kappa, &bh_d, &x_d, -1.0, st);
+        hop_df(g, xd, ud, 1, dag, 1.0, nullptr, nullptr, 0.0, st);
+        hop_df(g, ud, td, 0, dag, f.kappa * f.kappa, &bhd, &xd, -1.0, st);
       } else {
-        apply_mhat(opdf, x_d, t_d, dag, st, "odf");
-        blas_axpby(1.0, bh_d, -1.0, t_d, st);  // rhat = bhat - Mhat x
+        apply_mhat(opdf, xd, td, dag, st, "odf");
+        blas_axpby(1.0, bhd, -1.0, td, st);  // rhat = bhat - Mhat x
       }
       if (dwf) {  // |A rhat| (to FP64 for the block A; it decides no more than the stop)
-        blas_copy(t_d, S.t64, st);
-        dw_a_binv(dp, S.t64, S.u64, st);
-        blas_norm2(S.u64, rfull.data(), st, g);
+        blas_copy(td, t64, st);
+        dw_a_binv(dp, t64, u64, st);
+        blas_norm2(u64, rf, st, g);
       } else {
-        blas_norm2(t_d, rfull.data(), st, g);
+        blas_norm2(td, rf, st, g);
       }
-      for (int r = 0; r < nrhs; ++r) rfull[r] = std::sqrt(rfull[r]);
+      for (int r = r0; r < r0 + n; ++r) rfull[r] = std::sqrt(rfull[r]);
       if (cg_inner_normal) {
-        normal_residual(t_d);
+        normal_residual(td, r0, n);
         return;
       }
-      blas_norm2(r_outer, rn.data(), st, g);
+      blas_norm2(sub(r_outer, r0, n), rn.data() + r0, st, g);
       return;
     }
     if (wil64) {
@@ -881,56 +897,57 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
       //   r_e = b_e - x_e + kappa H_eo x_o  (= bhat - Mhat x_e; the odd half is zero up to
       // the rounding of x_o), so that the outer step that reaches the target has already
       // computed the final solution and its true residual.
+      Field re = sub(r_e64, r0, n), xo = sub(S.xo64, r0, n), bo = sub(S.b_o, r0, n), be = sub(S.b_e, r0, n);
       if (x_is_zero) {
-        blas_copy(S.bh, r_e64, st);  // x = (0, b_o): r_e = bhat, h = 0
-        blas_copy(S.b_o, S.xo64, st);
-        blas_zero(S.u64, st);
+        blas_copy(bh, re, st);  // x = (0, b_o): r_e = bhat, h = 0
+        blas_copy(bo, xo, st);
+        blas_zero(u64, st);
       } else {
-        hop(g, S.x64, S.u64, 1, dag, 1.0, nullptr, st);  // h
-        blas_copy(S.b_o, S.xo64, st);
-        blas_axpby(f.kappa, S.u64, 1.0, S.xo64, st);  // x_o
-        blas_copy(S.b_e, S.t64, st);
-        blas_axpby(-1.0, S.x64, 1.0, S.t64, st);  // b_e - x_e
-        hop(g, S.xo64, r_e64, 0, dag, f.kappa, &S.t64, st);  // r_e
+        hop(g, x64, u64, 1, dag, 1.0, nullptr, st);  // h
+        blas_copy(bo, xo, st);
+        blas_axpby(f.kappa, u64, 1.0, xo, st);  // x_o
+        blas_copy(be, t64, st);
+        blas_axpby(-1.0, x64, 1.0, t64, st);  // b_e - x_e
+        hop(g, xo, re, 0, dag, f.kappa, &t64, st);  // r_e
       }
-      blas_norm2(r_e64, rfull.data(), st, g);
-      for (int r = 0; r < nrhs; ++r) rfull[r] = std::sqrt(rfull[r]);
+      blas_norm2(re, rf, st, g);
+      for (int r = r0; r < r0 + n; ++r) rfull[r] = std::sqrt(rfull[r]);
       // the inner residual: r_e (BiCGStab) or Mhat^dag r_e (CG)
       if (cg_inner_normal) {
-        normal_residual(r_e64);
+        normal_residual(re, r0, n);
         return;
       }
-      if (!S.bicg()) apply_mhat(S.op64, r_e64, S.r64, 1, st, "o64");
-      blas_norm2(S.r64, rn.data(), st, g);
+      if (!S.bicg()) apply_mhat(S.op64, re, r64, 1, st, "o64");
+      blas_norm2(r64, rn.data() + r0, st, g);
       return;
     }
     if (x_is_zero) {
-      blas_copy(S.bh, S.t64, st);  // rhat = bhat
+      blas_copy(bh, t64, st);  // rhat = bhat
     } else {
-      apply_mhat(S.op64, S.x64, S.t64, dag, st, "o64");
-      blas_axpby(1.0, S.bh, -1.0, S.t64, st);  // t64 = bhat - Mhat x
+      apply_mhat(S.op64, x64, t64, dag, st, "o64");
+      blas_axpby(1.0, bh, -1.0, t64, st);  // t64 = bhat - Mhat x
     }
     if (dwf) {
-      dw_a_binv(dp, S.t64, S.u64, st);
-      blas_norm2(S.u64, rfull.data(), st, g);
+      dw_a_binv(dp, t64, u64, st);
+      blas_norm2(u64, rf, st, g);
     } else {
-      blas_norm2(S.t64, rfull.data(), st, g);
+      blas_norm2(t64, rf, st, g);
     }
-    for (int r = 0; r < nrhs; ++r) rfull[r] = std::sqrt(rfull[r]);
+    for (int r = r0; r < r0 + n; ++r) rfull[r] = std::sqrt(rfull[r]);
     // the inner residual: rhat (BiCGStab) or Mhat^dag rhat (CG)
     if (cg_inner_normal) {
-      normal_residual(S.t64);
+      normal_residual(t64, r0, n);
       return;
     }
     if (S.bicg()) {
-      blas_copy(S.t64, S.r64, st);
+      blas_copy(t64, r64, st);
     } else {
-      apply_mhat(S.op64, S.t64, S.r64, 1, st, "o64");
+      apply_mhat(S.op64, t64, r64, 1, st, "o64");
     }
-    blas_norm2(S.r64, rn.data(), st, g);
+    blas_norm2(r64, rn.data() + r0, st, g);
   };
 
-  true_residual(!prm.x0_given);
+  true_residual(!prm.x0_given, 0, nrhs);
   std::vector<double> target(nrhs);
   std::vector<int> conv(nrhs, 0), status(nrhs, QCD_OK), updates(nrhs, 0), restarts(nrhs, 0);
   int nactive = 0;
@@ -946,28 +963,33 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     }
   }
 
-  auto restart_from_residual = [&](bool full) {
+  auto restart_from_residual = [&](bool full, int r0, int n) {
     // r (inner) = outer residual; the recursion continues from the true residual
-    if (!cg_inner_normal) blas_copy(r_outer, S.r, st);
-    if (S.inner != QCD_F64) blas_zero(S.xin, st);
+    Field r = sub(S.r, r0, n), rt = sub(S.rt, r0, n), p = sub(S.p, r0, n), v = sub(S.v, r0, n);
+    if (!cg_inner_normal) blas_copy(sub(r_outer, r0, n), r, st);
+    if (S.inner != QCD_F64) {
+      Field xin = sub(S.xin, r0, n);
+      blas_zero(xin, st);
+    }
     std::vector<double> re, im;
     if (S.bicg()) {
       if (full) {
-        blas_copy(S.r, S.rt, st);
-        blas_zero(S.p, st);
-        blas_zero(S.v, st);
+        blas_copy(r, rt, st);
+        blas_zero(p, st);
+        blas_zero(v, st);
       }
-      S.cdot_host(S.rt, S.r, re, im);
+      S.cdot_host(rt, r, re, im);
     }
-    for (int r = 0; r < nrhs; ++r) {
-      Scal& s = S.hsc[r];
-      s.active = !conv[r];
+    for (int k = 0; k < n; ++k) {
+      const int rr = r0 + k;
+      Scal& s = S.hsc[rr];
+      s.active = !conv[rr];
       s.flag = FLAG_NONE;
-      s.r2_ref = rn[r];
-      s.r2 = rn[r];
+      s.r2_ref = rn[rr];
+      s.r2 = rn[rr];
       // inner phase ends for a true-residual check at the scaled target
-      double ratio = rfull[r] > 0 ? std::sqrt(rn[r]) / rfull[r] : 1.0;
-      double tgt = 0.5 * target[r] * ratio;
+      double ratio = rfull[rr] > 0 ? std::sqrt(rn[rr]) / rfull[rr] : 1.0;
+      double tgt = 0.5 * target[rr] * ratio;
       s.stop2 = tgt * tgt;
       s.delta2 = (S.inner == QCD_F64) ? 0.0 : delta * delta;
       if (S.bicg()) {
@@ -976,8 +998,8 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
           s.alpha[0] = 1.0, s.alpha[1] = 0.0;
           s.omega[0] = 1.0, s.omega[1] = 0.0;
         }
-        s.rho_new[0] = re[r];
-        s.rho_new[1] = im[r];
+        s.rho_new[0] = re[k];
+        s.rho_new[1] = im[k];
         // the first iteration's beta (later ones are formed by k_bicg_check)
         const std::complex<double> b = (std::complex<double>(s.rho_new[0], s.rho_new[1]) /
                                         std::complex<double>(s.rho[0], s.rho[1])) *
@@ -987,16 +1009,16 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
         s.beta[1] = b.imag();
       } else {
         if (full) s.rr = 1.0;
-        s.rr_new = rn[r];
+        s.rr_new = rn[rr];
         s.beta[0] = s.rr_new / s.rr;  // the first iteration's beta (p = 0 after a full restart)
         s.beta[1] = 0.0;
       }
     }
-    if (full && !S.bicg()) blas_zero(S.p, st);
+    if (full && !S.bicg()) blas_zero(p, st);
   };
 
   for (int r = 0; r < nrhs; ++r) S.hsc[r].iters = 0;
-  if (nactive > 0) restart_from_residual(true);
+  if (nactive > 0) restart_from_residual(true, 0, nrhs);
   S.upload();
 
   // host-side fault injection for tests (no device fault is ever provoked):
@@ -1018,7 +1040,21 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   // a chunk stops short of the expected next outer step and the last few
   // iterations run in chunks of 8 / 2: few launches are wasted after a stop.
   int last_stop = 0, gap = 0;
-  bool resid_stale = false;  // x64 changed since the last true_residual (plain FP64 solves)
+  // x64 of a right-hand side changed since its last true_residual (plain FP64 solves)
+  std::vector<char> stale(nrhs, 0);
+  // run `fn(r0, n)` over the maximal runs of consecutive right-hand sides with sel[r]
+  auto for_runs = [&](const std::vector<char>& sel, auto fn) {
+    for (int r0 = 0; r0 < nrhs;) {
+      if (!sel[r0]) {
+        ++r0;
+        continue;
+      }
+      int n = 1;
+      while (r0 + n < nrhs && sel[r0 + n]) ++n;
+      fn(r0, n);
+      r0 += n;
+    }
+  };
   while (nactive > 0) {
     int maxit = 0;
     for (int r = 0; r < nrhs; ++r)
@@ -1042,11 +1078,17 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
       S.run_chunk(k, graph && !capped);
     }
     // a plain FP64 solve iterates on x64 itself: the outer step's x_o and residual are stale
-    if (S.inner == QCD_F64) resid_stale = true;
+    if (S.inner == QCD_F64)
+      for (int r = 0; r < nrhs; ++r) stale[r] = stale[r] || !conv[r];
     S.download();
+    // ---- outer step for the right-hand sides whose step is due; the others go on
+    // iterating from where they are
+    std::vector<char> due(nrhs, 0);
     bool any = false;
-    for (int r = 0; r < nrhs; ++r)
-      if (S.hsc[r].active && S.hsc[r].flag != FLAG_NONE) any = true;
+    for (int r = 0; r < nrhs; ++r) {
+      due[r] = !conv[r] && S.hsc[r].active && S.hsc[r].flag != FLAG_NONE;
+      any = any || due[r];
+    }
     if (!any) continue;
     {
       int now = 0;
@@ -1055,31 +1097,49 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
       if (now > last_stop) gap = now - last_stop;
       last_stop = now;
     }
-    // ---- outer FP64 step for every right-hand side
-    bool need_full_restart = false;
+    std::vector<char> full(nrhs, 0);
     for (int r = 0; r < nrhs; ++r) {
+      if (!due[r]) continue;
       Scal& s = S.hsc[r];
       if (s.flag == FLAG_NAN) {
         status[r] = QCD_ERR_NAN;
       }
       if (s.flag == FLAG_BREAKDOWN) {
         if (++restarts[r] > 2) status[r] = QCD_ERR_BREAKDOWN;
-        need_full_restart = true;
+        full[r] = 1;
       }
     }
-    if (S.inner != QCD_F64) blas_axpby(1.0, S.xin, 1.0, dfo ? x_d : S.x64, st);
-    true_residual(false);
-    resid_stale = false;
+    for_runs(due, [&](int r0, int n) {
+      if (S.inner != QCD_F64) {
+        Field xin = sub(S.xin, r0, n), xo = sub(dfo ? x_d : S.x64, r0, n);
+        blas_axpby(1.0, xin, 1.0, xo, st);
+      }
+      true_residual(false, r0, n);
+      for (int r = r0; r < r0 + n; ++r) stale[r] = 0;
+    });
     nactive = 0;
+    std::vector<char> again(nrhs, 0), again_full(nrhs, 0);
     for (int r = 0; r < nrhs; ++r) {
       if (conv[r]) continue;
+      if (!due[r]) {
+        ++nactive;
+        continue;
+      }
       ++updates[r];
-      if (rfull[r] <= target[r]) conv[r] = 1;
-      else if (status[r] == QCD_ERR_NAN || status[r] == QCD_ERR_BREAKDOWN) conv[r] = 2;  // give up
-      else ++nactive;
+      if (rfull[r] <= target[r]) {
+        conv[r] = 1;
+        S.hsc[r].active = 0;
+      } else if (status[r] == QCD_ERR_NAN || status[r] == QCD_ERR_BREAKDOWN) {
+        conv[r] = 2;  // give up
+        S.hsc[r].active = 0;
+      } else {
+        ++nactive;
+        (full[r] ? again_full : again)[r] = 1;
+      }
     }
     if (nactive == 0) break;
-    restart_from_residual(need_full_restart);
+    for_runs(again, [&](int r0, int n) { restart_from_residual(false, r0, n); });
+    for_runs(again_full, [&](int r0, int n) { restart_from_residual(true, r0, n); });
     S.upload();
   }
 
@@ -1087,9 +1147,9 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   std::vector<double> re_(nrhs), ro_(nrhs);
   Field xe = S.x64, xo = S.t64;
   if (wil64) {
-    // x_e = x64 and x_o, h and r_e of the last outer step (recomputed if a plain FP64
+    // x_e = x64 and x_o, h and r_e of the last outer step (recomputed where a plain FP64
     // solve stopped at maxiter after iterating past it)
-    if (resid_stale) true_residual(false);
+    for_runs(stale, [&](int r0, int n) { true_residual(false, r0, n); });
     unpack_field(lat, 0, S.x64, x, st);
     unpack_field(lat, 1, S.xo64, x, st);
     blas_norm2(r_e64, re_.data(), st, g);

@@ -7,7 +7,9 @@
 // when QCD_TUNECACHE names a file, appended to it and read back by later
 // processes.  Candidates must be idempotent (out-of-place stencils).  While a
 // stream is being captured into a CUDA graph nothing can be timed, so an
-// unknown key then falls back to the first candidate without caching it.
+// unknown key then falls back to the first candidate without caching it; the
+// same when the kernels' stop word (the solver's) is raised, which would make
+// every candidate an empty launch.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -87,7 +89,7 @@ int sm_count() {
 
 LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
                void (*run)(void* ctx, const LaunchCfg& cfg), void* ctx, cudaStream_t st,
-               bool allow_timing) {
+               bool allow_timing, const int* stop) {
   if (cands.empty()) raise(QCD_ERR_ARG, "tune: no candidates for %s", key.c_str());
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -102,6 +104,14 @@ LaunchCfg tune(const std::string& key, const std::vector<LaunchCfg>& cands,
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   QCD_CK(cudaStreamIsCapturing(st, &cs));
   if (cs != cudaStreamCaptureStatusNone || cands.size() == 1) return cands[0];
+  if (stop) {
+    // a kernel whose stop word is raised returns at once: timing it would time empty
+    // launches, so an unknown key then takes the first candidate without caching it
+    int v = 0;
+    QCD_CK(cudaMemcpyAsync(&v, stop, sizeof v, cudaMemcpyDeviceToHost, st));
+    QCD_CK(cudaStreamSynchronize(st));
+    if (v != 0) return cands[0];
+  }
 
   cudaEvent_t e0, e1;
   QCD_CK(cudaEventCreate(&e0));

@@ -777,7 +777,7 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   char key[160];
   snprintf(key, sizeof key, "hop p%d r%d L%dx%dx%dx%d ns%d xp%d red%d", P, RECON, gh->lat.L[0],
            gh->lat.L[1], gh->lat.L[2], gh->lat.L[3], A.nslices, A.xpay, A.red);
-  LaunchCfg cfg = tune(key, cands, &run_cfg<P, RECON>, &L, st, allow_tuning);
+  LaunchCfg cfg = tune(key, cands, &run_cfg<P, RECON>, &L, st, allow_tuning, stop);
   run_cfg<P, RECON>(&L, cfg);
   QCD_LAUNCH_CK();
   if (multi_red) {  // per right-hand side sums of the per-warp partials

@@ -429,7 +429,7 @@ void hop_df(const qcd_gauge* gh, const Field& in, Field& out, int out_parity, in
   char key[128];
   snprintf(key, sizeof key, "hopdf L%dx%dx%dx%d ns%d x%d%d", gh->lat.L[0], gh->lat.L[1], gh->lat.L[2],
            gh->lat.L[3], L.nslices, A.x1, A.x2);
-  LaunchCfg cfg = tune(key, cands, &run_df, &L, st, allow_tuning);
+  LaunchCfg cfg = tune(key, cands, &run_df, &L, st, allow_tuning, stop);
   run_df(&L, cfg);
   QCD_LAUNCH_CK();
 }
