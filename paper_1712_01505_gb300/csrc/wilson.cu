@@ -527,6 +527,135 @@ __device__ __forceinline__ void hop_smp(const HopArgs<P, RECON>& A) {
   }
 }
 
+// Tensor-core variant of the 12-rhs FP16 stencil (a measured prototype): one
+// direction's link multiply (t forward) for the 12 right-hand sides x 2 spins
+// of a site runs as warp-level MMAs, m16n8k16 with FP16 operands and FP32
+// accumulation.  Per site it is the real 6 x 6 form of U_t(x) (rows: Re, Im of
+// the three output colours) times a 6 x 24 matrix of projected half spinors
+// (columns: right-hand side x spin), in three n-tiles of 8 columns; the operand
+// rows and columns beyond 6 are zero padding.  The half spinors reach the MMA
+// lanes through shared memory (rounded to FP16: the FP16 spinors are stored
+// scaled to |psi| <= 1 per site, so |h| <= 2), the products return through
+// shared memory to the thread that owns the (site, right-hand side) and are
+// reconstructed there; the other seven hops use the packed FP32x2 path.  Block:
+// 32 sites x 12 right-hand sides (one warp per right-hand side).
+__device__ __forceinline__ unsigned pack_h2(float lo, float hi) {
+  const __half2 v = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+// element (i, j) of the real form of U: rows Re / Im of the output colour, columns Re / Im of
+// the input colour
+__device__ __forceinline__ float real_form(const Cx<float> u[9], int i, int j) {
+  const Cx<float> e = u[(i % 3) * 3 + (j % 3)];
+  if (i < 3) return j < 3 ? e.re : -e.im;
+  return j < 3 ? e.im : e.re;
+}
+
+template <int P, int RECON>
+__global__ void __launch_bounds__(384) k_hop_tc(HopArgs<P, RECON> A) {
+  pdl_enter();
+  static_assert(P == P16 && RECON == 12, "the tensor-core prototype is the FP16, 12-real stencil");
+  if (A.stop && *A.stop) return;
+  __shared__ SmLinks12 sm;
+  __shared__ __align__(16) unsigned Hs[32][24][4];  // [site][column][k pair]: FP16 pairs, k = 6, 7 zero
+  __shared__ __align__(16) float Ds[32][6][24];     // [site][row][column]
+  const int tx = threadIdx.x, ty = threadIdx.y;     // site of the block, right-hand side (= warp)
+  const int cb = blockIdx.x * 32 + tx;
+  const bool valid = cb < A.g.Vh;
+  stage_links_sm12<P, RECON, 12>(A, sm, tx, ty, cb, valid);
+  __syncthreads();
+  const int r = fdiv(ty, A.d_ls), s = ty - r * A.ls;
+  const SpinorView<P> in = A.in.offset_rhs(r);
+  const long soff = (long)s * A.g.Vh;
+  P2 acc[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) acc[q] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  const float sg = A.dagger ? 1.f : -1.f;
+  if (valid) {
+    hop_link_smp<P, RECON, 0>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 1>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 2>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 3>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 4>(A, sm, tx, sg, in, soff, acc);
+    hop_link_smp<P, RECON, 5>(A, sm, tx, sg, in, soff, acc);
+  }
+  // direction L = 6 (t forward) by MMA
+  constexpr int L = 6, MU = 3;
+  float f = 0.f;
+  {
+    unsigned v[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+    if (valid) {
+      P2 w[6], h[3];
+      float scale;
+      in.load_p_raw(soff + sm.nb[L][tx], w, &scale);
+      f = sm.neg[L][tx] ? -scale : scale;
+      project_p<MU>(w, sg, h);
+      // column 2 ty + spin; k = Re of colours 0..2, then Im of colours 0..2
+      v[0][0] = pack_h2(h[0].re.x, h[1].re.x);
+      v[0][1] = pack_h2(h[2].re.x, h[0].im.x);
+      v[0][2] = pack_h2(h[1].im.x, h[2].im.x);
+      v[1][0] = pack_h2(h[0].re.y, h[1].re.y);
+      v[1][1] = pack_h2(h[2].re.y, h[0].im.y);
+      v[1][2] = pack_h2(h[1].im.y, h[2].im.y);
+    }
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+      *reinterpret_cast<uint4*>(&Hs[tx][2 * ty + sp][0]) = make_uint4(v[sp][0], v[sp][1], v[sp][2], v[sp][3]);
+  }
+  __syncthreads();
+  {
+    const int lane = tx, gq = lane >> 2, tq = lane & 3;
+    for (int j = ty; j < 96; j += 12) {  // (site, n-tile) jobs spread over the 12 warps
+      const int site = j / 3, tile = j - 3 * site;
+      unsigned a0 = 0u;
+      if (gq < 6 && tq < 3) {
+        Cx<float> u[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float4 e = sm.U[L][k][site];
+          u[2 * k] = {e.x, e.y};
+          u[2 * k + 1] = {e.z, e.w};
+        }
+        reconstruct_row2(u);
+        a0 = pack_h2(real_form(u, gq, 2 * tq), real_form(u, gq, 2 * tq + 1));
+      }
+      const unsigned b0 = Hs[site][8 * tile + gq][tq];
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+          "{%0,%1,%2,%3};"
+          : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+          : "r"(a0), "r"(0u), "r"(0u), "r"(0u), "r"(b0), "r"(0u));
+      if (gq < 6) *reinterpret_cast<float2*>(&Ds[site][gq][8 * tile + 2 * tq]) = make_float2(d0, d1);
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  {
+    P2 g[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      g[a].re = *reinterpret_cast<const float2*>(&Ds[tx][a][2 * ty]);
+      g[a].im = *reinterpret_cast<const float2*>(&Ds[tx][3 + a][2 * ty]);
+    }
+    reconstruct_p<MU>(g, sg, f, acc);
+  }
+  hop_link_smp<P, RECON, 7>(A, sm, tx, sg, in, soff, acc);
+  const long site = soff + cb;
+  const float2 a2 = bc2((float)A.a);
+  P2 o[6];
+  if (A.xpay) {
+    A.x.offset_rhs(r).load_p(site, o);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) o[q] = {fma2(a2, acc[q].re, o[q].re), fma2(a2, acc[q].im, o[q].im)};
+  } else {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) o[q] = {__fmul2_rn(a2, acc[q].re), __fmul2_rn(a2, acc[q].im)};
+  }
+  A.out.offset_rhs(r).store_p(site, o);
+}
+
 template <int P, int RECON, int BY, int RED, int L12>
 __global__ void __launch_bounds__(32 * BY) k_hop_smp(HopArgs<P, RECON> A) {
   pdl_enter();
@@ -618,6 +747,19 @@ void launch_pk(HopLaunch<P, RECON>* L, int block) {
   }
 }
 
+template <int P, int RECON>
+void launch_tc(HopLaunch<P, RECON>* L) {
+  if constexpr (P == P16 && RECON == 12) {
+    HopArgs<P, RECON> A = L->args;
+    if (A.nslices != 12) raise(QCD_ERR_UNSUPPORTED, "the tensor-core prototype takes 12 slices");
+    A.ntiles = 1;
+    A.d_ntiles = make_fastdiv(1u);
+    launch_k(k_hop_tc<P, RECON>, (unsigned)((A.g.Vh + 31) / 32), dim3(32, 12), 0, L->st, A);
+  } else {
+    raise(QCD_ERR_UNSUPPORTED, "the tensor-core prototype is the FP16, 12-real stencil");
+  }
+}
+
 template <int P, int RECON, int BY, int TS, int RED = 0, int OCC = 0>
 void launch_sm(HopLaunch<P, RECON>* L) {
   HopArgs<P, RECON> A = L->args;
@@ -652,7 +794,8 @@ void launch_smp(HopLaunch<P, RECON>* L) {
 // 64 registers per thread (32 resident warps per SM); -tile = 500 + 10 * BY + 1:
 // packed FP32x2 arithmetic, one slice per thread (k_hop_smp); 600 + ...: the
 // same with the registers bounded for 24 resident warps; 700 + ...: that with
-// the links staged as two rows
+// the links staged as two rows; -3121: 12 slices, one direction by tensor-core MMA
+// (k_hop_tc; FP16, 12-real)
 template <int P, int RECON>
 void run_cfg(void* ctx, const LaunchCfg& cfg) {
   auto* L = (HopLaunch<P, RECON>*)ctx;
@@ -694,6 +837,7 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case -681: launch_smp<P, RECON, 8, 0, 1>(L); break;
       case -741: launch_smp<P, RECON, 4, 0, 1, RECON == 12>(L); break;  // 18-real: the -641 kernel
       case -781: launch_smp<P, RECON, 8, 0, 1, RECON == 12>(L); break;
+      case -3121: launch_tc<P, RECON>(L); break;
       default: launch_sm<P, RECON, 8, 2>(L); break;
     }
   }
@@ -757,6 +901,7 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64 && A.nslices >= 8)
     for (int t : {-581, -681, -781})
       if (t != -781 || RECON == 12) cands.push_back({256, t});
+  if (P == P16 && RECON == 12 && A.nslices == 12) cands.push_back({384, -3121});  // tensor-core direction
   if (A.red) {  // the fused reduction exists for one slice per thread only
     cands.clear();
     for (int b : blocks) cands.push_back({b, 1});

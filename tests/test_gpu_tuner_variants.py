@@ -1,7 +1,8 @@
 """Every launch shape the stencil autotuner can choose computes the same operator.
 
 Each candidate (register tiles of 1 / 2 / 4 slices, the L1-prefetching single-slice
-kernels, the packed single-slice kernels, the shared-memory link kernels with scalar and packed FP32x2 arithmetic, the
+kernels, the packed single-slice kernels, the 12-rhs FP16 stencil with one direction on the
+tensor cores, the shared-memory link kernels with scalar and packed FP32x2 arithmetic, the
 fused-reduction stencils of the BiCGStab iteration with and without prefetches, and the
 domain-wall stencil with the fifth-dimension inverse in its epilogue) is forced through a tuning-cache
 file (QCD_TUNECACHE) in a child process, on a lattice of its own so that every
@@ -119,6 +120,12 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
             cases.append({"kind": "hop", "L": L, "prec": prec, "recon": recon, "nrhs": 1})
             lines.append(f"{_key(L, prec, recon, 1, 0, 0)}\t{block}\t{tile}")
             tol.append(1e-6 if prec == "f32" else 2e-3)
+    # the 12-rhs FP16 stencil with one direction on the tensor cores (a ragged last site block too)
+    for L in ((4, 4, 4, t), (6, 2, 4, t + 2)):
+        cases.append({"kind": "hop", "L": L, "prec": "f16", "recon": 12, "nrhs": 12})
+        lines.append(f"{_key(L, 'f16', 12, 12, 0, 0)}\t384\t-3121")
+        tol.append(2e-3)
+    t += 4
     # the fused-reduction stencils of the FP32 BiCGStab iteration, plain and with prefetches
     for tile, block in ((1, 64), (101, 128), (201, 64)):
         L = (8, 8, 8, t)
