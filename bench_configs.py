@@ -96,8 +96,9 @@ def run_dwf(args):
         a_ = torch.empty(nb, dtype=torch.uint8, device=dev)
         o_ = torch.empty(nb, dtype=torch.uint8, device=dev)
         qcd.field_pack(g, f, prec, 1, bd, a_)
-        if args.profile == "cg":  # ncu: one warmed-up CG solve (FP32 inner, double-float outer steps)
-            kw = dict(method=qcd.CG_NORMAL, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32, outer="df64")
+        if args.profile == "cg":  # ncu: one warmed-up CG solve (FP32 inner, IEEE-FP64 outer steps)
+            kw = dict(method=qcd.CG_NORMAL, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32,
+                      delta=(args.delta or 0.0), outer=args.outer)
             x = torch.zeros_like(bd)
             qcd.solve(g, f, bd, x, **kw)
             x.zero_()
@@ -146,11 +147,13 @@ def run_dwf(args):
     hop["f32"]["fused_5d_speedup"] = round(hop["f32"]["repeated_4d_ms"] / hop["f32"]["hop_ms"], 3)
     del a1, o1
     res = {}
-    # inner precision / outer precision of the mixed solves; "f64" is the plain FP64 CG
+    # inner precision / outer precision of the mixed solves; "f64" is the plain FP64 CG.  The
+    # reliable-update factor is the one measured fastest per inner precision (FP32: 1e-4, three
+    # outer steps; FP16: the library's 0.01) unless --delta is given
     for name, inner, outer in (("f16", "f16", "f64"), ("f32", "f32", "f64"), ("f16_df", "f16", "df64"),
                                ("f32_df", "f32", "df64"), ("f64", "f64", "f64")):
         kw = dict(method=qcd.CG_NORMAL, tol=1e-10, inner=inner, use_graph=True, graph_chunk=32,
-                  delta=(args.delta or 0.0), outer=outer)
+                  delta=(args.delta or (1e-4 if inner == "f32" else 0.0)), outer=outer)
         x = torch.zeros_like(bd)
         qcd.solve(g, f, bd, x, **kw)  # warm-up (tuning, workspace)
         x.zero_()
@@ -246,13 +249,27 @@ def run_batched(args):
     qcd.field_pack(g, f, "f32", 1, bd, a12, nrhs=12)
     ms12 = _time_launches(lambda: qcd.dslash(g, f, "D_EO", a12, o12, prec="f32", nrhs=12, layout=qcd.INTERNAL))
     if args.profile not in ("none", "cg"):  # ncu: profile 3 launches of the 12-rhs hop (tuned above)
+        pp = args.profile_prec if args.profile_prec in ("f32", "f16") else "f32"
+        if pp != "f32":
+            a12 = torch.empty(qcd.field_bytes(g, f, pp, 12), dtype=torch.uint8, device=dev)
+            o12 = torch.empty_like(a12)
+            qcd.field_pack(g, f, pp, 1, bd, a12, nrhs=12)
+            _time_launches(lambda: qcd.dslash(g, f, "D_EO", a12, o12, prec=pp, nrhs=12, layout=qcd.INTERNAL))
         torch.cuda.profiler.start()
         for _ in range(3):
-            qcd.dslash(g, f, "D_EO", a12, o12, prec="f32", nrhs=12, layout=qcd.INTERNAL)
+            qcd.dslash(g, f, "D_EO", a12, o12, prec=pp, nrhs=12, layout=qcd.INTERNAL)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
-        print("profile batched hop done", flush=True)
+        print(f"profile batched hop ({pp}) done", flush=True)
         return
+    # the 12-rhs stencil in FP16 (the tuner's choice among its launch shapes, which include
+    # one direction on the tensor cores)
+    nb16 = qcd.field_bytes(g, f, "f16", 12)
+    a16 = torch.empty(nb16, dtype=torch.uint8, device=dev)
+    o16 = torch.empty(nb16, dtype=torch.uint8, device=dev)
+    qcd.field_pack(g, f, "f16", 1, bd, a16, nrhs=12)
+    ms16 = _time_launches(lambda: qcd.dslash(g, f, "D_EO", a16, o16, prec="f16", nrhs=12, layout=qcd.INTERNAL))
+    del a16, o16
     nb1 = qcd.field_bytes(g, f, "f32", 1)
     ms1 = _time_launches(lambda: qcd.dslash(g, f, "D_EO", a12[:nb1], o12[:nb1], prec="f32",
                                             layout=qcd.INTERNAL))
@@ -304,7 +321,7 @@ def run_batched(args):
            "cpu_baseline": cpu,
            "dslash12_ms": round(ms12, 4), "dslash12_gflops": round(metrics.HOP_FLOP_SITE * Vh * 12 / ms12 / 1e6, 1),
            "dslash12_gbs": round(alg12 / ms12 / 1e6, 1), "dslash12_frac": round(alg12 / ms12 / 1e6 / _peak(), 4),
-           "dslash1_x12_ms": round(12 * ms1, 4),
+           "dslash1_x12_ms": round(12 * ms1, 4), "dslash12_f16_ms": round(ms16, 4),
            "solve12_s": round(t_batch, 4), "solve_12x1_s": round(t_seq, 4),
            "speedup_batched": round(t_seq / t_batch, 3),
            "iters": [i["iters"] for i in info], "iters_seq": iters_seq,
