@@ -142,8 +142,7 @@ typedef struct {
  *   QCD_F32 / QCD_F16: mixed precision with reliable updates -- true residual
  *   recomputed and solution accumulated in the outer precision, below).
  * delta: a reliable update is made when the iterated residual has dropped by
- *   this factor since the last one (0 < delta < 1; 0 selects 0.01 for an FP32
- *   and 0.1 for an FP16 inner solver).
+ *   this factor since the last one (0 < delta < 1; 0 selects 0.01).
  * use_graph: capture `graph_chunk` inner iterations in one CUDA graph and
  *   check convergence once per graph launch (0 = plain launches).
  * x0_given: x holds an initial guess on entry (warm start).

@@ -731,9 +731,10 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   const int ls = S.ls;
   const bool dwf = is_dw(f);
   const int dag = prm.dagger;
-  // default reliable-update factor: the FP32 recursion stays accurate over two decades,
-  // the FP16 one over one
-  const double delta = (prm.delta > 0 && prm.delta < 1) ? prm.delta : (prm.inner == QCD_F16 ? 0.1 : 0.01);
+  // default reliable-update factor: two decades between outer steps for FP32 and for FP16
+  // inner vectors (the FP16 spinors are scaled per site; measured at 32^3 x 64 Wilson and
+  // 16^3 x 32 x 16 domain-wall, 0.01 takes as many iterations as 0.1 with half the outer steps)
+  const double delta = (prm.delta > 0 && prm.delta < 1) ? prm.delta : 0.01;
 
   S.b_e = ws_field(g, "s.b_e", QCD_F64, ls, nrhs);
   S.b_o = ws_field(g, "s.b_o", QCD_F64, ls, nrhs);
