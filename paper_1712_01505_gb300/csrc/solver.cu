@@ -53,18 +53,8 @@ struct Scal {
   int active;
   int flag;
   int iters;
-  int flag_iter;  // iters when flag was raised
+  int pad;
 };
-
-// a right-hand side whose outer step is due waits at most this many iterations for
-// the others (several right-hand sides), so that steps due at about the same time
-// share one synchronisation
-constexpr int kFlagWait = 2;
-
-__device__ __forceinline__ void raise_flag(Scal& s, int fl) {
-  if (s.flag == FLAG_NONE) s.flag_iter = s.iters;
-  s.flag = fl;
-}
 
 constexpr int kThreads = 256;
 constexpr int kMaxPartial = 4;
@@ -322,8 +312,10 @@ __global__ void k_bicg_xr(AnyView x_, AnyView p_, AnyView s_, AnyView t_, AnyVie
 }
 
 // end of an iteration: rho_new, |r|^2, iteration count, stop decisions
-// and the next beta; with decide != 0 (one right-hand side) any flag stops the chunk
-// at once, otherwise k_decide weighs the flags of all right-hand sides
+// and the next beta; with decide != 0 any flag stops the chunk at once (the outer
+// step is then made for the right-hand sides that have flagged; waiting for others
+// to flag too was measured to cost iterations: 12 point sources at 24^3 x 48 ran
+// 49-53 iterations with a two-iteration wait, 46-49 without)
 __global__ void k_bicg_check(Scal* sc, const double* partial, int nblk, int* ctl, int decide) {
   pdl_enter();
   if (STOPPED(ctl)) return;
@@ -338,11 +330,11 @@ __global__ void k_bicg_check(Scal* sc, const double* partial, int nblk, int* ctl
   s.rho_new[1] = d[1];
   s.r2 = d[2];
   if (bad(d[0]) || bad(d[1]) || bad(d[2])) {
-    raise_flag(s, FLAG_NAN);
+    s.flag = FLAG_NAN;
   } else if (d[2] <= s.stop2) {
-    raise_flag(s, FLAG_CHECK);
+    s.flag = FLAG_CHECK;
   } else if (s.delta2 > 0.0 && d[2] <= s.delta2 * s.r2_ref) {
-    raise_flag(s, FLAG_UPDATE);
+    s.flag = FLAG_UPDATE;
   }
   const double2 b = cmul2(cdiv(make_double2(d[0], d[1]), make_double2(s.rho[0], s.rho[1])),
                           cdiv(make_double2(s.alpha[0], s.alpha[1]), make_double2(s.omega[0], s.omega[1])));
@@ -455,11 +447,11 @@ __global__ void k_cg_check(Scal* sc, const double* partial, int nblk, int* ctl, 
   s.rr_new = d[0];
   s.r2 = d[0];
   if (bad(d[0]))
-    raise_flag(s, FLAG_NAN);
+    s.flag = FLAG_NAN;
   else if (d[0] <= s.stop2)
-    raise_flag(s, FLAG_CHECK);
+    s.flag = FLAG_CHECK;
   else if (s.delta2 > 0.0 && d[0] <= s.delta2 * s.r2_ref)
-    raise_flag(s, FLAG_UPDATE);
+    s.flag = FLAG_UPDATE;
   s.beta[0] = d[0] / s.rr;
   s.beta[1] = 0.0;
   if (decide && s.flag != FLAG_NONE) *ctl = 1;
@@ -486,26 +478,6 @@ __global__ void k_rdot(AnyView a_, AnyView b_, long n, double* partial, const Sc
 }
 
 __global__ void k_reset(int* ctl) { *ctl = 0; }
-
-// End-of-iteration stop decision over all right-hand sides (<<<1, 32>>>).  The
-// outer step is made for the right-hand sides that have flagged (outer step due,
-// target reached) only; a flagged one keeps iterating for up to kFlagWait
-// iterations while others may flag too, so that their steps share one host
-// synchronisation (breakdown / NaN stop at once).
-__global__ void k_decide(const Scal* sc, int nrhs, int* ctl) {
-  pdl_enter();
-  if (STOPPED(ctl) || threadIdx.x) return;
-  int nact = 0, nflag = 0, urgent = 0;
-  for (int r = 0; r < nrhs; ++r) {
-    const Scal& s = sc[r];
-    if (!s.active) continue;
-    ++nact;
-    if (s.flag == FLAG_NONE) continue;
-    ++nflag;
-    if (s.flag == FLAG_NAN || s.flag == FLAG_BREAKDOWN || s.iters - s.flag_iter >= kFlagWait) ++urgent;
-  }
-  if (nflag > 0 && (nflag == nact || urgent > 0)) *ctl = 1;
-}
 
 unsigned red_blocks(long n) {
   long b = (n + kThreads - 1) / kThreads;
@@ -599,12 +571,8 @@ struct Solver {
                                                   fused_multi() ? 1 : (int)nblk, fused() ? ctl + 2 : nullptr,
                                                   partial2, sc, ctl);
       QCD_LAUNCH_CK();
-      launch_k(k_bicg_check, nrhs, kThreads, 0, st, sc, partial2, nblk, ctl, nrhs == 1);
+      launch_k(k_bicg_check, nrhs, kThreads, 0, st, sc, partial2, nblk, ctl, 1);
       QCD_LAUNCH_CK();
-      if (nrhs > 1) {
-        launch_k(k_decide, 1, 32, 0, st, sc, nrhs, ctl);
-        QCD_LAUNCH_CK();
-      }
     } else {
       launch_k(k_cg_p<R>, grid, kThreads, 0, st, any_view(r), any_view(p), nn, sc, ctl);
       QCD_LAUNCH_CK();
@@ -627,12 +595,8 @@ struct Solver {
       launch_k(k_cg_xr<R, RX>, grid, kThreads, 0, st, any_view(xin), any_view(p), any_view(q), any_view(r),
                                                 nn, partial, nb, nb_dev, partial2, sc, ctl);
       QCD_LAUNCH_CK();
-      launch_k(k_cg_check, nrhs, kThreads, 0, st, sc, partial2, nblk, ctl, nrhs == 1);
+      launch_k(k_cg_check, nrhs, kThreads, 0, st, sc, partial2, nblk, ctl, 1);
       QCD_LAUNCH_CK();
-      if (nrhs > 1) {
-        launch_k(k_decide, 1, 32, 0, st, sc, nrhs, ctl);
-        QCD_LAUNCH_CK();
-      }
     }
   }
 
