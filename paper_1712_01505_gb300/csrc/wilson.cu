@@ -856,8 +856,11 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   A.npartial = nullptr;
   const bool multi_red = red && red->mode && in.nrhs * in.ls > 1;
   if (red && red->mode) {
-    if (P == P16 || !x || (red->mode == 1 && !red->rt) || (multi_red && P != P32))
-      raise(QCD_ERR_ARG, "fused reductions need FP32 (or, for one right-hand side, FP64) fields and an x term");
+    // several slices: FP32 or FP16 (the sums use the computed output, which the FP16 store
+    // then rounds: a relative difference of order 1e-3 / sqrt(sites) in the sum); one: FP32 / FP64
+    if (!x || (red->mode == 1 && !red->rt) || (multi_red ? P == P64 : P == P16))
+      raise(QCD_ERR_ARG, "fused reductions need FP32 / FP16 fields (several slices) or FP32 / FP64 fields (one), "
+                         "and an x term");
     A.red = red->mode;
     A.partial = red->partial;
     A.gpartial = red->gpartial;

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 BC = (1, 1, 1, -1)
 GRIDS = [((4, 4, 4, 8), (1, 1, 1, 2)), ((8, 4, 4, 8), (2, 1, 1, 2)), ((4, 4, 4, 4), (2, 2, 2, 2)),
-         ((8, 8, 4, 4), (4, 2, 1, 1))]
+         ((8, 8, 4, 4), (4, 2, 1, 1)), ((4, 4, 4, 8), (1, 1, 1, 1))]  # the last: no cut at all
 
 
 def _setup(L, P, seed, recon=18):
@@ -117,4 +117,16 @@ def test_argument_checks():
     with pytest.raises(qcd.QCDError, match="NCCL"):
         D.dslash(qcd.wilson(0.12), "D_EO", [psi], [out])
     torch.cuda.synchronize()
+    D.free()
+
+
+def test_zero_source_gives_zero_solution():
+    device()
+    L, P = (4, 4, 4, 8), (1, 1, 1, 2)
+    _, ids, D = _setup(L, P, 39)
+    bl = [torch.zeros((int(np.prod(L)) // 2, 4, 3), dtype=torch.complex128, device=device()) for _ in ids]
+    xl = [torch.full_like(t, 1.0) for t in bl]
+    info, st = D.solve(qcd.wilson(0.12), bl, xl, tol=1e-10, inner="f32")
+    assert st == qcd.OK and info["converged"] and info["true_resid"] == 0.0
+    assert all(float(t.abs().max()) == 0.0 for t in xl)
     D.free()

@@ -68,8 +68,8 @@ for case in json.loads(sys.argv[1]):
         f = qcd.dwf(Ls, 1.8, 0.02)
         b = inputs.gaussian_source((Ls, V, 4, 3), 1)
         x = torch.zeros((Ls, V, 4, 3), dtype=torch.complex128, device="cuda")
-        qcd.solve(g, f, torch.from_numpy(b).cuda(), x, method=qcd.CG_NORMAL, tol=1e-10, inner="f32",
-                  use_graph=True, graph_chunk=8)
+        qcd.solve(g, f, torch.from_numpy(b).cuda(), x, method=qcd.CG_NORMAL, tol=1e-10,
+                  inner=case.get("inner", "f32"), use_graph=True, graph_chunk=8)
         xr = x.cpu().numpy()
         res.append(float(np.linalg.norm(b - ora.dw(L, BC, Ls, 1.8, 0.02, U, xr)) / np.linalg.norm(b)))
     else:
@@ -149,6 +149,13 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
         t += 2
         cases.append({"kind": "dwsolve", "L": L, "recon": 12, "Ls": 8})
         lines.append(f"{_key(L, 'f32', 12, 8, 1, 1)}\t{block}\t{tile}")
+        tol.append(1e-10)
+    # the same with FP16 inner vectors
+    for tile, block in ((-41, 128), (-641, 128), (-581, 256)):
+        L = (4, 4, 2, t)
+        t += 2
+        cases.append({"kind": "dwsolve", "L": L, "recon": 12, "Ls": 8, "inner": "f16"})
+        lines.append(f"{_key(L, 'f16', 12, 8, 1, 1)}\t{block}\t{tile}")
         tol.append(1e-10)
     # the domain-wall stencil with W in its epilogue: thread rows 4 / 8 / 16, plain or packed
     # arithmetic, Shamir and Mobius, FP32 and FP16, both adjoints of Mhat
