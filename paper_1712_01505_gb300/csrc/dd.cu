@@ -365,6 +365,7 @@ struct qcd_dd {
   void* nccl_comm = nullptr;   // set when the subdomains of other processes are reached by NCCL
   int rank = 0, nranks = 1;
   double* red_dev = nullptr;   // all-reduce staging (NCCL)
+  double* red_host = nullptr;  // pinned host copy of the subdomains' reduction partials
   int device = 0;
 };
 
@@ -633,7 +634,9 @@ void allreduce(qcd_dd* d, double* v, int n, cudaStream_t st) {
 
 // global (x, y) and |x|^2
 void dot(qcd_dd* d, const Vec& x, const Vec& y, std::complex<double>* xy, double* xx, cudaStream_t st) {
+  // every subdomain's partials to the pinned host buffer, one synchronisation
   std::vector<unsigned> nbs;
+  size_t off = 0;
   for (size_t k = 0; k < x.size(); ++k) {
     const long n = x[k].nsites();
     const unsigned nb = blocks_for(n);
@@ -643,14 +646,17 @@ void dot(qcd_dd* d, const Vec& x, const Vec& y, std::complex<double>* xy, double
     else
       k_dd_dot<float><<<nb, kThreads, 0, st>>>(any_view(x[k]), any_view(y[k]), n, d->subs[k].partial);
     QCD_LAUNCH_CK();
+    QCD_CK(cudaMemcpyAsync(d->red_host + off, d->subs[k].partial, sizeof(double) * nb * 4, cudaMemcpyDeviceToHost,
+                           st));
+    off += (size_t)nb * 4;
   }
+  QCD_CK(cudaStreamSynchronize(st));
   double v[3] = {0.0, 0.0, 0.0};
+  off = 0;
   for (size_t k = 0; k < x.size(); ++k) {
-    std::vector<double> h((size_t)nbs[k] * 4);
-    QCD_CK(cudaMemcpyAsync(h.data(), d->subs[k].partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
-    QCD_CK(cudaStreamSynchronize(st));
     for (unsigned b = 0; b < nbs[k]; ++b)
-      for (int j = 0; j < 3; ++j) v[j] += h[(size_t)b * 4 + j];
+      for (int j = 0; j < 3; ++j) v[j] += d->red_host[off + (size_t)b * 4 + j];
+    off += (size_t)nbs[k] * 4;
   }
   allreduce(d, v, 3, st);
   if (xy) *xy = std::complex<double>(v[0], v[1]);
@@ -749,6 +755,9 @@ void dd_create(const qcd_dd_geom* geom, int nlocal, const int32_t* ids, const vo
           QCD_CK(cudaMemcpyAsync(sb.bsites[par], list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, st));
       }
     }
+    size_t npart = 0;
+    for (auto& sb : d->subs) npart += (size_t)4 * blocks_for(sb.g->lat.Vh);
+    QCD_CK(cudaMallocHost((void**)&d->red_host, sizeof(double) * npart));
     QCD_CK(cudaStreamSynchronize(st));
   } catch (...) {
     dd_free(d);
@@ -764,6 +773,7 @@ void dd_free(qcd_dd* d) {
     if (s.g) qcd_gauge_free(s.g);
   if (d->nccl_comm) nccl().comm_destroy(d->nccl_comm);
   if (d->red_dev) cudaFree(d->red_dev);
+  if (d->red_host) cudaFreeHost(d->red_host);
   if (d->comm) cudaStreamDestroy(d->comm);
   if (d->ev_pack) cudaEventDestroy(d->ev_pack);
   if (d->ev_comm) cudaEventDestroy(d->ev_comm);
@@ -887,7 +897,7 @@ void dd_solve(qcd_dd* d, const qcd_fermion& f, const qcd_solver_params& prm, con
     status = QCD_ERR_NAN;
     conv = true;
   }
-  std::complex<double> rho(1.0), alpha(1.0), omega(1.0);
+  std::complex<double> rho(1.0), alpha(1.0), omega(1.0), rho_next(0.0);  // rho_next = (rt, r) of the current r
   double r2 = 0.0, r2_ref = 0.0, stop2 = 0.0;
   auto restart = [&](bool full) {
     vcopy(r64, r, st);
@@ -898,7 +908,9 @@ void dd_solve(qcd_dd* d, const qcd_fermion& f, const qcd_solver_params& prm, con
       vzero(v, st);
       rho = alpha = omega = 1.0;
     }
-    r2 = norm2(d, r, st);
+    std::complex<double> c;
+    dot(d, r, rt, &c, &r2, st);  // (r, rt) = conj((rt, r)) and |r|^2 together
+    rho_next = std::conj(c);
     r2_ref = r2;
     const double ratio = rfull > 0 ? std::sqrt(r2) / rfull : 1.0;
     const double tg = 0.5 * target * ratio;
@@ -910,9 +922,8 @@ void dd_solve(qcd_dd* d, const qcd_fermion& f, const qcd_solver_params& prm, con
       status = QCD_ERR_NOCONV;
       break;
     }
-    std::complex<double> rho_new, rtv, ts;
+    std::complex<double> rho_new = rho_next, rtv, ts;
     double tt;
-    dot(d, rt, r, &rho_new, nullptr, st);
     bool breakdown = std::abs(rho_new) < 1e-300;
     if (!breakdown) {
       const std::complex<double> beta = (rho_new / rho) * (alpha / omega);
@@ -931,7 +942,9 @@ void dd_solve(qcd_dd* d, const qcd_fermion& f, const qcd_solver_params& prm, con
           lin3(alpha, p, omega, s, 1.0, xin, st);  // x += alpha p + omega s
           lin3(1.0, s, -omega, t, 0.0, r, st);    // r = s - omega t
           rho = rho_new;
-          r2 = norm2(d, r, st);
+          std::complex<double> c;
+          dot(d, r, rt, &c, &r2, st);  // |r|^2 and the next iteration's (rt, r)
+          rho_next = std::conj(c);
           ++iters;
         }
       }
