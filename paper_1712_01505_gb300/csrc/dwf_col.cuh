@@ -92,6 +92,67 @@ __device__ __forceinline__ void col_inv(R* re, R* im, int cs, const ColCoef<R>& 
   }
 }
 
+// The same with the column held in registers (Ls <= NR): one read and one write of
+// the column instead of two reads and a write (the fused stencil's shared-memory tile)
+template <int NR, typename R>
+__device__ __forceinline__ void col_inv_reg(R* re, R* im, int cs, const ColCoef<R>& c, bool lower) {
+  const int Ls = c.Ls;
+  R vr[NR], vi[NR];
+#pragma unroll
+  for (int s = 0; s < NR; ++s)
+    if (s < Ls) {
+      vr[s] = re[s * cs];
+      vi[s] = im[s * cs];
+    }
+  if (lower) {
+    R pr = c.apow[0] * vr[0], pi = c.apow[0] * vi[0];
+#pragma unroll
+    for (int sp = 1; sp < NR; ++sp)
+      if (sp < Ls) {
+        const R w = -c.mf * c.apow[Ls - sp];
+        pr = fma(w, vr[sp], pr);
+        pi = fma(w, vi[sp], pi);
+      }
+    re[0] = pr;
+    im[0] = pi;
+#pragma unroll
+    for (int s = 1; s < NR; ++s)
+      if (s < Ls) {
+        pr = fma(c.ratio, pr, c.ainv * vr[s]);
+        pi = fma(c.ratio, pi, c.ainv * vi[s]);
+        re[s * cs] = pr;
+        im[s * cs] = pi;
+      }
+  } else {
+    const int l = Ls - 1;
+    R pr = 0, pi = 0;
+#pragma unroll
+    for (int sp = 0; sp < NR; ++sp)
+      if (sp == l) {
+        pr = c.apow[0] * vr[sp];
+        pi = c.apow[0] * vi[sp];
+      }
+#pragma unroll
+    for (int sp = 0; sp < NR; ++sp)
+      if (sp < l) {
+        const R w = -c.mf * c.apow[sp + 1];
+        pr = fma(w, vr[sp], pr);
+        pi = fma(w, vi[sp], pi);
+      }
+    // psi_l, then psi_s = chi_s / alpha + (beta / alpha) psi_{s+1} downwards
+#pragma unroll
+    for (int s = NR - 1; s >= 0; --s) {
+      if (s > l) continue;
+      if (s < l) {
+        pr = fma(c.ratio, pr, c.ainv * vr[s]);
+        pi = fma(c.ratio, pi, c.ainv * vi[s]);
+      }
+      re[s * cs] = pr;
+      im[s * cs] = pi;
+    }
+  }
+}
+
 // host description of a column operator
 struct ColSpec {
   int flags = 0;
@@ -132,13 +193,19 @@ inline ColSpec w_spec(const DwParams& p) {
   return cs;
 }
 
-// the passes of a column operator (dagger: post^T, inv^T, pre^T) on one complex column
-template <typename R>
+// the passes of a column operator (dagger: post^T, inv^T, pre^T) on one complex column;
+// NR > 0: the inverse with the column in registers (needs Ls <= NR)
+template <typename R, int NR = 0>
 __device__ __forceinline__ void col_apply(R* re, R* im, int cs, const ColCoef<R>& c, bool lower, int dagger) {
   const bool first = dagger ? (c.flags & kPost) : (c.flags & kPre);
   const bool last = dagger ? (c.flags & kPre) : (c.flags & kPost);
   if (first) col_mul(re, im, cs, c.Ls, lower, dagger ? c.post_d : c.pre_d, dagger ? c.post_e : c.pre_e, c.mf);
-  if (c.flags & kInv) col_inv(re, im, cs, c, lower);
+  if (c.flags & kInv) {
+    if constexpr (NR > 0)
+      col_inv_reg<NR>(re, im, cs, c, lower);
+    else
+      col_inv(re, im, cs, c, lower);
+  }
   if (last) col_mul(re, im, cs, c.Ls, lower, dagger ? c.pre_d : c.post_d, dagger ? c.pre_e : c.post_e, c.mf);
 }
 

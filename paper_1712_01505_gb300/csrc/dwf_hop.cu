@@ -109,7 +109,11 @@ __global__ void __launch_bounds__(32 * BY) k_dw_hop_w(HopArgs<P, RECON> A, ColCo
   }
   __syncthreads();
   for (int k = ty; k < 12; k += BY)
-    col_apply(tile + (2 * k) * 32 + tx, tile + (2 * k + 1) * 32 + tx, cs, c, (k < 6) != (A.dagger != 0), A.dagger);
+    if (Ls <= 16)  // the column of the inverse in registers
+      col_apply<R, 16>(tile + (2 * k) * 32 + tx, tile + (2 * k + 1) * 32 + tx, cs, c, (k < 6) != (A.dagger != 0),
+                       A.dagger);
+    else
+      col_apply(tile + (2 * k) * 32 + tx, tile + (2 * k + 1) * 32 + tx, cs, c, (k < 6) != (A.dagger != 0), A.dagger);
   __syncthreads();
   if (!valid) return;
   const R a = (R)A.a;
