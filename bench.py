@@ -230,7 +230,8 @@ def main():
                          "between cudaProfilerStart/Stop (use ncu --profile-from-start off); no JSON line")
     ap.add_argument("--profile-prec", default="f32", choices=["f32", "f64", "df64", "f16"],
                     help="precision of the D_eo launches of --profile dslash (and of the domain-wall hop / "
-                         "Mhat of --workload dwf --profile dslash / mhat)")
+                         "Mhat of --workload dwf --profile dslash / mhat); f16 with --profile step: the "
+                         "step's solve runs FP16 inner iterations")
     ap.add_argument("--workload", default="wilson32", choices=["wilson32", "dwf", "batched", "force", "dd"],
                     help="wilson32 (default, the bench line); the others characterise the other "
                          "configurations (domain-wall CG, 12-rhs propagator, force) and print their own line")
@@ -286,6 +287,8 @@ def main():
     delta = 1e-5 if args.delta is None else args.delta
     solve_kw = dict(method=qcd.BICGSTAB, tol=TOL, inner="f32", use_graph=True, graph_chunk=32, delta=delta,
                     outer=args.outer)
+    if args.profile == "step" and args.profile_prec == "f16":  # the FP16-inner solve of the f16_inner line
+        solve_kw = dict(solve_kw, inner="f16", delta=0.0)
 
     ev_d0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_d1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]

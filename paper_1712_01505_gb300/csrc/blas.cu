@@ -2,6 +2,7 @@
 // functions", Sec. V C): zero, precision-converting copy, axpby, and norms
 // with the global sum in FP64.  The solver's fused, device-scalar variants
 // live in solver.cu.
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -28,14 +29,17 @@ unsigned grid_for(long n) {
   return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
+// The storage precisions PX, PY of the operands are template arguments (the host
+// dispatches on the fields' precisions), so a kernel holds only its own formats'
+// code and registers.
 // grid: (blocks, nrhs); grid-stride over the sites of one right-hand side
-template <typename R>
+template <typename R, int PX, int PY>
 __global__ void k_axpby(R a, AnyView x, R b, AnyView y, long n) {
   int r = blockIdx.y;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vx[12], vy[12];
-    if (a != R(0)) any_load<R>(x, r, i, vx);
-    if (b != R(0)) any_load<R>(y, r, i, vy);
+    if (a != R(0)) any_load_p<R, PX>(x, r, i, vx);
+    if (b != R(0)) any_load_p<R, PY>(y, r, i, vy);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       Cx<R> o = {R(0), R(0)};
@@ -43,29 +47,49 @@ __global__ void k_axpby(R a, AnyView x, R b, AnyView y, long n) {
       if (b != R(0)) o = {fma(b, vy[k].re, o.re), fma(b, vy[k].im, o.im)};
       vy[k] = o;
     }
-    any_store<R>(y, r, i, vy);
+    any_store_p<R, PY>(y, r, i, vy);
   }
 }
 
-template <typename R>
+template <typename R, int PX, int PY>
 __global__ void k_copy(AnyView x, AnyView y, long n) {
   int r = blockIdx.y;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> v[12];
-    any_load<R>(x, r, i, v);
-    any_store<R>(y, r, i, v);
+    any_load_p<R, PX>(x, r, i, v);
+    any_store_p<R, PY>(y, r, i, v);
   }
+}
+
+// f(PX, PY) with PX, PY the runtime precisions px, py (F64 / F32 / F16) as
+// std::integral_constant arguments
+template <typename F>
+void dispatch2(int px, int py, F&& f) {
+  auto with_y = [&](auto cx) {
+    if (py == P64)
+      f(cx, std::integral_constant<int, P64>{});
+    else if (py == P32)
+      f(cx, std::integral_constant<int, P32>{});
+    else
+      f(cx, std::integral_constant<int, P16>{});
+  };
+  if (px == P64)
+    with_y(std::integral_constant<int, P64>{});
+  else if (px == P32)
+    with_y(std::integral_constant<int, P32>{});
+  else
+    with_y(std::integral_constant<int, P16>{});
 }
 
 // per-block partial sums of |x|^2: per-site sums in R, per-thread and
 // cross-thread sums in double
-template <typename R>
+template <typename R, int PX>
 __global__ void k_norm2(AnyView x, long n, double* partial) {
   int r = blockIdx.y;
   double acc[1] = {0.0};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> v[12];
-    any_load<R>(x, r, i, v);
+    any_load_p<R, PX>(x, r, i, v);
     R s = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) s = fma(v[k].re, v[k].re, fma(v[k].im, v[k].im, s));
@@ -125,10 +149,14 @@ void blas_copy(const Field& src, Field& dst, cudaStream_t st) {
     return;
   }
   dim3 grid(grid_for(n), src.nrhs);
-  if (src.prec == QCD_F64 || dst.prec == QCD_F64)
-    k_copy<double><<<grid, kThreads, 0, st>>>(any_view(src), any_view(dst), n);
-  else
-    k_copy<float><<<grid, kThreads, 0, st>>>(any_view(src), any_view(dst), n);
+  const AnyView vs = any_view(src), vd = any_view(dst);
+  dispatch2(src.prec, dst.prec, [&](auto cx, auto cy) {
+    constexpr int PX = decltype(cx)::value, PY = decltype(cy)::value;
+    if constexpr (PX == P64 || PY == P64)
+      k_copy<double, PX, PY><<<grid, kThreads, 0, st>>>(vs, vd, n);
+    else
+      k_copy<float, PX, PY><<<grid, kThreads, 0, st>>>(vs, vd, n);
+  });
   QCD_LAUNCH_CK();
 }
 
@@ -141,10 +169,14 @@ void blas_axpby(double a, const Field& x, double b, Field& y, cudaStream_t st) {
     return;
   }
   dim3 grid(grid_for(n), x.nrhs);
-  if (x.prec == QCD_F64 || y.prec == QCD_F64)
-    k_axpby<double><<<grid, kThreads, 0, st>>>(a, any_view(x), b, any_view(y), n);
-  else
-    k_axpby<float><<<grid, kThreads, 0, st>>>((float)a, any_view(x), (float)b, any_view(y), n);
+  const AnyView vx = any_view(x), vy = any_view(y);
+  dispatch2(x.prec, y.prec, [&](auto cx, auto cy) {
+    constexpr int PX = decltype(cx)::value, PY = decltype(cy)::value;
+    if constexpr (PX == P64 || PY == P64)
+      k_axpby<double, PX, PY><<<grid, kThreads, 0, st>>>(a, vx, b, vy, n);
+    else
+      k_axpby<float, PX, PY><<<grid, kThreads, 0, st>>>((float)a, vx, (float)b, vy, n);
+  });
   QCD_LAUNCH_CK();
 }
 
@@ -161,9 +193,11 @@ void blas_norm2(const Field& x, double* out_host, cudaStream_t st, qcd_gauge* g)
     df_norm2_partials(x, partial, nb, st);
   } else {
     if (x.prec == QCD_F64)
-      k_norm2<double><<<grid, kThreads, 0, st>>>(any_view(x), n, partial);
+      k_norm2<double, P64><<<grid, kThreads, 0, st>>>(any_view(x), n, partial);
+    else if (x.prec == QCD_F32)
+      k_norm2<float, P32><<<grid, kThreads, 0, st>>>(any_view(x), n, partial);
     else
-      k_norm2<float><<<grid, kThreads, 0, st>>>(any_view(x), n, partial);
+      k_norm2<float, P16><<<grid, kThreads, 0, st>>>(any_view(x), n, partial);
     QCD_LAUNCH_CK();
   }
   std::vector<double> h((size_t)nb * x.nrhs);

@@ -93,13 +93,37 @@ __device__ __forceinline__ void write_partial(double v[NR], double* partial, int
 
 #define STOPPED(ctl) (*(ctl) != 0)
 
+// Loads and stores of the solver's vectors: PV >= 0 fixes the storage precision
+// at compile time (the iteration kernels, which the host instantiates for the
+// inner precision: only that path is compiled, so the register count is that of
+// the one format), PV < 0 reads it from the view (the generic kernels).
+template <typename R, int PV>
+__device__ __forceinline__ void vld(const AnyView& v, int r, long i, Cx<R> out[12]) {
+  if constexpr (PV < 0)
+    any_load<R>(v, r, i, out);
+  else
+    any_load_p<R, PV>(v, r, i, out);
+}
+template <typename R, int PV>
+__device__ __forceinline__ void vst(const AnyView& v, int r, long i, const Cx<R> in[12]) {
+  if constexpr (PV < 0)
+    any_store<R>(v, r, i, in);
+  else
+    any_store_p<R, PV>(v, r, i, in);
+}
+// the precision of the inner solution accumulator for inner vectors of precision PV
+template <int PV>
+__host__ __device__ constexpr int x_prec() {
+  return PV < 0 ? -1 : (PV == P64 ? P64 : P32);
+}
+
 // ----------------------------------------------------------------------------- BiCGStab kernels
 // beta = (rho_new / rho)(alpha / omega) is formed at the end of an iteration by
 // k_bicg_check (and by the host when the recursion restarts); the first vector
 // kernel of the next iteration moves rho_new into rho.
 
 // p = r + beta (p - omega v); rho = rho_new
-template <typename R>
+template <typename R, int PV = -1>
 __global__ void k_bicg_p(AnyView r_, AnyView p_, AnyView v_, long n, Scal* sc, const int* ctl) {
   pdl_enter();
   if (STOPPED(ctl)) return;
@@ -113,20 +137,20 @@ __global__ void k_bicg_p(AnyView r_, AnyView p_, AnyView v_, long n, Scal* sc, c
   }
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vr[12], vp[12], vv[12];
-    any_load<R>(r_, r, i, vr);
-    any_load<R>(p_, r, i, vp);
-    any_load<R>(v_, r, i, vv);
+    vld<R, PV>(r_, r, i, vr);
+    vld<R, PV>(p_, r, i, vp);
+    vld<R, PV>(v_, r, i, vv);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       Cx<R> w = vp[k] - cmul(om, vv[k]);
       vp[k] = vr[k] + cmul(be, w);
     }
-    any_store<R>(p_, r, i, vp);
+    vst<R, PV>(p_, r, i, vp);
   }
 }
 
 // partial sums of (a, b) = sum conj(a) b  -> [re, im]
-template <typename R>
+template <typename R, int PV = -1>
 __global__ void k_cdot(AnyView a_, AnyView b_, long n, double* partial, const Scal* sc, const int* ctl) {
   pdl_enter();
   if (ctl && STOPPED(ctl)) return;
@@ -135,8 +159,8 @@ __global__ void k_cdot(AnyView a_, AnyView b_, long n, double* partial, const Sc
   double v[2] = {0.0, 0.0};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> va[12], vb[12];
-    any_load<R>(a_, r, i, va);
-    any_load<R>(b_, r, i, vb);
+    vld<R, PV>(a_, r, i, va);
+    vld<R, PV>(b_, r, i, vb);
     Cx<R> acc = {R(0), R(0)};
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc = cjmadd(va[k], vb[k], acc);
@@ -216,7 +240,7 @@ __device__ __forceinline__ bool block_omega(Scal& s, const double* partial, int 
 }
 
 // alpha from the (rt, v) partials, then s = r - alpha v
-template <typename R>
+template <typename R, int PV = -1>
 __global__ void k_bicg_s(AnyView r_, AnyView v_, AnyView s_, long n, Scal* sc, int* ctl, const double* partial,
                          int nblk, const int* nb_dev) {
   pdl_enter();
@@ -229,16 +253,16 @@ __global__ void k_bicg_s(AnyView r_, AnyView v_, AnyView s_, long n, Scal* sc, i
   const Cx<R> al = {(R)a.x, (R)a.y};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vr[12], vv[12];
-    any_load<R>(r_, r, i, vr);
-    any_load<R>(v_, r, i, vv);
+    vld<R, PV>(r_, r, i, vr);
+    vld<R, PV>(v_, r, i, vv);
 #pragma unroll
     for (int k = 0; k < 12; ++k) vr[k] = vr[k] - cmul(al, vv[k]);
-    any_store<R>(s_, r, i, vr);
+    vst<R, PV>(s_, r, i, vr);
   }
 }
 
 // partial sums of (t, s) [re, im] and |t|^2
-template <typename R>
+template <typename R, int PV = -1>
 __global__ void k_ts_tt(AnyView t_, AnyView s_, long n, double* partial, const Scal* sc, const int* ctl) {
   pdl_enter();
   if (STOPPED(ctl)) return;
@@ -247,8 +271,8 @@ __global__ void k_ts_tt(AnyView t_, AnyView s_, long n, double* partial, const S
   double v[3] = {0.0, 0.0, 0.0};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vt[12], vs[12];
-    any_load<R>(t_, r, i, vt);
-    any_load<R>(s_, r, i, vs);
+    vld<R, PV>(t_, r, i, vt);
+    vld<R, PV>(s_, r, i, vs);
     Cx<R> acc = {R(0), R(0)};
     R tt = 0;
 #pragma unroll
@@ -265,7 +289,7 @@ __global__ void k_ts_tt(AnyView t_, AnyView s_, long n, double* partial, const S
 
 // omega from the (t, s), |t|^2 partials, then x += alpha p + omega s;  r = s - omega t;
 // partials (rt, r) and |r|^2 into partial_out (not the array omega is read from)
-template <typename R, typename RX>
+template <typename R, typename RX, int PV = -1>
 __global__ void k_bicg_xr(AnyView x_, AnyView p_, AnyView s_, AnyView t_, AnyView r_, AnyView rt_,
                           long n, const double* partial_in, int nblk, const int* nb_dev, double* partial_out,
                           Scal* sc, int* ctl) {
@@ -283,20 +307,20 @@ __global__ void k_bicg_xr(AnyView x_, AnyView p_, AnyView s_, AnyView t_, AnyVie
     // every input first: the stores below may alias nothing the compiler can prove
     Cx<R> vp[12], vs[12], vt[12], vrt[12];
     Cx<RX> vx[12];
-    any_load<RX>(x_, r, i, vx);
-    any_load<R>(p_, r, i, vp);
-    any_load<R>(s_, r, i, vs);
-    any_load<R>(t_, r, i, vt);
-    any_load<R>(rt_, r, i, vrt);
+    vld<RX, x_prec<PV>()>(x_, r, i, vx);
+    vld<R, PV>(p_, r, i, vp);
+    vld<R, PV>(s_, r, i, vs);
+    vld<R, PV>(t_, r, i, vt);
+    vld<R, PV>(rt_, r, i, vrt);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       Cx<RX> pp = {(RX)vp[k].re, (RX)vp[k].im}, ss = {(RX)vs[k].re, (RX)vs[k].im};
       vx[k] = vx[k] + cmul(alx, pp) + cmul(omx, ss);
     }
-    any_store<RX>(x_, r, i, vx);
+    vst<RX, x_prec<PV>()>(x_, r, i, vx);
 #pragma unroll
     for (int k = 0; k < 12; ++k) vs[k] = vs[k] - cmul(om, vt[k]);
-    any_store<R>(r_, r, i, vs);
+    vst<R, PV>(r_, r, i, vs);
     Cx<R> acc = {R(0), R(0)};
     R rr = 0;
 #pragma unroll
@@ -349,7 +373,7 @@ __global__ void k_bicg_check(Scal* sc, const double* partial, int nblk, int* ctl
 // iteration moves rr_new into rr.
 
 // p = r + beta p; rr = rr_new
-template <typename R>
+template <typename R, int PV = -1>
 __global__ void k_cg_p(AnyView r_, AnyView p_, long n, Scal* sc, const int* ctl) {
   pdl_enter();
   if (STOPPED(ctl)) return;
@@ -360,11 +384,11 @@ __global__ void k_cg_p(AnyView r_, AnyView p_, long n, Scal* sc, const int* ctl)
   if (blockIdx.x == 0 && threadIdx.x == 0) s.rr = s.rr_new;  // no block of this kernel reads rr
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vr[12], vp[12];
-    any_load<R>(r_, r, i, vr);
-    any_load<R>(p_, r, i, vp);
+    vld<R, PV>(r_, r, i, vr);
+    vld<R, PV>(p_, r, i, vp);
 #pragma unroll
     for (int k = 0; k < 12; ++k) vp[k] = {fma(be, vp[k].re, vr[k].re), fma(be, vp[k].im, vr[k].im)};
-    any_store<R>(p_, r, i, vp);
+    vst<R, PV>(p_, r, i, vp);
   }
 }
 
@@ -397,7 +421,7 @@ __device__ __forceinline__ bool block_cg_alpha(Scal& s, const double* partial, i
 
 // alpha from the Re(p, q) partials, then x += alpha p; r -= alpha q; partial |r|^2
 // into partial_out (not the array alpha is read from)
-template <typename R, typename RX>
+template <typename R, typename RX, int PV = -1>
 __global__ void k_cg_xr(AnyView x_, AnyView p_, AnyView q_, AnyView r_, long n, const double* partial_in,
                         int nblk, const int* nb_dev, double* partial_out, Scal* sc, int* ctl) {
   pdl_enter();
@@ -413,21 +437,21 @@ __global__ void k_cg_xr(AnyView x_, AnyView p_, AnyView q_, AnyView r_, long n, 
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vp[12], vq[12], vr[12];
     Cx<RX> vx[12];
-    any_load<RX>(x_, r, i, vx);
-    any_load<R>(p_, r, i, vp);
-    any_load<R>(q_, r, i, vq);
-    any_load<R>(r_, r, i, vr);
+    vld<RX, x_prec<PV>()>(x_, r, i, vx);
+    vld<R, PV>(p_, r, i, vp);
+    vld<R, PV>(q_, r, i, vq);
+    vld<R, PV>(r_, r, i, vr);
 #pragma unroll
     for (int k = 0; k < 12; ++k)
       vx[k] = {fma(alx, (RX)vp[k].re, vx[k].re), fma(alx, (RX)vp[k].im, vx[k].im)};
-    any_store<RX>(x_, r, i, vx);
+    vst<RX, x_prec<PV>()>(x_, r, i, vx);
     R rr = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       vr[k] = {fma(-al, vq[k].re, vr[k].re), fma(-al, vq[k].im, vr[k].im)};
       rr = fma(vr[k].re, vr[k].re, fma(vr[k].im, vr[k].im, rr));
     }
-    any_store<R>(r_, r, i, vr);
+    vst<R, PV>(r_, r, i, vr);
     v[0] += (double)rr;
   }
   write_partial<1>(v, partial_out, r);
@@ -458,7 +482,7 @@ __global__ void k_cg_check(Scal* sc, const double* partial, int nblk, int* ctl, 
 }
 
 // partial sums of Re(a, b)
-template <typename R>
+template <typename R, int PV = -1>
 __global__ void k_rdot(AnyView a_, AnyView b_, long n, double* partial, const Scal* sc, const int* ctl) {
   pdl_enter();
   if (STOPPED(ctl)) return;
@@ -467,8 +491,8 @@ __global__ void k_rdot(AnyView a_, AnyView b_, long n, double* partial, const Sc
   double v[2] = {0.0, 0.0};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> va[12], vb[12];
-    any_load<R>(a_, r, i, va);
-    any_load<R>(b_, r, i, vb);
+    vld<R, PV>(a_, r, i, va);
+    vld<R, PV>(b_, r, i, vb);
     R acc = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc = fma(va[k].re, vb[k].re, fma(va[k].im, vb[k].im, acc));
@@ -527,17 +551,20 @@ struct Solver {
     const long nn = n();
     dim3 grid(nblk, nrhs);
     const int dag = prm.dagger;
-    if (inner == QCD_F64) {
-      body_t<double, double>(grid, nn, dag);
-    } else {
-      body_t<float, float>(grid, nn, dag);
-    }
+    if (inner == QCD_F64)
+      body_t<double, double, P64>(grid, nn, dag);
+    else if (inner == QCD_F32)
+      body_t<float, float, P32>(grid, nn, dag);
+    else
+      body_t<float, float, P16>(grid, nn, dag);
   }
 
-  template <typename R, typename RX>
+  // PV: the storage precision of the inner vectors (the solution accumulator is FP64
+  // with FP64 vectors, else FP32)
+  template <typename R, typename RX, int PV>
   void body_t(dim3 grid, long nn, int dag) {
     if (bicg()) {
-      launch_k(k_bicg_p<R>, grid, kThreads, 0, st, any_view(r), any_view(p), any_view(v), nn, sc, ctl);
+      launch_k(k_bicg_p<R, PV>, grid, kThreads, 0, st, any_view(r), any_view(p), any_view(v), nn, sc, ctl);
       QCD_LAUNCH_CK();
       if (fused()) {
         // (rt, v) and (t, s), |t|^2 formed in the epilogue of the stencil that writes v / t
@@ -545,7 +572,7 @@ struct Solver {
         RedSpec red1{1, &rt, bpartial, partial, counters, npart};
         RedSpec red2{2, nullptr, bpartial, partial, counters, npart};
         apply_mhat(opin, p, v, dag, st, "in", ctl, &red1);
-        launch_k(k_bicg_s<R>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
+        launch_k(k_bicg_s<R, PV>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
                                                npart);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl, &red2);
@@ -554,22 +581,22 @@ struct Solver {
         RedSpec red1{1, &rt, bpartial, partial, nullptr, nullptr};
         RedSpec red2{2, nullptr, bpartial, partial, nullptr, nullptr};
         apply_mhat(opin, p, v, dag, st, "in", ctl, &red1);
-        launch_k(k_bicg_s<R>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, 1,
+        launch_k(k_bicg_s<R, PV>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, 1,
                                                nullptr);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl, &red2);
       } else {
         apply_mhat(opin, p, v, dag, st, "in", ctl);
-        launch_k(k_cdot<R>, grid, kThreads, 0, st, any_view(rt), any_view(v), nn, partial, sc, ctl);
+        launch_k(k_cdot<R, PV>, grid, kThreads, 0, st, any_view(rt), any_view(v), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
-        launch_k(k_bicg_s<R>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
+        launch_k(k_bicg_s<R, PV>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
                                                nullptr);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl);
-        launch_k(k_ts_tt<R>, grid, kThreads, 0, st, any_view(t), any_view(s), nn, partial, sc, ctl);
+        launch_k(k_ts_tt<R, PV>, grid, kThreads, 0, st, any_view(t), any_view(s), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
       }
-      launch_k(k_bicg_xr<R, RX>, grid, kThreads, 0, st, any_view(xin), any_view(p), any_view(s), any_view(t),
+      launch_k(k_bicg_xr<R, RX, PV>, grid, kThreads, 0, st, any_view(xin), any_view(p), any_view(s), any_view(t),
                                                   any_view(r), any_view(rt), nn, partial,
                                                   fused_multi() ? 1 : (int)nblk, fused() ? ctl + 2 : nullptr,
                                                   partial2, sc, ctl);
@@ -577,7 +604,7 @@ struct Solver {
       launch_k(k_bicg_check, nrhs, kThreads, 0, st, sc, partial2, nblk, ctl, 1);
       QCD_LAUNCH_CK();
     } else {
-      launch_k(k_cg_p<R>, grid, kThreads, 0, st, any_view(r), any_view(p), nn, sc, ctl);
+      launch_k(k_cg_p<R, PV>, grid, kThreads, 0, st, any_view(r), any_view(p), nn, sc, ctl);
       QCD_LAUNCH_CK();
       apply_mhat(opin, p, w, 0, st, "in", ctl);
       int nb = (int)nblk;
@@ -592,10 +619,10 @@ struct Solver {
           nb = ls;  // one sum per slice
       } else {
         apply_mhat(opin, w, q, 1, st, "in", ctl);
-        launch_k(k_rdot<R>, grid, kThreads, 0, st, any_view(p), any_view(q), nn, partial, sc, ctl);
+        launch_k(k_rdot<R, PV>, grid, kThreads, 0, st, any_view(p), any_view(q), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
       }
-      launch_k(k_cg_xr<R, RX>, grid, kThreads, 0, st, any_view(xin), any_view(p), any_view(q), any_view(r),
+      launch_k(k_cg_xr<R, RX, PV>, grid, kThreads, 0, st, any_view(xin), any_view(p), any_view(q), any_view(r),
                                                 nn, partial, nb, nb_dev, partial2, sc, ctl);
       QCD_LAUNCH_CK();
       launch_k(k_cg_check, nrhs, kThreads, 0, st, sc, partial2, nblk, ctl, 1);
