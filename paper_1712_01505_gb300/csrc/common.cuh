@@ -342,12 +342,20 @@ struct SpinorView<P16> {
     }
   }
   __device__ __forceinline__ void store_p(long site, const P2 w[6]) const {
+    P2 unused[6];
+    store_p_rounded<false>(site, w, unused);
+  }
+  // the same, and with ROUNDED the values a later load returns (the stored halves
+  // times the site scale) in wr
+  template <bool ROUNDED>
+  __device__ __forceinline__ void store_p_rounded(long site, const P2 w[6], P2 wr[6]) const {
     float m = 0.f;
 #pragma unroll
     for (int q = 0; q < 6; ++q)
       m = fmaxf(m, fmaxf(fmaxf(fabsf(w[q].re.x), fabsf(w[q].re.y)), fmaxf(fabsf(w[q].im.x), fabsf(w[q].im.y))));
     float inv = (m > 0.f) ? 1.0f / m : 0.f;
     norm[site] = m;
+    const float2 m2 = make_float2(m, m);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       uint4 d;
@@ -357,6 +365,8 @@ struct SpinorView<P16> {
         const P2& w2 = w[2 * k + j];
         h[2 * j] = __floats2half2_rn(w2.re.x * inv, w2.re.y * inv);
         h[2 * j + 1] = __floats2half2_rn(w2.im.x * inv, w2.im.y * inv);
+        if constexpr (ROUNDED)
+          wr[2 * k + j] = {__fmul2_rn(__half22float2(h[2 * j]), m2), __fmul2_rn(__half22float2(h[2 * j + 1]), m2)};
       }
       p[k * stride + site] = d;
     }

@@ -42,7 +42,24 @@ using namespace dwcol;
 // complex components k, k + blockDim.y, ...), then writes (site, slice) units.
 // block: (SB sites) x (256 / SB); grid: (ceil(Vh/SB), nrhs); dynamic shared
 // memory Ls * 24 * SB reals laid out [s][real][site].
-template <typename R>
+// PV >= 0: in, out and x all stored in that precision (the common case, compiled for
+// that format alone); PV < 0: the precisions read from the views
+template <typename R, int PV>
+__device__ __forceinline__ void cld(const AnyView& v, int r, long i, Cx<R> out[12]) {
+  if constexpr (PV < 0)
+    any_load<R>(v, r, i, out);
+  else
+    any_load_p<R, PV>(v, r, i, out);
+}
+template <typename R, int PV>
+__device__ __forceinline__ void cst(const AnyView& v, int r, long i, const Cx<R> in[12]) {
+  if constexpr (PV < 0)
+    any_store<R>(v, r, i, in);
+  else
+    any_store_p<R, PV>(v, r, i, in);
+}
+
+template <typename R, int PV>
 __global__ void __launch_bounds__(256) k_col(ColCoef<R> c, AnyView in, AnyView out, long Vh, int dagger, R scale,
                                              AnyView x, int has_x, const int* stop) {
   pdl_enter();
@@ -58,7 +75,7 @@ __global__ void __launch_bounds__(256) k_col(ColCoef<R> c, AnyView in, AnyView o
   for (int s = threadIdx.y; s < Ls; s += blockDim.y) {
     Cx<R> v[12];
     if (cb < Vh) {
-      any_load<R>(in, r, (long)s * Vh + cb, v);
+      cld<R, PV>(in, r, (long)s * Vh + cb, v);
     } else {
 #pragma unroll
       for (int k = 0; k < 12; ++k) v[k] = {R(0), R(0)};
@@ -83,14 +100,14 @@ __global__ void __launch_bounds__(256) k_col(ColCoef<R> c, AnyView in, AnyView o
     for (int k = 0; k < 12; ++k) acc[k] = {sm[s * cs + (2 * k) * SB + tx], sm[s * cs + (2 * k + 1) * SB + tx]};
     if (has_x) {
       Cx<R> w[12];
-      any_load<R>(x, r, (long)s * Vh + cb, w);
+      cld<R, PV>(x, r, (long)s * Vh + cb, w);
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = {fma(scale, acc[k].re, w[k].re), fma(scale, acc[k].im, w[k].im)};
     } else {
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] = {scale * acc[k].re, scale * acc[k].im};
     }
-    any_store<R>(out, r, (long)s * Vh + cb, acc);
+    cst<R, PV>(out, r, (long)s * Vh + cb, acc);
   }
 }
 
@@ -170,15 +187,29 @@ void run_col(const DwParams& p, const ColSpec& spec, const Field& in, Field& out
   dim3 grid((unsigned)((in.Vh + SB - 1) / SB), in.nrhs);
   static std::atomic<unsigned long long> attr_mask{0};
   if (first_use_on_device(attr_mask)) {
-    QCD_CK(cudaFuncSetAttribute(k_col<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-    QCD_CK(cudaFuncSetAttribute(k_col<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    for (const void* k : {(const void*)k_col<double, -1>, (const void*)k_col<double, P64>, (const void*)k_col<float, -1>,
+                          (const void*)k_col<float, P32>, (const void*)k_col<float, P16>})
+      QCD_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   }
-  if (dbl)
-    launch_k(k_col<double>, grid, blk, smem, st, make_coef<double>(p, spec), any_view(in), any_view(out), in.Vh, dagger,
-                                           scale, xv, x != nullptr, stop);
-  else
-    launch_k(k_col<float>, grid, blk, smem, st, make_coef<float>(p, spec), any_view(in), any_view(out), in.Vh, dagger,
-                                          (float)scale, xv, x != nullptr, stop);
+  const int pv = (in.prec == out.prec && (!x || x->prec == out.prec)) ? in.prec : -1;  // one storage format
+  const AnyView iv = any_view(in), ov = any_view(out);
+  const bool hx = x != nullptr;
+  if (dbl) {
+    const ColCoef<double> cc = make_coef<double>(p, spec);
+    if (pv == QCD_F64)
+      launch_k(k_col<double, P64>, grid, blk, smem, st, cc, iv, ov, in.Vh, dagger, scale, xv, hx, stop);
+    else
+      launch_k(k_col<double, -1>, grid, blk, smem, st, cc, iv, ov, in.Vh, dagger, scale, xv, hx, stop);
+  } else {
+    const ColCoef<float> cc = make_coef<float>(p, spec);
+    const float sc = (float)scale;
+    if (pv == QCD_F32)
+      launch_k(k_col<float, P32>, grid, blk, smem, st, cc, iv, ov, in.Vh, dagger, sc, xv, hx, stop);
+    else if (pv == QCD_F16)
+      launch_k(k_col<float, P16>, grid, blk, smem, st, cc, iv, ov, in.Vh, dagger, sc, xv, hx, stop);
+    else
+      launch_k(k_col<float, -1>, grid, blk, smem, st, cc, iv, ov, in.Vh, dagger, sc, xv, hx, stop);
+  }
   QCD_LAUNCH_CK();
 }
 

@@ -534,16 +534,13 @@ struct Solver {
 
   bool bicg() const { return prm.method == QCD_BICGSTAB; }
   // BiCGStab inner products fused into the stencil epilogue: one Wilson
-  // right-hand side stored in FP32 or FP64 (group sums by the stencil's last
-  // blocks), or several stored in FP32 (per-warp partials summed per rhs)
-  bool fused() const { return bicg() && f.type == QCD_WILSON && nrhs == 1 && inner != QCD_F16; }
+  // right-hand side (group sums by the stencil's last blocks), or several stored
+  // in FP32 (per-warp partials summed per rhs)
+  bool fused() const { return bicg() && f.type == QCD_WILSON && nrhs == 1; }
   bool fused_multi() const { return bicg() && f.type == QCD_WILSON && nrhs > 1 && inner == QCD_F32; }
-  // CG: Re(p, q) formed in the epilogue of the last stencil of Mhat^dag (FP32, or FP16 with
-  // several slices; per-warp partials summed per slice when there are several slices, else
-  // group sums)
-  bool fused_cg() const {
-    return !bicg() && (inner == QCD_F32 || (inner == QCD_F16 && nrhs * ls > 1));
-  }
+  // CG: Re(p, q) formed in the epilogue of the last stencil of Mhat^dag (FP32 or FP16;
+  // per-warp partials summed per slice when there are several slices, else group sums)
+  bool fused_cg() const { return !bicg() && (inner == QCD_F32 || inner == QCD_F16); }
   bool cg_single() const { return fused_cg() && nrhs * ls == 1; }
   long n() const { return r.nsites(); }
 

@@ -238,6 +238,58 @@ __global__ void __launch_bounds__(256) k_hop_pk(HopArgs<P, RECON> A) {
   A.out.offset_rhs(r).store_p(site, o);
 }
 
+constexpr int kRedGroup = 64;
+
+// The group sums of the single-slice stencils' fused inner products: v[3] per
+// thread, summed per warp in R, per block in FP64 (one partial per block), then
+// by the last block of each group of kRedGroup blocks in block order.
+template <typename R, typename HA>
+__device__ __forceinline__ void red_epilogue(const HA& A, R v[3]) {
+  // warp sums in R
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  __shared__ double wsum[8][3];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) wsum[warp][k] = (double)v[k];
+  __syncthreads();
+  const int ngroups = (gridDim.x + kRedGroup - 1) / kRedGroup;
+  const int grp = blockIdx.x / kRedGroup;
+  if (threadIdx.x == 0) {
+    double b[3] = {0.0, 0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) b[k] += wsum[w][k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) A.partial[(long)blockIdx.x * 4 + k] = b[k];
+    __threadfence();
+    const int members = min(kRedGroup, (int)gridDim.x - grp * kRedGroup);
+    last = (atomicAdd(&A.counters[grp], 1) == members - 1);
+    if (blockIdx.x == 0) *A.npartial = ngroups;
+  }
+  __syncthreads();
+  if (last && warp == 0) {  // the group's last block: sum its members in order
+    __threadfence();
+    const int first = grp * kRedGroup;
+    const int members = min(kRedGroup, (int)gridDim.x - first);
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int m = lane; m < members; m += 32)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) g[k] += __ldcg(&A.partial[(long)(first + m) * 4 + k]);  // L2, not a stale L1
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      for (int o = 16; o > 0; o >>= 1) g[k] += __shfl_down_sync(0xffffffffu, g[k], o);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) A.gpartial[(long)grp * 4 + k] = g[k];
+      A.counters[grp] = 0;
+    }
+  }
+}
+
 // Single right-hand side, out = x + a H in, with a BiCGStab inner product
 // formed in the epilogue from the values just stored (FP32 / FP64 storage,
 // so the stored and the computed values agree): RED = 1 gives (rt, out),
@@ -246,8 +298,6 @@ __global__ void __launch_bounds__(256) k_hop_pk(HopArgs<P, RECON> A) {
 // across warps and blocks in FP64: one partial per block, then the last
 // block of each group of 64 blocks sums the group (fixed order, so the result
 // does not depend on block scheduling).
-constexpr int kRedGroup = 64;
-
 template <int P, int RECON, int RED, int PF>
 __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
   pdl_enter();
@@ -292,49 +342,68 @@ __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
     v[0] = d.re;
     v[1] = d.im;
   }
-  // warp sums in R
+  red_epilogue<R>(A, v);
+}
+
+// The packed single-slice stencil (k_hop_pk) with the inner products of
+// k_hop_red in its epilogue, for FP16 storage: the sums use the values as stored
+// (the FP16 halves times the site scale, for out as for rt and x), so they are
+// the inner products of the fields the next kernels read.
+template <int P, int RECON, int RED>
+__global__ void __launch_bounds__(256) k_hop_pk_red(HopArgs<P, RECON> A) {
+  pdl_enter();
+  static_assert(P == P16, "the packed stencil with fused inner products is the FP16 one");
+  if (A.stop && *A.stop) return;
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  float v[3] = {0.f, 0.f, 0.f};
+  if (cb < A.g.Vh) {
+    const SiteCoords c = cb_to_site(A.g, cb, A.out_parity);
+    P2 acc[6];
 #pragma unroll
-  for (int k = 0; k < 3; ++k)
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-  __shared__ double wsum[8][3];
-  __shared__ int last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0)
+    for (int k = 0; k < 6; ++k) acc[k] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const float sg = A.dagger ? 1.f : -1.f;
+    hop_link_gp<P, RECON, 0, false>(A, c, cb, sg, A.in, 0, acc);
+    hop_link_gp<P, RECON, 0, true>(A, c, cb, sg, A.in, 0, acc);
+    hop_link_gp<P, RECON, 1, false>(A, c, cb, sg, A.in, 0, acc);
+    hop_link_gp<P, RECON, 1, true>(A, c, cb, sg, A.in, 0, acc);
+    hop_link_gp<P, RECON, 2, false>(A, c, cb, sg, A.in, 0, acc);
+    hop_link_gp<P, RECON, 2, true>(A, c, cb, sg, A.in, 0, acc);
+    hop_link_gp<P, RECON, 3, false>(A, c, cb, sg, A.in, 0, acc);
+    hop_link_gp<P, RECON, 3, true>(A, c, cb, sg, A.in, 0, acc);
+    const float2 a2 = bc2((float)A.a);
+    P2 xs[6], o[6], orr[6];
+    A.x.load_p(cb, xs);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) wsum[warp][k] = (double)v[k];
-  __syncthreads();
-  const int ngroups = (gridDim.x + kRedGroup - 1) / kRedGroup;
-  const int grp = blockIdx.x / kRedGroup;
-  if (threadIdx.x == 0) {
-    double b[3] = {0.0, 0.0, 0.0};
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+    for (int k = 0; k < 6; ++k) o[k] = {fma2(a2, acc[k].re, xs[k].re), fma2(a2, acc[k].im, xs[k].im)};
+    A.out.template store_p_rounded<true>(cb, o, orr);
+    float2 dr = make_float2(0.f, 0.f), di = dr, dj = dr;
+    if constexpr (RED == 1) {  // (rt, out) = sum conj(rt) out
+      P2 w[6];
+      A.rt.load_p(cb, w);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) b[k] += wsum[w][k];
+      for (int q = 0; q < 6; ++q) {
+        dr = fma2(w[q].re, orr[q].re, dr);
+        dr = fma2(w[q].im, orr[q].im, dr);
+        di = fma2(w[q].re, orr[q].im, di);
+        dj = fma2(w[q].im, orr[q].re, dj);
+      }
+    } else {  // (out, x) = sum conj(out) x, |out|^2
+      float2 oo = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) A.partial[(long)blockIdx.x * 4 + k] = b[k];
-    __threadfence();
-    const int members = min(kRedGroup, (int)gridDim.x - grp * kRedGroup);
-    last = (atomicAdd(&A.counters[grp], 1) == members - 1);
-    if (blockIdx.x == 0) *A.npartial = ngroups;
-  }
-  __syncthreads();
-  if (last && warp == 0) {  // the group's last block: sum its members in order
-    __threadfence();
-    const int first = grp * kRedGroup;
-    const int members = min(kRedGroup, (int)gridDim.x - first);
-    double g[3] = {0.0, 0.0, 0.0};
-    for (int m = lane; m < members; m += 32)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) g[k] += __ldcg(&A.partial[(long)(first + m) * 4 + k]);  // L2, not a stale L1
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      for (int o = 16; o > 0; o >>= 1) g[k] += __shfl_down_sync(0xffffffffu, g[k], o);
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) A.gpartial[(long)grp * 4 + k] = g[k];
-      A.counters[grp] = 0;
+      for (int q = 0; q < 6; ++q) {
+        dr = fma2(orr[q].re, xs[q].re, dr);
+        dr = fma2(orr[q].im, xs[q].im, dr);
+        di = fma2(orr[q].re, xs[q].im, di);
+        dj = fma2(orr[q].im, xs[q].re, dj);
+        oo = fma2(orr[q].re, orr[q].re, oo);
+        oo = fma2(orr[q].im, orr[q].im, oo);
+      }
+      v[2] = oo.x + oo.y;
     }
+    v[0] = dr.x + dr.y;
+    v[1] = (di.x + di.y) - (dj.x + dj.y);
   }
+  red_epilogue<float>(A, v);
 }
 
 // RED (with TS = 1, several right-hand sides): the BiCGStab inner products of
@@ -796,11 +865,28 @@ void launch_smp(HopLaunch<P, RECON>* L) {
 // same with the registers bounded for 24 resident warps; 700 + ...: that with
 // the links staged as two rows; -3121: 12 slices, one direction by tensor-core MMA
 // (k_hop_tc; FP16, 12-real)
+// the packed FP16 stencil with fused inner products (one slice, A.red 1 or 2)
+template <int P, int RECON>
+void launch_pk_red(HopLaunch<P, RECON>* L, int block) {
+  if constexpr (P == P16) {
+    const HopArgs<P, RECON>& A = L->args;
+    const unsigned blocks = (unsigned)((A.g.Vh + block - 1) / block);
+    if (A.red == 1)
+      launch_k(k_hop_pk_red<P, RECON, 1>, blocks, block, 0, L->st, A);
+    else
+      launch_k(k_hop_pk_red<P, RECON, 2>, blocks, block, 0, L->st, A);
+  } else {
+    raise(QCD_ERR_UNSUPPORTED, "the packed stencil with fused inner products is the FP16 one");
+  }
+}
+
 template <int P, int RECON>
 void run_cfg(void* ctx, const LaunchCfg& cfg) {
   auto* L = (HopLaunch<P, RECON>*)ctx;
   if constexpr (P == P64) {
     launch_tile<P, RECON, 1>(L, cfg.block);
+  } else if (P == P16 && L->args.red && L->args.nslices == 1) {  // the one FP16 kernel with fused sums
+    launch_pk_red<P, RECON>(L, cfg.block);
   } else if (L->args.red && L->args.nslices > 1) {  // fused reductions over several slices
     switch (cfg.tile) {
       case -81: L->args.red == 1 ? launch_sm<P, RECON, 8, 1, 1>(L) : launch_sm<P, RECON, 8, 1, 2>(L); break;
@@ -824,6 +910,7 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case 301: launch_pk<P, RECON, 0>(L, cfg.block); break;
       case 311: launch_pk<P, RECON, 1>(L, cfg.block); break;
       case 321: launch_pk<P, RECON, 2>(L, cfg.block); break;
+      case 341: launch_pk_red<P, RECON>(L, cfg.block); break;
       case 2: launch_tile<P, RECON, 2>(L, cfg.block); break;
       case 4: launch_tile<P, RECON, 4>(L, cfg.block); break;
       case -41: launch_sm<P, RECON, 4, 1>(L); break;
@@ -858,9 +945,9 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (red && red->mode) {
     // several slices: FP32 or FP16 (the sums use the computed output, which the FP16 store
     // then rounds: a relative difference of order 1e-3 / sqrt(sites) in the sum); one: FP32 / FP64
-    if (!x || (red->mode == 1 && !red->rt) || (multi_red ? P == P64 : P == P16))
-      raise(QCD_ERR_ARG, "fused reductions need FP32 / FP16 fields (several slices) or FP32 / FP64 fields (one), "
-                         "and an x term");
+    if (!x || (red->mode == 1 && !red->rt) || (multi_red && P == P64))
+      raise(QCD_ERR_ARG, "fused reductions need FP32 / FP16 fields (several slices) or FP64 / FP32 / FP16 "
+                         "fields (one), and an x term");
     A.red = red->mode;
     A.partial = red->partial;
     A.gpartial = red->gpartial;
@@ -907,11 +994,14 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P == P16 && RECON == 12 && A.nslices == 12) cands.push_back({384, -3121});  // tensor-core direction
   if (A.red) {  // the fused reduction exists for one slice per thread only
     cands.clear();
-    for (int b : blocks) cands.push_back({b, 1});
+    if (P != P16)
+      for (int b : blocks) cands.push_back({b, 1});
   }
-  if (P != P64)  // one slice per thread with prefetches (memory-bound precisions)
+  if (P != P64 && !(A.red && P == P16))  // one slice per thread with prefetches (memory-bound precisions)
     for (int pf : {101, 201})
       for (int b : blocks) cands.push_back({b, pf});
+  if (A.red && P == P16)  // FP16: the packed stencil, its sums over the values as stored
+    for (int b : blocks) cands.push_back({b, 341});
   if (P != P64 && !A.red)  // one slice per thread, packed arithmetic, with 0, 1 or 2 directions of prefetch
     for (int pk : {301, 311, 321})
       for (int b : blocks) cands.push_back({b, pk});

@@ -78,8 +78,8 @@ for case in json.loads(sys.argv[1]):
         nrhs = case.get("nrhs", 1)
         b = inputs.z2_source((nrhs, V, 4, 3), 0)
         x = torch.zeros((nrhs, V, 4, 3), dtype=torch.complex128, device="cuda")
-        qcd.solve(g, f, torch.from_numpy(b).cuda(), x, nrhs=nrhs, tol=1e-10, inner="f32", use_graph=True,
-                  graph_chunk=8)
+        qcd.solve(g, f, torch.from_numpy(b).cuda(), x, nrhs=nrhs, tol=1e-10, inner=case.get("inner", "f32"),
+                  method=qcd.CG_NORMAL if case.get("cg") else qcd.BICGSTAB, use_graph=True, graph_chunk=8)
         xr = x.cpu().numpy()
         res.append(max(float(np.linalg.norm(b[k] - ora.wilson(L, BC, kappa, U, xr[k])) / np.linalg.norm(b[k]))
                        for k in range(nrhs)))
@@ -134,6 +134,14 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
         for xp, red in ((0, 0), (1, 1), (1, 2)):
             lines.append(f"{_key(L, 'f32', 12, 1, xp, red)}\t{block}\t{tile}")
         tol.append(1e-10)
+    # the packed FP16 stencil with the inner products in its epilogue (BiCGStab and CG; a ragged
+    # last block too)
+    for L, block, cg in (((8, 8, 8, t), 64, False), ((6, 6, 4, t + 2), 256, False), ((8, 8, 8, t + 4), 128, True)):
+        cases.append({"kind": "solve", "L": L, "recon": 12, "inner": "f16", "cg": cg})
+        for xp, red in ((1, 1), (1, 2)) if not cg else ((1, 1),):
+            lines.append(f"{_key(L, 'f16', 12, 1, xp, red)}\t{block}\t341")
+        tol.append(1e-10)
+    t += 6
     # the fused-reduction shared-memory stencils of the batched (several rhs) iteration
     for tile, block in ((-41, 128), (-81, 256), (-241, 128), (-281, 256), (-541, 128), (-581, 256),
                         (-641, 128), (-681, 256), (-741, 128), (-781, 256)):
