@@ -122,9 +122,11 @@ def run_dwf(args):
         a_ = torch.empty(nb, dtype=torch.uint8, device=dev)
         o_ = torch.empty(nb, dtype=torch.uint8, device=dev)
         qcd.field_pack(g, f, prec, 1, bd, a_)
-        if args.profile == "cg":  # ncu: one warmed-up CG solve (FP32 inner, IEEE-FP64 outer steps)
-            kw = dict(method=qcd.CG_NORMAL, tol=1e-10, inner="f32", use_graph=True, graph_chunk=32,
-                      delta=(args.delta or 0.0), outer=args.outer)
+        if args.profile == "cg":  # ncu: one warmed-up CG solve (inner precision --profile-prec, FP32 or
+            # FP16, at the reliable-update factor of the measured solve; IEEE-FP64 outer steps)
+            pin = "f16" if args.profile_prec == "f16" else "f32"
+            kw = dict(method=qcd.CG_NORMAL, tol=1e-10, inner=pin, use_graph=True, graph_chunk=32,
+                      delta=(args.delta or (1e-4 if pin == "f32" else 0.0)), outer=args.outer)
             x = torch.zeros_like(bd)
             qcd.solve(g, f, bd, x, **kw)
             x.zero_()
