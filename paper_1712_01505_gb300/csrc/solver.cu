@@ -30,6 +30,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -503,6 +505,32 @@ __global__ void k_rdot(AnyView a_, AnyView b_, long n, double* partial, const Sc
 
 __global__ void k_reset(int* ctl) { *ctl = 0; }
 
+// Blocks of a grid-stride iteration kernel: one full wave (its resident blocks per SM
+// times the SMs; fewer for short vectors), so that no partly filled last wave leaves
+// SMs idle (the FP32 x / r update holds 3 blocks per SM; launched as 4 per SM, its
+// second wave ran on a third of the slots).
+unsigned wave_blocks(const void* kernel, long n) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> occ;  // resident blocks per SM, per device
+  int dev = 0;
+  QCD_CK(cudaGetDevice(&dev));
+  int o = 1;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = occ.find({dev, kernel});
+    if (it == occ.end()) {
+      int v = 0;
+      QCD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kThreads, 0));
+      it = occ.emplace(std::make_pair(dev, kernel), std::max(v, 1)).first;
+    }
+    o = it->second;
+  }
+  const long need = (n + kThreads - 1) / kThreads;
+  return (unsigned)std::max(1L, std::min(need, (long)o * sm_count()));
+}
+// the most blocks per SM any of them can have (2048 threads of 256): the partial-sum arrays' size
+constexpr int kMaxBlocksPerSM = 8;
+
 unsigned red_blocks(long n) {
   long b = (n + kThreads - 1) / kThreads;
   long cap = 4L * sm_count();
@@ -546,22 +574,30 @@ struct Solver {
 
   void body() {
     const long nn = n();
-    dim3 grid(nblk, nrhs);
     const int dag = prm.dagger;
     if (inner == QCD_F64)
-      body_t<double, double, P64>(grid, nn, dag);
+      body_t<double, double, P64>(nn, dag);
     else if (inner == QCD_F32)
-      body_t<float, float, P32>(grid, nn, dag);
+      body_t<float, float, P32>(nn, dag);
     else
-      body_t<float, float, P16>(grid, nn, dag);
+      body_t<float, float, P16>(nn, dag);
+  }
+
+  // grid of a grid-stride kernel over all right-hand sides (one wave per rhs row)
+  template <typename K>
+  dim3 wave(K kernel, long nn) const {
+    return dim3(wave_blocks((const void*)kernel, nn), nrhs);
   }
 
   // PV: the storage precision of the inner vectors (the solution accumulator is FP64
-  // with FP64 vectors, else FP32)
+  // with FP64 vectors, else FP32).  A kernel that writes per-block partial sums hands
+  // its block count to the one that reads them.
   template <typename R, typename RX, int PV>
-  void body_t(dim3 grid, long nn, int dag) {
+  void body_t(long nn, int dag) {
     if (bicg()) {
-      launch_k(k_bicg_p<R, PV>, grid, kThreads, 0, st, any_view(r), any_view(p), any_view(v), nn, sc, ctl);
+      int nb_ts = 0;  // partials of (t, s), |t|^2 from k_ts_tt (the unfused path)
+      launch_k(k_bicg_p<R, PV>, wave(k_bicg_p<R, PV>, nn), kThreads, 0, st, any_view(r), any_view(p), any_view(v),
+               nn, sc, ctl);
       QCD_LAUNCH_CK();
       if (fused()) {
         // (rt, v) and (t, s), |t|^2 formed in the epilogue of the stencil that writes v / t
@@ -569,8 +605,8 @@ struct Solver {
         RedSpec red1{1, &rt, bpartial, partial, counters, npart};
         RedSpec red2{2, nullptr, bpartial, partial, counters, npart};
         apply_mhat(opin, p, v, dag, st, "in", ctl, &red1);
-        launch_k(k_bicg_s<R, PV>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
-                                               npart);
+        launch_k(k_bicg_s<R, PV>, wave(k_bicg_s<R, PV>, nn), kThreads, 0, st, any_view(r), any_view(v), any_view(s),
+                 nn, sc, ctl, partial, 0, npart);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl, &red2);
       } else if (fused_multi()) {
@@ -578,33 +614,36 @@ struct Solver {
         RedSpec red1{1, &rt, bpartial, partial, nullptr, nullptr};
         RedSpec red2{2, nullptr, bpartial, partial, nullptr, nullptr};
         apply_mhat(opin, p, v, dag, st, "in", ctl, &red1);
-        launch_k(k_bicg_s<R, PV>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, 1,
-                                               nullptr);
+        launch_k(k_bicg_s<R, PV>, wave(k_bicg_s<R, PV>, nn), kThreads, 0, st, any_view(r), any_view(v), any_view(s),
+                 nn, sc, ctl, partial, 1, nullptr);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl, &red2);
       } else {
         apply_mhat(opin, p, v, dag, st, "in", ctl);
-        launch_k(k_cdot<R, PV>, grid, kThreads, 0, st, any_view(rt), any_view(v), nn, partial, sc, ctl);
+        const dim3 gc = wave(k_cdot<R, PV>, nn);
+        launch_k(k_cdot<R, PV>, gc, kThreads, 0, st, any_view(rt), any_view(v), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
-        launch_k(k_bicg_s<R, PV>, grid, kThreads, 0, st, any_view(r), any_view(v), any_view(s), nn, sc, ctl, partial, nblk,
-                                               nullptr);
+        launch_k(k_bicg_s<R, PV>, wave(k_bicg_s<R, PV>, nn), kThreads, 0, st, any_view(r), any_view(v), any_view(s),
+                 nn, sc, ctl, partial, (int)gc.x, nullptr);
         QCD_LAUNCH_CK();
         apply_mhat(opin, s, t, dag, st, "in", ctl);
-        launch_k(k_ts_tt<R, PV>, grid, kThreads, 0, st, any_view(t), any_view(s), nn, partial, sc, ctl);
+        const dim3 gt = wave(k_ts_tt<R, PV>, nn);
+        launch_k(k_ts_tt<R, PV>, gt, kThreads, 0, st, any_view(t), any_view(s), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
+        nb_ts = (int)gt.x;
       }
-      launch_k(k_bicg_xr<R, RX, PV>, grid, kThreads, 0, st, any_view(xin), any_view(p), any_view(s), any_view(t),
-                                                  any_view(r), any_view(rt), nn, partial,
-                                                  fused_multi() ? 1 : (int)nblk, fused() ? ctl + 2 : nullptr,
-                                                  partial2, sc, ctl);
+      const dim3 gx = wave(k_bicg_xr<R, RX, PV>, nn);
+      launch_k(k_bicg_xr<R, RX, PV>, gx, kThreads, 0, st, any_view(xin), any_view(p), any_view(s), any_view(t),
+               any_view(r), any_view(rt), nn, partial, fused_multi() ? 1 : nb_ts, fused() ? ctl + 2 : nullptr,
+               partial2, sc, ctl);
       QCD_LAUNCH_CK();
-      launch_k(k_bicg_check, nrhs, kThreads, 0, st, sc, partial2, nblk, ctl, 1);
+      launch_k(k_bicg_check, nrhs, kThreads, 0, st, sc, partial2, (int)gx.x, ctl, 1);
       QCD_LAUNCH_CK();
     } else {
-      launch_k(k_cg_p<R, PV>, grid, kThreads, 0, st, any_view(r), any_view(p), nn, sc, ctl);
+      launch_k(k_cg_p<R, PV>, wave(k_cg_p<R, PV>, nn), kThreads, 0, st, any_view(r), any_view(p), nn, sc, ctl);
       QCD_LAUNCH_CK();
       apply_mhat(opin, p, w, 0, st, "in", ctl);
-      int nb = (int)nblk;
+      int nb = 0;
       const int* nb_dev = nullptr;
       if (fused_cg()) {  // (p, q) in the epilogue of q = Mhat^dag w
         int* npart = ctl + 2;
@@ -616,13 +655,16 @@ struct Solver {
           nb = ls;  // one sum per slice
       } else {
         apply_mhat(opin, w, q, 1, st, "in", ctl);
-        launch_k(k_rdot<R, PV>, grid, kThreads, 0, st, any_view(p), any_view(q), nn, partial, sc, ctl);
+        const dim3 gr = wave(k_rdot<R, PV>, nn);
+        launch_k(k_rdot<R, PV>, gr, kThreads, 0, st, any_view(p), any_view(q), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
+        nb = (int)gr.x;
       }
-      launch_k(k_cg_xr<R, RX, PV>, grid, kThreads, 0, st, any_view(xin), any_view(p), any_view(q), any_view(r),
-                                                nn, partial, nb, nb_dev, partial2, sc, ctl);
+      const dim3 gx = wave(k_cg_xr<R, RX, PV>, nn);
+      launch_k(k_cg_xr<R, RX, PV>, gx, kThreads, 0, st, any_view(xin), any_view(p), any_view(q), any_view(r), nn,
+               partial, nb, nb_dev, partial2, sc, ctl);
       QCD_LAUNCH_CK();
-      launch_k(k_cg_check, nrhs, kThreads, 0, st, sc, partial2, nblk, ctl, 1);
+      launch_k(k_cg_check, nrhs, kThreads, 0, st, sc, partial2, (int)gx.x, ctl, 1);
       QCD_LAUNCH_CK();
     }
   }
@@ -760,9 +802,10 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   // reductions); per-block partials of the fused reductions (blocks of >= 64
   // sites) and one counter per group of 64 blocks, zeroed once here
   const size_t nstencil_blocks = (size_t)(lat.Vh / 64 + 1);
-  const size_t npart = std::max<size_t>((size_t)S.nblk * nrhs, nstencil_blocks / 64 + 1);
+  const size_t nwave = (size_t)std::max<long>(S.nblk, (long)kMaxBlocksPerSM * sm_count());  // grid of any wave
+  const size_t npart = std::max<size_t>(nwave * nrhs, nstencil_blocks / 64 + 1);
   S.partial = (double*)g->ws.get("s.partial", sizeof(double) * npart * kMaxPartial);
-  S.partial2 = (double*)g->ws.get("s.partial2", sizeof(double) * (size_t)S.nblk * nrhs * kMaxPartial);
+  S.partial2 = (double*)g->ws.get("s.partial2", sizeof(double) * nwave * nrhs * kMaxPartial);
   if (S.fused_multi() || (S.fused_cg() && !S.cg_single()))  // per-warp partials of every slice
     S.bpartial = (double*)g->ws.get("s.bpartialN",
                                     sizeof(double) * (size_t)nrhs * ls * ((lat.Vh + 31) / 32) * kMaxPartial);
