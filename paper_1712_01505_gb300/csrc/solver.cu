@@ -642,19 +642,19 @@ struct Solver {
     } else {
       launch_k(k_cg_p<R, PV>, wave(k_cg_p<R, PV>, nn), kThreads, 0, st, any_view(r), any_view(p), nn, sc, ctl);
       QCD_LAUNCH_CK();
-      apply_mhat(opin, p, w, 0, st, "in", ctl);
+      apply_mhat(opin, p, w, dag, st, "in", ctl);  // A p, A = Mhat (Mhat^dag for the adjoint system)
       int nb = 0;
       const int* nb_dev = nullptr;
       if (fused_cg()) {  // (p, q) in the epilogue of q = Mhat^dag w
         int* npart = ctl + 2;
         RedSpec red{1, &p, bpartial, partial, counters, npart};
-        apply_mhat(opin, w, q, 1, st, "in", ctl, &red);
+        apply_mhat(opin, w, q, 1 - dag, st, "in", ctl, &red);
         if (cg_single())
           nb_dev = npart;
         else
           nb = ls;  // one sum per slice
       } else {
-        apply_mhat(opin, w, q, 1, st, "in", ctl);
+        apply_mhat(opin, w, q, 1 - dag, st, "in", ctl);
         const dim3 gr = wave(k_rdot<R, PV>, nn);
         launch_k(k_rdot<R, PV>, gr, kThreads, 0, st, any_view(p), any_view(q), nn, partial, sc, ctl);
         QCD_LAUNCH_CK();
@@ -892,7 +892,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
   auto normal_residual = [&](const Field& rhat, int r0, int n) {
     Field w = sub(S.w, r0, n), r = sub(S.r, r0, n);
     blas_copy(rhat, w, st);
-    apply_mhat(S.opin, w, r, 1, st, "in");
+    apply_mhat(S.opin, w, r, 1 - dag, st, "in");  // A^dag rhat
     blas_norm2(r, rn.data() + r0, st, g);
   };
   auto true_residual = [&](bool x_is_zero, int r0, int n) {
@@ -947,12 +947,12 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
       }
       blas_norm2(re, rf, st, g);
       for (int r = r0; r < r0 + n; ++r) rfull[r] = std::sqrt(rfull[r]);
-      // the inner residual: r_e (BiCGStab) or Mhat^dag r_e (CG)
+      // the inner residual: r_e (BiCGStab) or A^dag r_e (CG; A = Mhat, Mhat^dag for the adjoint)
       if (cg_inner_normal) {
         normal_residual(re, r0, n);
         return;
       }
-      if (!S.bicg()) apply_mhat(S.op64, re, r64, 1, st, "o64");
+      if (!S.bicg()) apply_mhat(S.op64, re, r64, 1 - dag, st, "o64");
       blas_norm2(r64, rn.data() + r0, st, g);
       return;
     }
@@ -969,7 +969,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
       blas_norm2(t64, rf, st, g);
     }
     for (int r = r0; r < r0 + n; ++r) rfull[r] = std::sqrt(rfull[r]);
-    // the inner residual: rhat (BiCGStab) or Mhat^dag rhat (CG)
+    // the inner residual: rhat (BiCGStab) or A^dag rhat (CG; A = Mhat, Mhat^dag for the adjoint)
     if (cg_inner_normal) {
       normal_residual(t64, r0, n);
       return;
@@ -977,7 +977,7 @@ void solve_device(qcd_gauge* g, const qcd_fermion& f, const qcd_solver_params& p
     if (S.bicg()) {
       blas_copy(t64, r64, st);
     } else {
-      apply_mhat(S.op64, t64, r64, 1, st, "o64");
+      apply_mhat(S.op64, t64, r64, 1 - dag, st, "o64");
     }
     blas_norm2(r64, rn.data() + r0, st, g);
   };

@@ -54,6 +54,44 @@ def test_wilson_mixed_precision_reaches_1e10(inner, graph):
         assert info[0]["outer_updates"] >= 2
 
 
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_wilson_cg_normal_adjoint_system(inner):
+    # CG on the normal equations of the adjoint system: A = Mhat^dag, iterated on A^dag A = Mhat Mhat^dag
+    device()
+    L, kappa = (4, 4, 6, 8), 0.12
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.3, 9)
+    b = inputs.gaussian_source((V, 4, 3), 10)
+    g = qcd.Gauge.load(to_dev(U), L, BC)
+    f = qcd.wilson(kappa)
+    x = torch.zeros((V, 4, 3), dtype=torch.complex128, device=device())
+    info, _ = qcd.solve(g, f, to_dev(b), x, method=qcd.CG_NORMAL, tol=1e-10, inner=inner, dagger=True)
+    assert info[0]["converged"], info
+    assert oracle_resid_wilson(L, kappa, U, b, x.cpu().numpy(), dagger=True) <= 1e-10
+
+
+@pytest.mark.parametrize("method", ["bicgstab", "cg"])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_wilson_fp16_inner_with_fused_sums(method, dagger):
+    # one right-hand side with FP16 inner vectors: the inner products come from the epilogue of
+    # the packed FP16 stencil (BiCGStab: (rt, v), (t, s), |t|^2; CG on the normal equations:
+    # Re(p, q)); a lattice whose last site block is ragged
+    device()
+    L, kappa = (6, 6, 4, 8), 0.12
+    V = int(np.prod(L))
+    U = inputs.gauge_field(L, 0.3, 7)
+    b = inputs.gaussian_source((V, 4, 3), 8)
+    g = qcd.Gauge.load(to_dev(U), L, BC, recon=12)
+    f = qcd.wilson(kappa)
+    x = torch.zeros((V, 4, 3), dtype=torch.complex128, device=device())
+    m = qcd.BICGSTAB if method == "bicgstab" else qcd.CG_NORMAL
+    info, _ = qcd.solve(g, f, to_dev(b), x, method=m, tol=1e-10, inner="f16", dagger=dagger, use_graph=True,
+                        graph_chunk=8)
+    assert info[0]["converged"], info
+    assert oracle_resid_wilson(L, kappa, U, b, x.cpu().numpy(), dagger=dagger) <= 1e-10
+    assert info[0]["outer_updates"] >= 2
+
+
 def test_wilson_dagger_solve_and_warm_start():
     device()
     L, kappa = (4, 4, 6, 8), 0.12
