@@ -348,15 +348,17 @@ __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
 // The packed single-slice stencil (k_hop_pk) with the inner products of
 // k_hop_red in its epilogue, for FP16 storage: the sums use the values as stored
 // (the FP16 halves times the site scale, for out as for rt and x), so they are
-// the inner products of the fields the next kernels read.
-template <int P, int RECON, int RED>
+// the inner products of the fields the next kernels read.  SPT sites per thread.
+template <int P, int RECON, int RED, int SPT>
 __global__ void __launch_bounds__(256) k_hop_pk_red(HopArgs<P, RECON> A) {
   pdl_enter();
   static_assert(P == P16, "the packed stencil with fused inner products is the FP16 one");
   if (A.stop && *A.stop) return;
-  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   float v[3] = {0.f, 0.f, 0.f};
-  if (cb < A.g.Vh) {
+#pragma unroll 1
+  for (int it = 0; it < SPT; ++it) {  // SPT sites per thread: one reduction epilogue per SPT blocks' worth
+    const int cb = (blockIdx.x * SPT + it) * blockDim.x + threadIdx.x;
+    if (cb >= A.g.Vh) break;
     const SiteCoords c = cb_to_site(A.g, cb, A.out_parity);
     P2 acc[6];
 #pragma unroll
@@ -398,10 +400,10 @@ __global__ void __launch_bounds__(256) k_hop_pk_red(HopArgs<P, RECON> A) {
         oo = fma2(orr[q].re, orr[q].re, oo);
         oo = fma2(orr[q].im, orr[q].im, oo);
       }
-      v[2] = oo.x + oo.y;
+      v[2] += oo.x + oo.y;
     }
-    v[0] = dr.x + dr.y;
-    v[1] = (di.x + di.y) - (dj.x + dj.y);
+    v[0] += dr.x + dr.y;
+    v[1] += (di.x + di.y) - (dj.x + dj.y);
   }
   red_epilogue<float>(A, v);
 }
@@ -855,9 +857,25 @@ void launch_smp(HopLaunch<P, RECON>* L) {
     launch_k(k_hop_smp<P, RECON, BY, RED, L12>, grid, blk, 0, L->st, A);
 }
 
+// the packed FP16 stencil with fused inner products (one slice, A.red 1 or 2), SPT sites per thread
+template <int P, int RECON, int SPT = 1>
+void launch_pk_red(HopLaunch<P, RECON>* L, int block) {
+  if constexpr (P == P16) {
+    const HopArgs<P, RECON>& A = L->args;
+    const unsigned blocks = (unsigned)((A.g.Vh + block * SPT - 1) / (block * SPT));
+    if (A.red == 1)
+      launch_k(k_hop_pk_red<P, RECON, 1, SPT>, blocks, block, 0, L->st, A);
+    else
+      launch_k(k_hop_pk_red<P, RECON, 2, SPT>, blocks, block, 0, L->st, A);
+  } else {
+    raise(QCD_ERR_UNSUPPORTED, "the packed stencil with fused inner products is the FP16 one");
+  }
+}
+
 // cfg.tile > 0: register tile of that many slices per thread (k_hop), 101 /
 // 201: one slice per thread with prefetch mode 1 / 2; 301 / 311 / 321: one slice
-// per thread with packed arithmetic (k_hop_pk), prefetch mode 0 / 1 / 2;
+// per thread with packed arithmetic (k_hop_pk), prefetch mode 0 / 1 / 2; 341 / 342 /
+// 344: the FP16 stencil with the fused inner products, 1 / 2 / 4 sites per thread;
 // cfg.tile < 0: shared-memory links (k_hop_sm), -tile = 10 * BY + TS for
 // BY thread rows of TS slices each; -tile = 200 + 10 * BY + TS: the same with at most
 // 64 registers per thread (32 resident warps per SM); -tile = 500 + 10 * BY + 1:
@@ -865,28 +883,18 @@ void launch_smp(HopLaunch<P, RECON>* L) {
 // same with the registers bounded for 24 resident warps; 700 + ...: that with
 // the links staged as two rows; -3121: 12 slices, one direction by tensor-core MMA
 // (k_hop_tc; FP16, 12-real)
-// the packed FP16 stencil with fused inner products (one slice, A.red 1 or 2)
-template <int P, int RECON>
-void launch_pk_red(HopLaunch<P, RECON>* L, int block) {
-  if constexpr (P == P16) {
-    const HopArgs<P, RECON>& A = L->args;
-    const unsigned blocks = (unsigned)((A.g.Vh + block - 1) / block);
-    if (A.red == 1)
-      launch_k(k_hop_pk_red<P, RECON, 1>, blocks, block, 0, L->st, A);
-    else
-      launch_k(k_hop_pk_red<P, RECON, 2>, blocks, block, 0, L->st, A);
-  } else {
-    raise(QCD_ERR_UNSUPPORTED, "the packed stencil with fused inner products is the FP16 one");
-  }
-}
-
 template <int P, int RECON>
 void run_cfg(void* ctx, const LaunchCfg& cfg) {
   auto* L = (HopLaunch<P, RECON>*)ctx;
   if constexpr (P == P64) {
     launch_tile<P, RECON, 1>(L, cfg.block);
-  } else if (P == P16 && L->args.red && L->args.nslices == 1) {  // the one FP16 kernel with fused sums
-    launch_pk_red<P, RECON>(L, cfg.block);
+  } else if (P == P16 && L->args.red && L->args.nslices == 1) {  // the FP16 kernel with fused sums
+    if (cfg.tile == 344)
+      launch_pk_red<P, RECON, 4>(L, cfg.block);
+    else if (cfg.tile == 342)
+      launch_pk_red<P, RECON, 2>(L, cfg.block);
+    else
+      launch_pk_red<P, RECON, 1>(L, cfg.block);
   } else if (L->args.red && L->args.nslices > 1) {  // fused reductions over several slices
     switch (cfg.tile) {
       case -81: L->args.red == 1 ? launch_sm<P, RECON, 8, 1, 1>(L) : launch_sm<P, RECON, 8, 1, 2>(L); break;
@@ -910,7 +918,6 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case 301: launch_pk<P, RECON, 0>(L, cfg.block); break;
       case 311: launch_pk<P, RECON, 1>(L, cfg.block); break;
       case 321: launch_pk<P, RECON, 2>(L, cfg.block); break;
-      case 341: launch_pk_red<P, RECON>(L, cfg.block); break;
       case 2: launch_tile<P, RECON, 2>(L, cfg.block); break;
       case 4: launch_tile<P, RECON, 4>(L, cfg.block); break;
       case -41: launch_sm<P, RECON, 4, 1>(L); break;
@@ -1000,8 +1007,9 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64 && !(A.red && P == P16))  // one slice per thread with prefetches (memory-bound precisions)
     for (int pf : {101, 201})
       for (int b : blocks) cands.push_back({b, pf});
-  if (A.red && P == P16)  // FP16: the packed stencil, its sums over the values as stored
-    for (int b : blocks) cands.push_back({b, 341});
+  if (A.red && P == P16)  // FP16: the packed stencil, its sums over the values as stored, 1 / 2 / 4 sites a thread
+    for (int t : {341, 342, 344})
+      for (int b : blocks) cands.push_back({b, t});
   if (P != P64 && !A.red)  // one slice per thread, packed arithmetic, with 0, 1 or 2 directions of prefetch
     for (int pk : {301, 311, 321})
       for (int b : blocks) cands.push_back({b, pk});

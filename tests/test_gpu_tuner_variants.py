@@ -134,14 +134,16 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
         for xp, red in ((0, 0), (1, 1), (1, 2)):
             lines.append(f"{_key(L, 'f32', 12, 1, xp, red)}\t{block}\t{tile}")
         tol.append(1e-10)
-    # the packed FP16 stencil with the inner products in its epilogue (BiCGStab and CG; a ragged
-    # last block too)
-    for L, block, cg in (((8, 8, 8, t), 64, False), ((6, 6, 4, t + 2), 256, False), ((8, 8, 8, t + 4), 128, True)):
+    # the packed FP16 stencil with the inner products in its epilogue, 1 / 2 / 4 sites per thread
+    # (BiCGStab and CG; a ragged last block too)
+    for L, block, cg, tile in (((8, 8, 8, t), 64, False, 341), ((6, 6, 4, t + 2), 256, False, 341),
+                               ((8, 8, 8, t + 4), 128, True, 341), ((6, 6, 4, t + 6), 64, False, 342),
+                               ((6, 6, 4, t + 8), 128, True, 344), ((8, 8, 8, t + 10), 64, False, 344)):
         cases.append({"kind": "solve", "L": L, "recon": 12, "inner": "f16", "cg": cg})
         for xp, red in ((1, 1), (1, 2)) if not cg else ((1, 1),):
-            lines.append(f"{_key(L, 'f16', 12, 1, xp, red)}\t{block}\t341")
+            lines.append(f"{_key(L, 'f16', 12, 1, xp, red)}\t{block}\t{tile}")
         tol.append(1e-10)
-    t += 6
+    t += 12
     # the fused-reduction shared-memory stencils of the batched (several rhs) iteration
     for tile, block in ((-41, 128), (-81, 256), (-241, 128), (-281, 256), (-541, 128), (-581, 256),
                         (-641, 128), (-681, 256), (-741, 128), (-781, 256)):
