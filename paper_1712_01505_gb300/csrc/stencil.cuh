@@ -341,6 +341,67 @@ __device__ __forceinline__ void hop_link_smp(const HopArgs<P, RECON>& A, const S
   reconstruct_p<MU>(g, sgn, f, acc);
 }
 
+// ----------------------------------------------------------------------------- bulk staging
+// Neighbour spinors staged in shared memory by the bulk-copy engine (cp.async.bulk
+// with an mbarrier that counts the bytes), so that a warp's next direction arrives
+// while it computes the current one, with no registers and no load instructions
+// of its own.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// generic-proxy accesses of shared memory ordered before later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// wait for the completion of the barrier's phase `parity`, at most about 2^20 polls;
+// false if it did not complete
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (int i = 0; i < (1 << 20); ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// acc += the hop from direction L for one slice (as hop_link_smp), the neighbour's six
+// 16-byte chunks read from a staged run: chunk q of site n at run[q * RUN + n - base]
+template <int P, int RECON, int L, int RUN, typename SM>
+__device__ __forceinline__ void hop_link_run(const SM& sm, int tx, float sg, const float4* run, int base,
+                                             P2 acc[6]) {
+  static_assert(P == P32, "the staged runs hold FP32 spinors");
+  constexpr int MU = L >> 1;
+  constexpr bool BACK = (L & 1) != 0;
+  const int n = sm.nb[L][tx] - base;
+  const float sgn = BACK ? -sg : sg;
+  P2 w[6], h[3], g[3];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float4 d = run[q * RUN + n];
+    w[q] = {make_float2(d.x, d.y), make_float2(d.z, d.w)};
+  }
+  const float f = sm.neg[L][tx] ? -1.f : 1.f;
+  project_p<MU>(w, sgn, h);
+  float4 e[9];
+  link_elems(sm, L, tx, e);
+  link_mul_p<BACK>(e, h, g);
+  reconstruct_p<MU>(g, sgn, f, acc);
+}
+
 // The same for one site whose links come from global memory (single-slice
 // stencil): direction MU, forward or backward.
 template <int P, int RECON, int MU, bool BACK>

@@ -18,6 +18,7 @@
 // Only the half spinor h is multiplied by the link: 2 x 66 flops instead of
 // 4 x 66.  Per output site and slice: 8 x (12 projection + 132 link) + 7 x 24
 // accumulation = 1320 flops.
+#include <climits>
 #include <cstdio>
 #include <string>
 #include <type_traits>
@@ -598,6 +599,129 @@ __device__ __forceinline__ void hop_smp(const HopArgs<P, RECON>& A) {
   }
 }
 
+// A measured prototype, slower than hop_smp (about 1.5 million copies of 16-byte
+// chunk runs of at most 512 bytes per launch at 16^3 x 32 x 16; the data still
+// crosses the shared-memory pipe once): kept as a tuner candidate.
+// The shared-memory-link kernel with packed arithmetic and two-row links (hop_smp,
+// L12) whose neighbour spinors are staged in shared memory by bulk copies: NBUF
+// buffers per warp (a warp is 32 consecutive sites of one slice), the copies of
+// direction L + NBUF - 1 issued (one chunk per lane) while direction L is computed
+// from shared memory.  The neighbours of a warp's sites in one direction lie in a run
+// of at most 32 consecutive sites unless the direction wraps around the lattice
+// between the warp's rows (y, z, t); such a direction is read from global memory as
+// in hop_smp.  A copy that never completes (bounded wait) makes the output NaN, which
+// the solver reports.
+constexpr int kRunSites = 32;
+constexpr int kRunFloat4 = 6 * kRunSites;  // one staged direction: 6 chunks x 32 sites
+
+template <int NBUF>
+struct SmtState {
+  int base[NBUF];
+  bool staged[NBUF];
+  unsigned phase[NBUF];
+  bool failed;
+};
+
+template <int L, int NBUF>
+__device__ __forceinline__ void smt_issue(const SmLinks12& sm, float4* stage, unsigned long long* bar,
+                                          const SpinorView<P32>& in, long soff, int tx, bool valid,
+                                          SmtState<NBUF>& S) {
+  constexpr int b = L % NBUF;
+  const int lo = __reduce_min_sync(0xffffffffu, valid ? sm.nb[L][tx] : INT_MAX);
+  const int hi = __reduce_max_sync(0xffffffffu, valid ? sm.nb[L][tx] : INT_MIN);
+  const int span = hi - lo + 1;
+  S.staged[b] = span <= kRunSites;
+  S.base[b] = lo;
+  if (!S.staged[b]) return;
+  if (tx == 0) mbar_expect_tx(&bar[b], 6u * (unsigned)span * 16u);
+  __syncwarp();
+  if (tx < 6) {  // lane q copies chunk q
+    fence_proxy_async();  // this buffer's earlier reads (ordered by the last __syncwarp) before the copy
+    bulk_g2s(stage + b * kRunFloat4 + tx * kRunSites, in.p + tx * in.stride + soff + lo, (unsigned)span * 16u,
+             &bar[b]);
+  }
+}
+
+template <int L, int NBUF>
+__device__ __forceinline__ void smt_step(const HopArgs<P32, 12>& A, const SmLinks12& sm, float4* stage,
+                                         unsigned long long* bar, const SpinorView<P32>& in, long soff, int tx,
+                                         bool valid, float sg, SmtState<NBUF>& S, P2 acc[6]) {
+  if constexpr (L + NBUF - 1 < 8) smt_issue<L + NBUF - 1, NBUF>(sm, stage, bar, in, soff, tx, valid, S);
+  constexpr int b = L % NBUF;
+  if (S.staged[b]) {
+    if (!mbar_wait(&bar[b], S.phase[b])) S.failed = true;
+    S.phase[b] ^= 1u;
+    if (valid) hop_link_run<P32, 12, L, kRunSites>(sm, tx, sg, stage + b * kRunFloat4, S.base[b], acc);
+  } else if (valid) {
+    hop_link_smp<P32, 12, L>(A, sm, tx, sg, in, soff, acc);
+  }
+  __syncwarp();  // every lane has read buffer b before later copies overwrite it
+}
+
+// dynamic shared memory: [BY][NBUF][kRunFloat4] float4, then [BY][NBUF] barriers
+template <int BY, int NBUF>
+constexpr size_t smt_smem() {
+  return (size_t)BY * NBUF * kRunFloat4 * sizeof(float4) + (size_t)BY * NBUF * sizeof(unsigned long long);
+}
+
+template <int BY, int NBUF>
+__global__ void __launch_bounds__(32 * BY) k_hop_smt(HopArgs<P32, 12> A) {
+  pdl_enter();
+  if (A.stop && *A.stop) return;
+  __shared__ SmLinks12 sm;
+  extern __shared__ __align__(16) unsigned char smt_raw[];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float4* stage = reinterpret_cast<float4*>(smt_raw) + (size_t)ty * NBUF * kRunFloat4;
+  unsigned long long* bar =
+      reinterpret_cast<unsigned long long*>(smt_raw + (size_t)BY * NBUF * kRunFloat4 * sizeof(float4)) + ty * NBUF;
+  const int sblock = fdiv(blockIdx.x, A.d_ntiles);
+  const int stile = blockIdx.x - sblock * A.ntiles;
+  const int cb = sblock * 32 + tx;
+  const bool valid = cb < A.g.Vh;
+  stage_links_sm12<P32, 12, BY>(A, sm, tx, ty, cb, valid);
+  if (tx < NBUF) mbar_init(&bar[tx], 1);
+  if (tx == 0) mbar_init_fence();
+  __syncthreads();
+  const int q0 = stile * BY + ty;
+  if (q0 >= A.nslices) return;  // a whole warp (one row of slices)
+  const int r = fdiv(q0, A.d_ls), s = q0 - r * A.ls;
+  const SpinorView<P32> in = A.in.offset_rhs(r);
+  const long soff = (long)s * A.g.Vh;
+  const float sg = A.dagger ? 1.f : -1.f;
+  P2 acc[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) acc[q] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  SmtState<NBUF> S;
+#pragma unroll
+  for (int k = 0; k < NBUF; ++k) S.phase[k] = 0u;
+  S.failed = false;
+  smt_issue<0, NBUF>(sm, stage, bar, in, soff, tx, valid, S);
+  if constexpr (NBUF > 2) smt_issue<1, NBUF>(sm, stage, bar, in, soff, tx, valid, S);
+  if constexpr (NBUF > 3) smt_issue<2, NBUF>(sm, stage, bar, in, soff, tx, valid, S);
+  smt_step<0, NBUF>(A, sm, stage, bar, in, soff, tx, valid, sg, S, acc);
+  smt_step<1, NBUF>(A, sm, stage, bar, in, soff, tx, valid, sg, S, acc);
+  smt_step<2, NBUF>(A, sm, stage, bar, in, soff, tx, valid, sg, S, acc);
+  smt_step<3, NBUF>(A, sm, stage, bar, in, soff, tx, valid, sg, S, acc);
+  smt_step<4, NBUF>(A, sm, stage, bar, in, soff, tx, valid, sg, S, acc);
+  smt_step<5, NBUF>(A, sm, stage, bar, in, soff, tx, valid, sg, S, acc);
+  smt_step<6, NBUF>(A, sm, stage, bar, in, soff, tx, valid, sg, S, acc);
+  smt_step<7, NBUF>(A, sm, stage, bar, in, soff, tx, valid, sg, S, acc);
+  if (!valid) return;
+  const long site = soff + cb;
+  float2 a2 = bc2((float)A.a);
+  if (S.failed) a2 = bc2(__int_as_float(0x7fc00000));  // a copy that never arrived: NaN output
+  P2 o[6];
+  if (A.xpay) {
+    A.x.offset_rhs(r).load_p(site, o);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) o[q] = {fma2(a2, acc[q].re, o[q].re), fma2(a2, acc[q].im, o[q].im)};
+  } else {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) o[q] = {__fmul2_rn(a2, acc[q].re), __fmul2_rn(a2, acc[q].im)};
+  }
+  A.out.offset_rhs(r).store_p(site, o);
+}
+
 // Tensor-core variant of the 12-rhs FP16 stencil (a measured prototype): one
 // direction's link multiply (t forward) for the 12 right-hand sides x 2 spins
 // of a site runs as warp-level MMAs, m16n8k16 with FP16 operands and FP32
@@ -857,6 +981,25 @@ void launch_smp(HopLaunch<P, RECON>* L) {
     launch_k(k_hop_smp<P, RECON, BY, RED, L12>, grid, blk, 0, L->st, A);
 }
 
+// the shared-memory-link kernel with bulk-copy staged neighbours (FP32, 12-real links,
+// 4 thread rows, NBUF buffers per warp)
+template <int P, int RECON, int NBUF>
+void launch_smt(HopLaunch<P, RECON>* L) {
+  if constexpr (P == P32 && RECON == 12) {
+    constexpr size_t smem = smt_smem<4, NBUF>();
+    static std::atomic<unsigned long long> attr_mask{0};
+    if (first_use_on_device(attr_mask))
+      QCD_CK(cudaFuncSetAttribute(k_hop_smt<4, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HopArgs<P, RECON> A = L->args;
+    A.ntiles = (A.nslices + 3) / 4;
+    A.d_ntiles = make_fastdiv((unsigned)A.ntiles);
+    const long sblocks = (A.g.Vh + 31) / 32;
+    launch_k(k_hop_smt<4, NBUF>, (unsigned)(sblocks * A.ntiles), dim3(32, 4), smem, L->st, A);
+  } else {
+    raise(QCD_ERR_UNSUPPORTED, "the bulk-copy staged stencil is the FP32, 12-real one");
+  }
+}
+
 // the packed FP16 stencil with fused inner products (one slice, A.red 1 or 2), SPT sites per thread
 template <int P, int RECON, int SPT = 1>
 void launch_pk_red(HopLaunch<P, RECON>* L, int block) {
@@ -881,8 +1024,10 @@ void launch_pk_red(HopLaunch<P, RECON>* L, int block) {
 // 64 registers per thread (32 resident warps per SM); -tile = 500 + 10 * BY + 1:
 // packed FP32x2 arithmetic, one slice per thread (k_hop_smp); 600 + ...: the
 // same with the registers bounded for 24 resident warps; 700 + ...: that with
-// the links staged as two rows; -3121: 12 slices, one direction by tensor-core MMA
-// (k_hop_tc; FP16, 12-real)
+// the links staged as two rows; -942: that with the neighbour spinors staged in shared
+// memory by bulk copies, 2 buffers per warp (k_hop_smt; FP32, 12-real; a measured
+// prototype, slower); -3121: 12 slices, one direction by
+// tensor-core MMA (k_hop_tc; FP16, 12-real)
 template <int P, int RECON>
 void run_cfg(void* ctx, const LaunchCfg& cfg) {
   auto* L = (HopLaunch<P, RECON>*)ctx;
@@ -932,6 +1077,7 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case -741: launch_smp<P, RECON, 4, 0, 1, RECON == 12>(L); break;  // 18-real: the -641 kernel
       case -781: launch_smp<P, RECON, 8, 0, 1, RECON == 12>(L); break;
       case -3121: launch_tc<P, RECON>(L); break;
+      case -942: launch_smt<P, RECON, 2>(L); break;
       default: launch_sm<P, RECON, 8, 2>(L); break;
     }
   }
@@ -999,6 +1145,7 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
     for (int t : {-581, -681, -781})
       if (t != -781 || RECON == 12) cands.push_back({256, t});
   if (P == P16 && RECON == 12 && A.nslices == 12) cands.push_back({384, -3121});  // tensor-core direction
+  if (P == P32 && RECON == 12 && A.nslices >= 4) cands.push_back({128, -942});  // bulk-copy staged neighbours
   if (A.red) {  // the fused reduction exists for one slice per thread only
     cands.clear();
     if (P != P16)

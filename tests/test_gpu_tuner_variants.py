@@ -98,7 +98,7 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
     # (tile code, block) of every candidate family; the shared-memory kernels fix their block
     shapes = [(1, 128), (2, 64), (4, 256), (101, 64), (201, 128), (301, 64), (311, 128), (321, 256), (-41, 128),
               (-42, 128), (-81, 256), (-82, 256), (-241, 128), (-281, 256), (-541, 128), (-581, 256), (-641, 128),
-              (-681, 256), (-741, 128), (-781, 256)]
+              (-681, 256), (-741, 128), (-781, 256), (-942, 128)]
     cases, lines, tol = [], [], []
     t = 4
     for prec, recon in (("f32", 12), ("f32", 18), ("f16", 12)):
@@ -107,11 +107,20 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
                 continue  # the register-bounded shapes are FP32 only
             if tile in (-741, -781) and recon != 12:
                 continue  # two-row link staging exists for 12-real links only
+            if tile == -942 and (prec, recon) != ("f32", 12):
+                continue  # the bulk-copy staged stencil is the FP32 12-real one
             L = (4, 4, 4, t)
             t += 2
             cases.append({"kind": "hop", "L": L, "prec": prec, "recon": recon, "nrhs": 16})
             lines.append(f"{_key(L, prec, recon, 16, 0, 0)}\t{block}\t{tile}")
             tol.append(1e-6 if prec == "f32" else 2e-3)
+    # the bulk-copy staged stencil where most directions are staged (8^4: x, z, t in one run per
+    # warp, y wrapping inside every warp and read from global memory) and on a ragged last block
+    for L, ns, tile in (((8, 8, 8, 8), 16, -942), ((6, 2, 4, t), 8, -942), ((8, 8, 8, 6), 5, -942)):
+        cases.append({"kind": "hop", "L": L, "prec": "f32", "recon": 12, "nrhs": ns})
+        lines.append(f"{_key(L, 'f32', 12, ns, 0, 0)}\t128\t{tile}")
+        tol.append(1e-6)
+    t += 2
     # the packed single-slice stencil on one right-hand side (the FP16 inner solves' D_eo)
     for prec, recon in (("f32", 12), ("f16", 12), ("f16", 18)):
         for tile, block in ((301, 128), (311, 256), (321, 64)):
