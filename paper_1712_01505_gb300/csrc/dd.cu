@@ -287,16 +287,33 @@ __global__ void __launch_bounds__(kThreads) k_dd_exterior(DDArgs<P, RECON> A) {
 }
 
 // ----------------------------------------------------------------------------- BLAS of the solver
+// Loads and stores with the storage precision PV fixed at compile time (the solver's
+// vectors share one precision), or read from the view (PV < 0)
+template <typename R, int PV>
+__device__ __forceinline__ void dld(const AnyView& v, long i, Cx<R> out[12]) {
+  if constexpr (PV < 0)
+    any_load<R>(v, 0, i, out);
+  else
+    any_load_p<R, PV>(v, 0, i, out);
+}
+template <typename R, int PV>
+__device__ __forceinline__ void dst(const AnyView& v, long i, const Cx<R> in[12]) {
+  if constexpr (PV < 0)
+    any_store<R>(v, 0, i, in);
+  else
+    any_store_p<R, PV>(v, 0, i, in);
+}
+
 // out = a x + b y + c out (complex host scalars; a term with a zero coefficient is not read)
-template <typename R>
+template <typename R, int PV>
 __global__ void k_dd_lin3(double2 a, AnyView x, double2 b, AnyView y, double2 c, AnyView out, long n) {
   const Cx<R> ca = {(R)a.x, (R)a.y}, cb_ = {(R)b.x, (R)b.y}, cc = {(R)c.x, (R)c.y};
   const bool ua = a.x != 0.0 || a.y != 0.0, ub = b.x != 0.0 || b.y != 0.0, uc = c.x != 0.0 || c.y != 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vx[12], vy[12], vo[12];
-    if (ua) any_load<R>(x, 0, i, vx);
-    if (ub) any_load<R>(y, 0, i, vy);
-    if (uc) any_load<R>(out, 0, i, vo);
+    if (ua) dld<R, PV>(x, i, vx);
+    if (ub) dld<R, PV>(y, i, vy);
+    if (uc) dld<R, PV>(out, i, vo);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       Cx<R> o = {R(0), R(0)};
@@ -305,24 +322,29 @@ __global__ void k_dd_lin3(double2 a, AnyView x, double2 b, AnyView y, double2 c,
       if (uc) o = cmadd(cc, vo[k], o);
       vo[k] = o;
     }
-    any_store<R>(out, 0, i, vo);
+    dst<R, PV>(out, i, vo);
   }
 }
 
-// per-block partial sums of (x, y) = sum conj(x) y (re, im) and |x|^2, in FP64
-template <typename R>
+// per-block partial sums of (x, y) = sum conj(x) y (re, im) and |x|^2: per site in R (FP32
+// vectors: FP32, as the single-domain solver's sums), across sites and threads in FP64
+template <typename R, int PV>
 __global__ void k_dd_dot(AnyView x, AnyView y, long n, double* partial) {
   double v[3] = {0.0, 0.0, 0.0};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     Cx<R> vx[12], vy[12];
-    any_load<R>(x, 0, i, vx);
-    any_load<R>(y, 0, i, vy);
+    dld<R, PV>(x, i, vx);
+    dld<R, PV>(y, i, vy);
+    R re = 0, im = 0, xx = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      v[0] += (double)vx[k].re * vy[k].re + (double)vx[k].im * vy[k].im;
-      v[1] += (double)vx[k].re * vy[k].im - (double)vx[k].im * vy[k].re;
-      v[2] += (double)vx[k].re * vx[k].re + (double)vx[k].im * vx[k].im;
+      re = fma(vx[k].re, vy[k].re, fma(vx[k].im, vy[k].im, re));
+      im = fma(vx[k].re, vy[k].im, fma(-vx[k].im, vy[k].re, im));
+      xx = fma(vx[k].re, vx[k].re, fma(vx[k].im, vx[k].im, xx));
     }
+    v[0] += (double)re;
+    v[1] += (double)im;
+    v[2] += (double)xx;
   }
   block_sum<3>(v);
   if (threadIdx.x == 0)
@@ -613,10 +635,15 @@ void lin3(std::complex<double> a, const Vec& x, std::complex<double> b, const Ve
     const double2 ca = make_double2(a.real(), a.imag()), cb = make_double2(b.real(), b.imag()),
                   cc = make_double2(c.real(), c.imag());
     const AnyView vx = any_view(x[k]), vy = any_view(y[k]), vo = any_view(out[k]);
-    if (out[k].prec == QCD_F64)
-      k_dd_lin3<double><<<blocks_for(n), kThreads, 0, st>>>(ca, vx, cb, vy, cc, vo, n);
+    const int pv = (x[k].prec == out[k].prec && y[k].prec == out[k].prec) ? out[k].prec : -1;
+    if (pv == QCD_F64)
+      k_dd_lin3<double, P64><<<blocks_for(n), kThreads, 0, st>>>(ca, vx, cb, vy, cc, vo, n);
+    else if (pv == QCD_F32)
+      k_dd_lin3<float, P32><<<blocks_for(n), kThreads, 0, st>>>(ca, vx, cb, vy, cc, vo, n);
+    else if (out[k].prec == QCD_F64)
+      k_dd_lin3<double, -1><<<blocks_for(n), kThreads, 0, st>>>(ca, vx, cb, vy, cc, vo, n);
     else
-      k_dd_lin3<float><<<blocks_for(n), kThreads, 0, st>>>(ca, vx, cb, vy, cc, vo, n);
+      k_dd_lin3<float, -1><<<blocks_for(n), kThreads, 0, st>>>(ca, vx, cb, vy, cc, vo, n);
     QCD_LAUNCH_CK();
   }
 }
@@ -641,10 +668,15 @@ void dot(qcd_dd* d, const Vec& x, const Vec& y, std::complex<double>* xy, double
     const long n = x[k].nsites();
     const unsigned nb = blocks_for(n);
     nbs.push_back(nb);
-    if (x[k].prec == QCD_F64)
-      k_dd_dot<double><<<nb, kThreads, 0, st>>>(any_view(x[k]), any_view(y[k]), n, d->subs[k].partial);
+    const int pv = x[k].prec == y[k].prec ? x[k].prec : -1;
+    if (pv == QCD_F64)
+      k_dd_dot<double, P64><<<nb, kThreads, 0, st>>>(any_view(x[k]), any_view(y[k]), n, d->subs[k].partial);
+    else if (pv == QCD_F32)
+      k_dd_dot<float, P32><<<nb, kThreads, 0, st>>>(any_view(x[k]), any_view(y[k]), n, d->subs[k].partial);
+    else if (x[k].prec == QCD_F64 || y[k].prec == QCD_F64)
+      k_dd_dot<double, -1><<<nb, kThreads, 0, st>>>(any_view(x[k]), any_view(y[k]), n, d->subs[k].partial);
     else
-      k_dd_dot<float><<<nb, kThreads, 0, st>>>(any_view(x[k]), any_view(y[k]), n, d->subs[k].partial);
+      k_dd_dot<float, -1><<<nb, kThreads, 0, st>>>(any_view(x[k]), any_view(y[k]), n, d->subs[k].partial);
     QCD_LAUNCH_CK();
     QCD_CK(cudaMemcpyAsync(d->red_host + off, d->subs[k].partial, sizeof(double) * nb * 4, cudaMemcpyDeviceToHost,
                            st));
