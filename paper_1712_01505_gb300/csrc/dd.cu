@@ -352,6 +352,45 @@ __global__ void k_dd_dot(AnyView x, AnyView y, long n, double* partial) {
     for (int k = 0; k < 3; ++k) partial[blockIdx.x * 4 + k] = v[k];
 }
 
+// x += alpha p + omega s; r = s - omega t (in lin3's order of operations) and the per-block
+// partial sums of (r, rt) and |r|^2 as k_dd_dot forms them
+template <typename R, int PV>
+__global__ void k_dd_xr(double2 al, double2 om, AnyView p, AnyView s, AnyView t, AnyView x, AnyView r,
+                        AnyView rt, long n, double* partial) {
+  const Cx<R> a = {(R)al.x, (R)al.y}, w = {(R)om.x, (R)om.y}, mw = {(R)-om.x, (R)-om.y}, one = {R(1), R(0)};
+  double v[3] = {0.0, 0.0, 0.0};
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    Cx<R> vp[12], vs[12], vt[12], vx[12], vr[12];
+    dld<R, PV>(p, i, vp);
+    dld<R, PV>(s, i, vs);
+    dld<R, PV>(t, i, vt);
+    dld<R, PV>(x, i, vx);
+    dld<R, PV>(rt, i, vr);  // rt here; r is written below
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const Cx<R> zero = {R(0), R(0)};
+      vx[k] = cmadd(one, vx[k], cmadd(w, vs[k], cmadd(a, vp[k], zero)));
+      vs[k] = cmadd(mw, vt[k], cmadd(one, vs[k], zero));
+    }
+    dst<R, PV>(x, i, vx);
+    dst<R, PV>(r, i, vs);
+    R re = 0, im = 0, xx = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      re = fma(vs[k].re, vr[k].re, fma(vs[k].im, vr[k].im, re));
+      im = fma(vs[k].re, vr[k].im, fma(-vs[k].im, vr[k].re, im));
+      xx = fma(vs[k].re, vs[k].re, fma(vs[k].im, vs[k].im, xx));
+    }
+    v[0] += (double)re;
+    v[1] += (double)im;
+    v[2] += (double)xx;
+  }
+  block_sum<3>(v);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) partial[blockIdx.x * 4 + k] = v[k];
+}
+
 unsigned blocks_for(long n) {
   long b = (n + kThreads - 1) / kThreads;
   long cap = 4L * sm_count();
@@ -659,15 +698,38 @@ void allreduce(qcd_dd* d, double* v, int n, cudaStream_t st) {
   QCD_CK(cudaStreamSynchronize(st));
 }
 
-// global (x, y) and |x|^2
-void dot(qcd_dd* d, const Vec& x, const Vec& y, std::complex<double>* xy, double* xx, cudaStream_t st) {
-  // every subdomain's partials to the pinned host buffer, one synchronisation
+// The global sums (over this process's subdomains in id order, then over the processes) of
+// the per-block partials that launch(k, nb) leaves in subdomain k's partial buffer: every
+// subdomain's partials go to the pinned host buffer together, one synchronisation.
+template <typename F>
+void global_sums(qcd_dd* d, size_t nsub, F&& launch, double v[3], cudaStream_t st) {
   std::vector<unsigned> nbs;
   size_t off = 0;
-  for (size_t k = 0; k < x.size(); ++k) {
+  for (size_t k = 0; k < nsub; ++k) {
+    const unsigned nb = launch(k);
+    QCD_LAUNCH_CK();
+    nbs.push_back(nb);
+    QCD_CK(cudaMemcpyAsync(d->red_host + off, d->subs[k].partial, sizeof(double) * nb * 4, cudaMemcpyDeviceToHost,
+                           st));
+    off += (size_t)nb * 4;
+  }
+  QCD_CK(cudaStreamSynchronize(st));
+  v[0] = v[1] = v[2] = 0.0;
+  off = 0;
+  for (size_t k = 0; k < nsub; ++k) {
+    for (unsigned b = 0; b < nbs[k]; ++b)
+      for (int j = 0; j < 3; ++j) v[j] += d->red_host[off + (size_t)b * 4 + j];
+    off += (size_t)nbs[k] * 4;
+  }
+  allreduce(d, v, 3, st);
+}
+
+// global (x, y) and |x|^2
+void dot(qcd_dd* d, const Vec& x, const Vec& y, std::complex<double>* xy, double* xx, cudaStream_t st) {
+  double v[3];
+  global_sums(d, x.size(), [&](size_t k) {
     const long n = x[k].nsites();
     const unsigned nb = blocks_for(n);
-    nbs.push_back(nb);
     const int pv = x[k].prec == y[k].prec ? x[k].prec : -1;
     if (pv == QCD_F64)
       k_dd_dot<double, P64><<<nb, kThreads, 0, st>>>(any_view(x[k]), any_view(y[k]), n, d->subs[k].partial);
@@ -677,22 +739,31 @@ void dot(qcd_dd* d, const Vec& x, const Vec& y, std::complex<double>* xy, double
       k_dd_dot<double, -1><<<nb, kThreads, 0, st>>>(any_view(x[k]), any_view(y[k]), n, d->subs[k].partial);
     else
       k_dd_dot<float, -1><<<nb, kThreads, 0, st>>>(any_view(x[k]), any_view(y[k]), n, d->subs[k].partial);
-    QCD_LAUNCH_CK();
-    QCD_CK(cudaMemcpyAsync(d->red_host + off, d->subs[k].partial, sizeof(double) * nb * 4, cudaMemcpyDeviceToHost,
-                           st));
-    off += (size_t)nb * 4;
-  }
-  QCD_CK(cudaStreamSynchronize(st));
-  double v[3] = {0.0, 0.0, 0.0};
-  off = 0;
-  for (size_t k = 0; k < x.size(); ++k) {
-    for (unsigned b = 0; b < nbs[k]; ++b)
-      for (int j = 0; j < 3; ++j) v[j] += d->red_host[off + (size_t)b * 4 + j];
-    off += (size_t)nbs[k] * 4;
-  }
-  allreduce(d, v, 3, st);
+    return nb;
+  }, v, st);
   if (xy) *xy = std::complex<double>(v[0], v[1]);
   if (xx) *xx = v[2];
+}
+
+// x += alpha p + omega s; r = s - omega t; the global (r, rt) and |r|^2 (one pass over the
+// vectors, all of the solver's inner precision)
+void xr_dot(qcd_dd* d, std::complex<double> alpha, std::complex<double> omega, const Vec& p, const Vec& s,
+            const Vec& t, Vec& x, Vec& r, const Vec& rt, std::complex<double>* rrt, double* rr, cudaStream_t st) {
+  double v[3];
+  const double2 al = make_double2(alpha.real(), alpha.imag()), om = make_double2(omega.real(), omega.imag());
+  global_sums(d, p.size(), [&](size_t k) {
+    const long n = p[k].nsites();
+    const unsigned nb = blocks_for(n);
+    const AnyView vp = any_view(p[k]), vs = any_view(s[k]), vt = any_view(t[k]), vx = any_view(x[k]),
+                  vr = any_view(r[k]), vrt = any_view(rt[k]);
+    if (p[k].prec == QCD_F64)
+      k_dd_xr<double, P64><<<nb, kThreads, 0, st>>>(al, om, vp, vs, vt, vx, vr, vrt, n, d->subs[k].partial);
+    else
+      k_dd_xr<float, P32><<<nb, kThreads, 0, st>>>(al, om, vp, vs, vt, vx, vr, vrt, n, d->subs[k].partial);
+    return nb;
+  }, v, st);
+  *rrt = std::complex<double>(v[0], v[1]);
+  *rr = v[2];
 }
 
 double norm2(qcd_dd* d, const Vec& y, cudaStream_t st) {
@@ -971,11 +1042,10 @@ void dd_solve(qcd_dd* d, const qcd_fermion& f, const qcd_solver_params& prm, con
         breakdown = !(tt > 0.0);
         if (!breakdown) {
           omega = ts / tt;
-          lin3(alpha, p, omega, s, 1.0, xin, st);  // x += alpha p + omega s
-          lin3(1.0, s, -omega, t, 0.0, r, st);    // r = s - omega t
           rho = rho_new;
           std::complex<double> c;
-          dot(d, r, rt, &c, &r2, st);  // |r|^2 and the next iteration's (rt, r)
+          // x += alpha p + omega s, r = s - omega t, |r|^2 and the next iteration's (rt, r)
+          xr_dot(d, alpha, omega, p, s, t, xin, r, rt, &c, &r2, st);
           rho_next = std::conj(c);
           ++iters;
         }
