@@ -531,6 +531,7 @@ unsigned wave_blocks(const void* kernel, long n) {
 // the most blocks per SM any of them can have (2048 threads of 256): the partial-sum arrays' size
 constexpr int kMaxBlocksPerSM = 8;
 
+// blocks of the host-side inner products (cdot_host): 4 per SM
 unsigned red_blocks(long n) {
   long b = (n + kThreads - 1) / kThreads;
   long cap = 4L * sm_count();
@@ -554,7 +555,7 @@ struct Solver {
   double* partial2 = nullptr;  // the end-of-iteration partials (k_bicg_xr reads omega's from `partial`)
   double* bpartial = nullptr;  // per-block partials of the fused stencil reductions
   int* counters = nullptr;     // their group counters (zero between launches)
-  unsigned nblk = 1;
+  unsigned nblk = 1;  // blocks of cdot_host (red_blocks); the iteration kernels size their own grids
   // fields
   Field b_e, b_o, bh, x64, r64, t64, u64, xo64, re64;  // FP64
   Field r, rt, p, v, s, t, q, w, xin;        // inner
