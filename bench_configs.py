@@ -457,6 +457,23 @@ def run_dd(args):
     g = qcd.Gauge.load(torch.from_numpy(U).to(dev), L, BC, recon=12)
     bd = torch.from_numpy(b).to(dev)
     out = {"workload": "dd_wilson_32x32x32x64_kappa0.125", "note": "subdomains of one process on one GPU"}
+    if args.profile == "cg":  # ncu launch list: one warmed-up decomposed solve in two subdomains
+        P = (1, 1, 1, 2)
+        ids = [0, 1]
+        D = dd.Decomposition(L, P, BC, ids, [dd.scatter_gauge(U, L, P, s) for s in ids], recon=12)
+        bl = [torch.from_numpy(dd.scatter_spinor(b, L, P, s)).to(dev) for s in ids]
+        xl = [torch.zeros_like(t_) for t_ in bl]
+        D.solve(f, bl, xl, tol=1e-10, inner="f32", delta=1e-5)
+        for t_ in xl:
+            t_.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        info, _ = D.solve(f, bl, xl, tol=1e-10, inner="f32", delta=1e-5)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(f"profile dd solve done: {info}", flush=True)
+        D.free()
+        return
     src = bd.clone()
     w = torch.empty_like(bd)
     ref = {}
