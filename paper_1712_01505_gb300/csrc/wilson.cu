@@ -199,8 +199,7 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
 // rides on the hop's boundary factor, the link multiply and the projection run
 // two spins per instruction).  PF as in k_hop.
 template <int P, int RECON, int PF>
-__global__ void __launch_bounds__(256) k_hop_pk(HopArgs<P, RECON> A) {
-  pdl_enter();
+__device__ __forceinline__ void hop_pk(const HopArgs<P, RECON>& A) {
   if (A.stop && *A.stop) return;
   const int sblock = fdiv(blockIdx.x, A.d_ntiles);
   const int q = blockIdx.x - sblock * A.ntiles;
@@ -237,6 +236,20 @@ __global__ void __launch_bounds__(256) k_hop_pk(HopArgs<P, RECON> A) {
     for (int k = 0; k < 6; ++k) o[k] = {__fmul2_rn(a2, acc[k].re), __fmul2_rn(a2, acc[k].im)};
   }
   A.out.offset_rhs(r).store_p(site, o);
+}
+
+template <int P, int RECON, int PF>
+__global__ void __launch_bounds__(256) k_hop_pk(HopArgs<P, RECON> A) {
+  pdl_enter();
+  hop_pk<P, RECON, PF>(A);
+}
+
+// the same for blocks of 64 threads with the registers bounded so that 14 blocks (28
+// warps) fit on an SM
+template <int P, int RECON, int PF>
+__global__ void __launch_bounds__(64, 14) k_hop_pk_occ(HopArgs<P, RECON> A) {
+  pdl_enter();
+  hop_pk<P, RECON, PF>(A);
 }
 
 constexpr int kRedGroup = 64;
@@ -349,10 +362,10 @@ __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
 // The packed single-slice stencil (k_hop_pk) with the inner products of
 // k_hop_red in its epilogue, for FP16 storage: the sums use the values as stored
 // (the FP16 halves times the site scale, for out as for rt and x), so they are
-// the inner products of the fields the next kernels read.  SPT sites per thread.
+// the inner products of the fields the next kernels read.  SPT sites per thread; the _occ
+// kernel: blocks of 64 threads with the registers bounded for 14 blocks (28 warps) per SM.
 template <int P, int RECON, int RED, int SPT>
-__global__ void __launch_bounds__(256) k_hop_pk_red(HopArgs<P, RECON> A) {
-  pdl_enter();
+__device__ __forceinline__ void hop_pk_red(const HopArgs<P, RECON>& A) {
   static_assert(P == P16, "the packed stencil with fused inner products is the FP16 one");
   if (A.stop && *A.stop) return;
   float v[3] = {0.f, 0.f, 0.f};
@@ -407,6 +420,18 @@ __global__ void __launch_bounds__(256) k_hop_pk_red(HopArgs<P, RECON> A) {
     v[1] += (di.x + di.y) - (dj.x + dj.y);
   }
   red_epilogue<float>(A, v);
+}
+
+template <int P, int RECON, int RED, int SPT>
+__global__ void __launch_bounds__(256) k_hop_pk_red(HopArgs<P, RECON> A) {
+  pdl_enter();
+  hop_pk_red<P, RECON, RED, SPT>(A);
+}
+
+template <int P, int RECON, int RED, int SPT>
+__global__ void __launch_bounds__(64, 14) k_hop_pk_red_occ(HopArgs<P, RECON> A) {
+  pdl_enter();
+  hop_pk_red<P, RECON, RED, SPT>(A);
 }
 
 // RED (with TS = 1, several right-hand sides): the BiCGStab inner products of
@@ -929,7 +954,7 @@ void launch_tile(HopLaunch<P, RECON>* L, int block) {
   launch_k(k_hop<P, RECON, TILE, PF>, (unsigned)(sblocks * A.ntiles), block, 0, L->st, A);
 }
 
-template <int P, int RECON, int PF>
+template <int P, int RECON, int PF, int OCC = 0>
 void launch_pk(HopLaunch<P, RECON>* L, int block) {
   if constexpr (P == P64) {
     raise(QCD_ERR_UNSUPPORTED, "no packed FP64 stencil");
@@ -937,8 +962,12 @@ void launch_pk(HopLaunch<P, RECON>* L, int block) {
     HopArgs<P, RECON> A = L->args;
     A.ntiles = A.nslices;
     A.d_ntiles = make_fastdiv((unsigned)A.ntiles);
+    if (OCC) block = 64;
     const long sblocks = (A.g.Vh + block - 1) / block;
-    launch_k(k_hop_pk<P, RECON, PF>, (unsigned)(sblocks * A.ntiles), block, 0, L->st, A);
+    if constexpr (OCC)
+      launch_k(k_hop_pk_occ<P, RECON, PF>, (unsigned)(sblocks * A.ntiles), block, 0, L->st, A);
+    else
+      launch_k(k_hop_pk<P, RECON, PF>, (unsigned)(sblocks * A.ntiles), block, 0, L->st, A);
   }
 }
 
@@ -1000,16 +1029,25 @@ void launch_smt(HopLaunch<P, RECON>* L) {
   }
 }
 
-// the packed FP16 stencil with fused inner products (one slice, A.red 1 or 2), SPT sites per thread
-template <int P, int RECON, int SPT = 1>
+// the packed FP16 stencil with fused inner products (one slice, A.red 1 or 2), SPT sites per
+// thread; OCC: the register-bounded kernel (blocks of 64)
+template <int P, int RECON, int SPT = 1, int OCC = 0>
 void launch_pk_red(HopLaunch<P, RECON>* L, int block) {
   if constexpr (P == P16) {
     const HopArgs<P, RECON>& A = L->args;
+    if (OCC) block = 64;
     const unsigned blocks = (unsigned)((A.g.Vh + block * SPT - 1) / (block * SPT));
-    if (A.red == 1)
-      launch_k(k_hop_pk_red<P, RECON, 1, SPT>, blocks, block, 0, L->st, A);
-    else
-      launch_k(k_hop_pk_red<P, RECON, 2, SPT>, blocks, block, 0, L->st, A);
+    if constexpr (OCC) {
+      if (A.red == 1)
+        launch_k(k_hop_pk_red_occ<P, RECON, 1, SPT>, blocks, block, 0, L->st, A);
+      else
+        launch_k(k_hop_pk_red_occ<P, RECON, 2, SPT>, blocks, block, 0, L->st, A);
+    } else {
+      if (A.red == 1)
+        launch_k(k_hop_pk_red<P, RECON, 1, SPT>, blocks, block, 0, L->st, A);
+      else
+        launch_k(k_hop_pk_red<P, RECON, 2, SPT>, blocks, block, 0, L->st, A);
+    }
   } else {
     raise(QCD_ERR_UNSUPPORTED, "the packed stencil with fused inner products is the FP16 one");
   }
@@ -1017,8 +1055,10 @@ void launch_pk_red(HopLaunch<P, RECON>* L, int block) {
 
 // cfg.tile > 0: register tile of that many slices per thread (k_hop), 101 /
 // 201: one slice per thread with prefetch mode 1 / 2; 301 / 311 / 321: one slice
-// per thread with packed arithmetic (k_hop_pk), prefetch mode 0 / 1 / 2; 341 / 342 /
-// 344: the FP16 stencil with the fused inner products, 1 / 2 / 4 sites per thread;
+// per thread with packed arithmetic (k_hop_pk), prefetch mode 0 / 1 / 2; 306 / 316: that
+// (prefetch mode 0 / 1) with blocks of 64 and registers bounded for 28 warps per SM; 341 /
+// 342 / 344: the FP16 stencil with the fused inner products, 1 / 2 / 4 sites per thread;
+// 346: that with one site per thread, register-bounded as 306;
 // cfg.tile < 0: shared-memory links (k_hop_sm), -tile = 10 * BY + TS for
 // BY thread rows of TS slices each; -tile = 200 + 10 * BY + TS: the same with at most
 // 64 registers per thread (32 resident warps per SM); -tile = 500 + 10 * BY + 1:
@@ -1038,6 +1078,8 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       launch_pk_red<P, RECON, 4>(L, cfg.block);
     else if (cfg.tile == 342)
       launch_pk_red<P, RECON, 2>(L, cfg.block);
+    else if (cfg.tile == 346)
+      launch_pk_red<P, RECON, 1, 1>(L, 64);
     else
       launch_pk_red<P, RECON, 1>(L, cfg.block);
   } else if (L->args.red && L->args.nslices > 1) {  // fused reductions over several slices
@@ -1063,6 +1105,8 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
       case 301: launch_pk<P, RECON, 0>(L, cfg.block); break;
       case 311: launch_pk<P, RECON, 1>(L, cfg.block); break;
       case 321: launch_pk<P, RECON, 2>(L, cfg.block); break;
+      case 306: launch_pk<P, RECON, 0, 1>(L, 64); break;
+      case 316: launch_pk<P, RECON, 1, 1>(L, 64); break;
       case 2: launch_tile<P, RECON, 2>(L, cfg.block); break;
       case 4: launch_tile<P, RECON, 4>(L, cfg.block); break;
       case -41: launch_sm<P, RECON, 4, 1>(L); break;
@@ -1157,9 +1201,12 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (A.red && P == P16)  // FP16: the packed stencil, its sums over the values as stored, 1 / 2 / 4 sites a thread
     for (int t : {341, 342, 344})
       for (int b : blocks) cands.push_back({b, t});
+  if (A.red && P == P16) cands.push_back({64, 346});  // the same register-bounded (28 warps per SM)
   if (P != P64 && !A.red)  // one slice per thread, packed arithmetic, with 0, 1 or 2 directions of prefetch
     for (int pk : {301, 311, 321})
       for (int b : blocks) cands.push_back({b, pk});
+  if (P == P16 && !A.red)  // the packed FP16 stencil with the registers bounded for 28 warps per SM
+    for (int pk : {306, 316}) cands.push_back({64, pk});
   if (multi_red) {  // shared-memory links, one slice per thread
     cands = {{128, -41}, {256, -81}, {128, -241}, {256, -281}, {128, -541}, {256, -581}, {128, -641}, {256, -681}};
     if (RECON == 12) {

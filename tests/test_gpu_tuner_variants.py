@@ -121,6 +121,12 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
         lines.append(f"{_key(L, 'f32', 12, ns, 0, 0)}\t128\t{tile}")
         tol.append(1e-6)
     t += 2
+    # the register-bounded packed FP16 stencil (28 warps per SM), one and several slices
+    for L, ns, tile, recon in (((4, 4, 4, t), 1, 306, 12), ((6, 2, 4, t + 2), 1, 316, 12), ((4, 4, 4, t + 4), 4, 306, 18)):
+        cases.append({"kind": "hop", "L": L, "prec": "f16", "recon": recon, "nrhs": ns})
+        lines.append(f"{_key(L, 'f16', recon, ns, 0, 0)}\t64\t{tile}")
+        tol.append(2e-3)
+    t += 6
     # the packed single-slice stencil on one right-hand side (the FP16 inner solves' D_eo)
     for prec, recon in (("f32", 12), ("f16", 12), ("f16", 18)):
         for tile, block in ((301, 128), (311, 256), (321, 64)):
@@ -147,12 +153,13 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
     # (BiCGStab and CG; a ragged last block too)
     for L, block, cg, tile in (((8, 8, 8, t), 64, False, 341), ((6, 6, 4, t + 2), 256, False, 341),
                                ((8, 8, 8, t + 4), 128, True, 341), ((6, 6, 4, t + 6), 64, False, 342),
-                               ((6, 6, 4, t + 8), 128, True, 344), ((8, 8, 8, t + 10), 64, False, 344)):
+                               ((6, 6, 4, t + 8), 128, True, 344), ((8, 8, 8, t + 10), 64, False, 344),
+                               ((6, 6, 4, t + 12), 64, False, 346), ((8, 8, 8, t + 14), 64, True, 346)):
         cases.append({"kind": "solve", "L": L, "recon": 12, "inner": "f16", "cg": cg})
         for xp, red in ((1, 1), (1, 2)) if not cg else ((1, 1),):
             lines.append(f"{_key(L, 'f16', 12, 1, xp, red)}\t{block}\t{tile}")
         tol.append(1e-10)
-    t += 12
+    t += 16
     # the fused-reduction shared-memory stencils of the batched (several rhs) iteration
     for tile, block in ((-41, 128), (-81, 256), (-241, 128), (-281, 256), (-541, 128), (-581, 256),
                         (-641, 128), (-681, 256), (-741, 128), (-781, 256)):
