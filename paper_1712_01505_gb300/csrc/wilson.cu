@@ -148,8 +148,7 @@ __device__ __forceinline__ void prefetch_before(const HopArgs<P, RECON>& A, cons
 }
 
 template <int P, int RECON, int TILE, int PF>
-__global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
-  pdl_enter();
+__device__ __forceinline__ void hop_tile(const HopArgs<P, RECON>& A) {
   using R = typename MathType<P>::type;
   if (A.stop && *A.stop) return;
   // block -> (site block, slice tile), tiles of one site block adjacent in
@@ -191,6 +190,20 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
     }
     A.out.offset_rhs(r).store(site, o);
   }
+}
+
+template <int P, int RECON, int TILE, int PF>
+__global__ void __launch_bounds__(256) k_hop(HopArgs<P, RECON> A) {
+  pdl_enter();
+  hop_tile<P, RECON, TILE, PF>(A);
+}
+
+// one slice per thread in blocks of 64 with the registers bounded so that 14 blocks (28
+// warps) fit on an SM
+template <int P, int RECON, int PF>
+__global__ void __launch_bounds__(64, 14) k_hop_occ(HopArgs<P, RECON> A) {
+  pdl_enter();
+  hop_tile<P, RECON, 1, PF>(A);
 }
 
 // One (site, slice) per thread with the packed FP32x2 arithmetic of stencil.cuh
@@ -313,8 +326,7 @@ __device__ __forceinline__ void red_epilogue(const HA& A, R v[3]) {
 // block of each group of 64 blocks sums the group (fixed order, so the result
 // does not depend on block scheduling).
 template <int P, int RECON, int RED, int PF>
-__global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
-  pdl_enter();
+__device__ __forceinline__ void hop_red(const HopArgs<P, RECON>& A) {
   using R = typename MathType<P>::type;
   if (A.stop && *A.stop) return;
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
@@ -357,6 +369,18 @@ __global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
     v[1] = d.im;
   }
   red_epilogue<R>(A, v);
+}
+
+template <int P, int RECON, int RED, int PF>
+__global__ void __launch_bounds__(256) k_hop_red(HopArgs<P, RECON> A) {
+  pdl_enter();
+  hop_red<P, RECON, RED, PF>(A);
+}
+
+template <int P, int RECON, int RED, int PF>
+__global__ void __launch_bounds__(64, 14) k_hop_red_occ(HopArgs<P, RECON> A) {
+  pdl_enter();
+  hop_red<P, RECON, RED, PF>(A);
 }
 
 // The packed single-slice stencil (k_hop_pk) with the inner products of
@@ -935,23 +959,35 @@ struct HopLaunch {
   cudaStream_t st;
 };
 
-template <int P, int RECON, int TILE, int PF = 0>
+// OCC = 1 (one slice per thread): the register-bounded kernels, blocks of 64
+template <int P, int RECON, int TILE, int PF = 0, int OCC = 0>
 void launch_tile(HopLaunch<P, RECON>* L, int block) {
+  static_assert(OCC == 0 || TILE == 1, "the register-bounded stencil has one slice per thread");
   HopArgs<P, RECON> A = L->args;
   A.ntiles = (A.nslices + TILE - 1) / TILE;
   A.d_ntiles = make_fastdiv((unsigned)A.ntiles);
+  if (OCC) block = 64;
   long sblocks = (A.g.Vh + block - 1) / block;
   if constexpr (TILE == 1 && P != P16) {
     if (A.red == 1) {
-      launch_k(k_hop_red<P, RECON, 1, PF>, (unsigned)sblocks, block, 0, L->st, A);
+      if constexpr (OCC)
+        launch_k(k_hop_red_occ<P, RECON, 1, PF>, (unsigned)sblocks, block, 0, L->st, A);
+      else
+        launch_k(k_hop_red<P, RECON, 1, PF>, (unsigned)sblocks, block, 0, L->st, A);
       return;
     }
     if (A.red == 2) {
-      launch_k(k_hop_red<P, RECON, 2, PF>, (unsigned)sblocks, block, 0, L->st, A);
+      if constexpr (OCC)
+        launch_k(k_hop_red_occ<P, RECON, 2, PF>, (unsigned)sblocks, block, 0, L->st, A);
+      else
+        launch_k(k_hop_red<P, RECON, 2, PF>, (unsigned)sblocks, block, 0, L->st, A);
       return;
     }
   }
-  launch_k(k_hop<P, RECON, TILE, PF>, (unsigned)(sblocks * A.ntiles), block, 0, L->st, A);
+  if constexpr (OCC)
+    launch_k(k_hop_occ<P, RECON, PF>, (unsigned)(sblocks * A.ntiles), block, 0, L->st, A);
+  else
+    launch_k(k_hop<P, RECON, TILE, PF>, (unsigned)(sblocks * A.ntiles), block, 0, L->st, A);
 }
 
 template <int P, int RECON, int PF, int OCC = 0>
@@ -1054,7 +1090,9 @@ void launch_pk_red(HopLaunch<P, RECON>* L, int block) {
 }
 
 // cfg.tile > 0: register tile of that many slices per thread (k_hop), 101 /
-// 201: one slice per thread with prefetch mode 1 / 2; 301 / 311 / 321: one slice
+// 201: one slice per thread with prefetch mode 1 / 2; 501 / 511: one slice per thread,
+// prefetch mode 0 / 1, blocks of 64 with the registers bounded for 28 warps per SM
+// (k_hop_occ, k_hop_red_occ); 301 / 311 / 321: one slice
 // per thread with packed arithmetic (k_hop_pk), prefetch mode 0 / 1 / 2; 306 / 316: that
 // (prefetch mode 0 / 1) with blocks of 64 and registers bounded for 28 warps per SM; 341 /
 // 342 / 344: the FP16 stencil with the fused inner products, 1 / 2 / 4 sites per thread;
@@ -1101,6 +1139,8 @@ void run_cfg(void* ctx, const LaunchCfg& cfg) {
     switch (cfg.tile) {
       case 1: launch_tile<P, RECON, 1>(L, cfg.block); break;
       case 101: launch_tile<P, RECON, 1, 1>(L, cfg.block); break;
+      case 501: launch_tile<P, RECON, 1, 0, 1>(L, 64); break;
+      case 511: launch_tile<P, RECON, 1, 1, 1>(L, 64); break;
       case 201: launch_tile<P, RECON, 1, 2>(L, cfg.block); break;
       case 301: launch_pk<P, RECON, 0>(L, cfg.block); break;
       case 311: launch_pk<P, RECON, 1>(L, cfg.block); break;
@@ -1198,6 +1238,8 @@ void hop_impl(const qcd_gauge* gh, const void* links, const Field& in, Field& ou
   if (P != P64 && !(A.red && P == P16))  // one slice per thread with prefetches (memory-bound precisions)
     for (int pf : {101, 201})
       for (int b : blocks) cands.push_back({b, pf});
+  if (P == P32 && A.nslices == 1)  // the same register-bounded (blocks of 64, 28 warps per SM)
+    for (int t : {501, 511}) cands.push_back({64, t});
   if (A.red && P == P16)  // FP16: the packed stencil, its sums over the values as stored, 1 / 2 / 4 sites a thread
     for (int t : {341, 342, 344})
       for (int b : blocks) cands.push_back({b, t});

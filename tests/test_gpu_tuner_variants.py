@@ -121,6 +121,12 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
         lines.append(f"{_key(L, 'f32', 12, ns, 0, 0)}\t128\t{tile}")
         tol.append(1e-6)
     t += 2
+    # the register-bounded scalar FP32 stencil (28 warps per SM) on one right-hand side
+    for L, tile in (((4, 4, 4, t), 501), ((6, 2, 4, t + 2), 511)):
+        cases.append({"kind": "hop", "L": L, "prec": "f32", "recon": 12, "nrhs": 1})
+        lines.append(f"{_key(L, 'f32', 12, 1, 0, 0)}\t64\t{tile}")
+        tol.append(1e-6)
+    t += 4
     # the register-bounded packed FP16 stencil (28 warps per SM), one and several slices
     for L, ns, tile, recon in (((4, 4, 4, t), 1, 306, 12), ((6, 2, 4, t + 2), 1, 316, 12), ((4, 4, 4, t + 4), 4, 306, 18)):
         cases.append({"kind": "hop", "L": L, "prec": "f16", "recon": recon, "nrhs": ns})
@@ -141,8 +147,9 @@ def test_every_stencil_candidate_matches_the_oracle(tmp_path):
         lines.append(f"{_key(L, 'f16', 12, 12, 0, 0)}\t384\t-3121")
         tol.append(2e-3)
     t += 4
-    # the fused-reduction stencils of the FP32 BiCGStab iteration, plain and with prefetches
-    for tile, block in ((1, 64), (101, 128), (201, 64)):
+    # the fused-reduction stencils of the FP32 BiCGStab iteration, plain and with prefetches,
+    # and register-bounded
+    for tile, block in ((1, 64), (101, 128), (201, 64), (501, 64), (511, 64)):
         L = (8, 8, 8, t)
         t += 2
         cases.append({"kind": "solve", "L": L, "recon": 12})
